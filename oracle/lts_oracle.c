@@ -1,0 +1,1149 @@
+/*
+ * Oracle for Localized Topological Simplification (LTS) on Freudenthal grids.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded CPU
+ * restatement of the method, written to be checked against the paper by eye.
+ * Only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or helper with the
+ * CUDA library.
+ *
+ * What follows the paper, and where:
+ *   - domain, star/link, lower/upper link, critical point index ....... Sec. 3.1
+ *   - persistence pairs by the Elder rule (input selector) ............ Sec. 3.3
+ *   - order field (sort by value, ties by memory position) ............ Sec. 4.1
+ *   - superlevel set propagation from one maximum (step 1) ............ Sec. 4.2
+ *   - hill chains: stop / merge at saddles, queue melding, union-find . Sec. 4.3
+ *   - arrival counter of unvisited higher neighbours .................. Sec. 4.4
+ *   - localized simplification by alternating propagations (step 2) .. Sec. 4.2, Eq. 3-5
+ *   - local to global order (step 3), pair order ...................... Sec. 4.2, Eq. 6
+ *   - symbolic to numerical perturbation (step 4) ..................... Sec. 4.2
+ *   - minima processed symmetrically to maxima ........................ Sec. 4
+ *
+ * Readings taken where the paper is silent (each is listed in the design
+ * notes of the repository):
+ *   - the triangulation is Freudenthal/Kuhn with diagonals along +(1,1)
+ *     and +(1,1,1); a missing neighbour at the grid boundary is dropped;
+ *   - -0.0 and +0.0 are one value (ties by vertex id); NaN is an error;
+ *   - "higher neighbour visited by some propagation" (Sec. 4.3) is read as
+ *     "owned by a propagation that has arrived at this saddle": the counter
+ *     of Sec. 4.4 counts the higher neighbours whose class has not yet
+ *     arrived.  The same regions are given by a join-tree sweep (method B);
+ *   - the vertex set to minus infinity in step 2 is, among the vertices of
+ *     R other than s that have a neighbour outside R and whose removal
+ *     leaves R connected, the one with the lowest order (with a cut vertex
+ *     the first propagation would not end there and could leave no
+ *     authorized minimum);
+ *   - the sublevel propagation of step 2 starts from every vertex allowed
+ *     to be a minimum (every vertex of R other than s with a neighbour
+ *     outside R), not only from those that are minima of the current local
+ *     order: seeded from the current minima alone, the alternation can cycle
+ *     forever (a cluster hanging off a cut vertex swaps its stray minimum and
+ *     maximum at every iteration);
+ *   - the pair order of Eq. 6 is made total for regions sharing a saddle:
+ *     sibling blocks are ordered by the order of their highest vertex;
+ *   - the numerical perturbation uses zeta = 0: every region vertex takes the
+ *     saddle's value bit for bit;
+ *   - one minima pass, then one maxima pass.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_NAN 2
+#define ORC_ERR_NO_AUTHORIZED 3
+#define ORC_ERR_OOM 4
+#define ORC_ERR_INTERNAL 7
+
+#define ORC_MODE_MIN 1
+#define ORC_MODE_MAX 2
+#define ORC_MODE_BOTH 3
+
+typedef struct {
+    int64_t n_vertices;
+    int64_t removed[2];          /* [0] minima pass, [1] maxima pass: unauthorized extrema */
+    int64_t regions[2];          /* regions (one per hill chain)                          */
+    int64_t region_vertices[2];  /* vertices moved (region members, saddles excluded)     */
+    int64_t max_region[2];       /* largest region, members only                          */
+    int32_t max_local_floods[2]; /* most propagations any region needed in step 2         */
+    int32_t pad;
+    int64_t total_local_floods[2];
+} orc_stats;
+
+/* ------------------------------------------------------------------------ */
+/* Domain: regular grid with the Freudenthal (Kuhn) triangulation.          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int ndim;
+    int64_t X, Y, Z, n;
+    int nn;
+    int off[14][3];
+} grid_t;
+
+/* The neighbours of a vertex are the lattice points p with p-v in {0,1}^d or
+ * in -{0,1}^d (v excluded): every such segment is an edge of the Kuhn
+ * triangulation of the unit cubes. */
+static void make_offsets(grid_t* G) {
+    int k = 0;
+    int d = G->ndim;
+    for (int m = 1; m < (1 << d); ++m) {
+        int o[3] = {0, 0, 0};
+        for (int b = 0; b < d; ++b) o[b] = (m >> b) & 1;
+        G->off[k][0] = o[0]; G->off[k][1] = o[1]; G->off[k][2] = o[2];
+        ++k;
+    }
+    int half = k;
+    for (int i = 0; i < half; ++i) {
+        G->off[k][0] = -G->off[i][0]; G->off[k][1] = -G->off[i][1]; G->off[k][2] = -G->off[i][2];
+        ++k;
+    }
+    G->nn = k;
+}
+
+static int grid_init(grid_t* G, int ndim, const int64_t* dims) {
+    if (ndim != 2 && ndim != 3) return ORC_ERR_ARG;
+    G->ndim = ndim;
+    G->X = dims[0]; G->Y = dims[1]; G->Z = (ndim == 3) ? dims[2] : 1;
+    if (G->X < 2 || G->Y < 2 || (ndim == 3 && G->Z < 2)) return ORC_ERR_ARG;
+    G->n = G->X * G->Y * G->Z;
+    if (G->n >= ((int64_t)1 << 31)) return ORC_ERR_ARG;
+    make_offsets(G);
+    return ORC_OK;
+}
+
+/* Existing neighbours of v, in offset order; returns their count. */
+static int nbrs(const grid_t* G, int64_t v, int32_t* out) {
+    int64_t x = v % G->X, y = (v / G->X) % G->Y, z = v / (G->X * G->Y);
+    int c = 0;
+    for (int k = 0; k < G->nn; ++k) {
+        int64_t a = x + G->off[k][0], b = y + G->off[k][1], e = z + G->off[k][2];
+        if (a < 0 || a >= G->X || b < 0 || b >= G->Y || e < 0 || e >= G->Z) continue;
+        out[c++] = (int32_t)(a + G->X * (b + G->Y * e));
+    }
+    return c;
+}
+
+/* Same, but also reports which offset each neighbour came from. */
+static int nbrs_k(const grid_t* G, int64_t v, int32_t* out, int* kk) {
+    int64_t x = v % G->X, y = (v / G->X) % G->Y, z = v / (G->X * G->Y);
+    int c = 0;
+    for (int k = 0; k < G->nn; ++k) {
+        int64_t a = x + G->off[k][0], b = y + G->off[k][1], e = z + G->off[k][2];
+        if (a < 0 || a >= G->X || b < 0 || b >= G->Y || e < 0 || e >= G->Z) continue;
+        kk[c] = k;
+        out[c++] = (int32_t)(a + G->X * (b + G->Y * e));
+    }
+    return c;
+}
+
+/* A set of lattice points is a simplex of the Kuhn triangulation iff the
+ * points form a chain under the componentwise order and the last minus the
+ * first lies in {0,1}^d. */
+static int is_kuhn_simplex(int d, int cnt, const int (*pts)[3]) {
+    int idx[4] = {0, 1, 2, 3};
+    /* sort by coordinate sum (insertion sort, at most four points) */
+    for (int i = 1; i < cnt; ++i) {
+        int j = i;
+        while (j > 0) {
+            const int* p = pts[idx[j - 1]];
+            const int* q = pts[idx[j]];
+            if (p[0] + p[1] + p[2] > q[0] + q[1] + q[2]) {
+                int t = idx[j]; idx[j] = idx[j - 1]; idx[j - 1] = t; --j;
+            } else break;
+        }
+    }
+    for (int i = 1; i < cnt; ++i) {
+        const int* p = pts[idx[i - 1]];
+        const int* q = pts[idx[i]];
+        int same = 1;
+        for (int b = 0; b < d; ++b) {
+            if (q[b] < p[b]) return 0;
+            if (q[b] != p[b]) same = 0;
+        }
+        if (same) return 0;
+    }
+    const int* lo = pts[idx[0]];
+    const int* hi = pts[idx[cnt - 1]];
+    for (int b = 0; b < d; ++b) {
+        int df = hi[b] - lo[b];
+        if (df != 0 && df != 1) return 0;
+    }
+    return 1;
+}
+
+/* Link graph of an interior vertex: pairs of offsets (a,b) with {0,a,b} a
+ * simplex.  Writes pairs of offset indices; returns the number of edges. */
+int orc_link_edges(int ndim, int32_t* pairs) {
+    grid_t G; memset(&G, 0, sizeof G); G.ndim = ndim; make_offsets(&G);
+    int e = 0;
+    for (int i = 0; i < G.nn; ++i)
+        for (int j = i + 1; j < G.nn; ++j) {
+            int pts[3][3] = {{0, 0, 0},
+                             {G.off[i][0], G.off[i][1], G.off[i][2]},
+                             {G.off[j][0], G.off[j][1], G.off[j][2]}};
+            if (is_kuhn_simplex(ndim, 3, (const int (*)[3])pts)) {
+                if (pairs) { pairs[2 * e] = i; pairs[2 * e + 1] = j; }
+                ++e;
+            }
+        }
+    return e;
+}
+
+/* Triangles of the link (3D): triples of offsets (a,b,c) with {0,a,b,c} a
+ * tetrahedron of the triangulation. */
+int orc_link_triangles(int ndim, int32_t* tris) {
+    grid_t G; memset(&G, 0, sizeof G); G.ndim = ndim; make_offsets(&G);
+    int t = 0;
+    for (int i = 0; i < G.nn; ++i)
+        for (int j = i + 1; j < G.nn; ++j)
+            for (int k = j + 1; k < G.nn; ++k) {
+                int pts[4][3] = {{0, 0, 0},
+                                 {G.off[i][0], G.off[i][1], G.off[i][2]},
+                                 {G.off[j][0], G.off[j][1], G.off[j][2]},
+                                 {G.off[k][0], G.off[k][1], G.off[k][2]}};
+                if (is_kuhn_simplex(ndim, 4, (const int (*)[3])pts)) {
+                    if (tris) { tris[3 * t] = i; tris[3 * t + 1] = j; tris[3 * t + 2] = k; }
+                    ++t;
+                }
+            }
+    return t;
+}
+
+int orc_neighbour_offsets(int ndim, int32_t* off) {
+    grid_t G; memset(&G, 0, sizeof G); G.ndim = ndim; make_offsets(&G);
+    for (int k = 0; k < G.nn; ++k)
+        for (int b = 0; b < 3; ++b) off[3 * k + b] = G.off[k][b];
+    return G.nn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Order field (Sec. 4.1): vertices sorted by increasing f, equal values     */
+/* disambiguated by their position in memory; O(v) is the rank of v.        */
+/* ------------------------------------------------------------------------ */
+
+static const float* s_sort_f;
+static int cmp_value_then_id(const void* pa, const void* pb) {
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    float fa = s_sort_f[a], fb = s_sort_f[b];
+    if (fa < fb) return -1;        /* IEEE compare: -0.0 == +0.0 */
+    if (fa > fb) return 1;
+    return (a > b) - (a < b);
+}
+
+int orc_order_field(int ndim, const int64_t* dims, const float* f, int32_t* O) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    for (int64_t v = 0; v < G.n; ++v)
+        if (isnan(f[v])) return ORC_ERR_NAN;
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * G.n);
+    if (!idx) return ORC_ERR_OOM;
+    for (int64_t v = 0; v < G.n; ++v) idx[v] = (int32_t)v;
+    s_sort_f = f;
+    qsort(idx, (size_t)G.n, sizeof(int32_t), cmp_value_then_id);
+    for (int64_t i = 0; i < G.n; ++i) O[idx[i]] = (int32_t)i;
+    free(idx);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Critical points (Sec. 3.1): numbers of connected components of the lower  */
+/* and upper links.  Minimum: empty lower link; maximum: empty upper link;    */
+/* regular: both non-empty and connected; otherwise a saddle.                */
+/* ------------------------------------------------------------------------ */
+
+static int small_find(int* p, int a) { while (p[a] != a) a = p[a]; return a; }
+
+int orc_classify(int ndim, const int64_t* dims, const int32_t* O, int8_t* n_lower, int8_t* n_upper) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    int32_t pairs[2 * 64];
+    int ne = orc_link_edges(ndim, pairs);
+    for (int64_t v = 0; v < G.n; ++v) {
+        int32_t nb[14]; int kk[14];
+        int c = nbrs_k(&G, v, nb, kk);
+        int present[14], lower[14], pos[14];
+        for (int k = 0; k < 14; ++k) { present[k] = 0; lower[k] = 0; pos[k] = -1; }
+        for (int i = 0; i < c; ++i) {
+            present[kk[i]] = 1;
+            lower[kk[i]] = O[nb[i]] < O[v];
+            pos[kk[i]] = i;
+        }
+        for (int side = 0; side < 2; ++side) {
+            int p[14];
+            for (int k = 0; k < 14; ++k) p[k] = k;
+            for (int e = 0; e < ne; ++e) {
+                int a = pairs[2 * e], b = pairs[2 * e + 1];
+                if (!present[a] || !present[b]) continue;
+                int wa = side == 0 ? lower[a] : !lower[a];
+                int wb = side == 0 ? lower[b] : !lower[b];
+                if (wa && wb) {
+                    int ra = small_find(p, a), rb = small_find(p, b);
+                    if (ra != rb) p[ra] = rb;
+                }
+            }
+            int comps = 0;
+            for (int k = 0; k < G.nn; ++k) {
+                if (!present[k]) continue;
+                int w = side == 0 ? lower[k] : !lower[k];
+                if (w && small_find(p, k) == k) ++comps;
+            }
+            if (side == 0) n_lower[v] = (int8_t)comps; else n_upper[v] = (int8_t)comps;
+        }
+        (void)pos;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Topological persistence (Sec. 3.3), used to select authorized extrema.   */
+/* Maxima: components of the superlevel sets are born at maxima and merge at */
+/* saddles; at a merge the component whose maximum is lower (the youngest)   */
+/* dies, giving the pair <s, m> with persistence f(m) - f(s).  The global    */
+/* maximum gets the function range.  Minima: the same on sublevel sets.      */
+/* pers[v] is NaN for vertices that are not extrema of that kind.           */
+/* ------------------------------------------------------------------------ */
+
+static int64_t uf_find64(int64_t* p, int64_t a) {
+    while (p[a] != a) { p[a] = p[p[a]]; a = p[a]; }
+    return a;
+}
+
+static int persistence_one(const grid_t* G, const float* f, const int32_t* O,
+                           const int32_t* perm, int descending, double* pers) {
+    int64_t n = G->n;
+    int64_t* par = (int64_t*)malloc(sizeof(int64_t) * n);
+    int32_t* best = (int32_t*)malloc(sizeof(int32_t) * n);  /* extremum of component (at root) */
+    if (!par || !best) { free(par); free(best); return ORC_ERR_OOM; }
+    for (int64_t v = 0; v < n; ++v) { par[v] = -1; pers[v] = NAN; }
+    double fmin = INFINITY, fmax = -INFINITY;
+    for (int64_t v = 0; v < n; ++v) {
+        if (f[v] < fmin) fmin = f[v];
+        if (f[v] > fmax) fmax = f[v];
+    }
+    double range = fmax - fmin;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t v = descending ? perm[n - 1 - i] : perm[i];
+        int32_t nb[14];
+        int c = nbrs(G, v, nb);
+        int64_t roots[14]; int nr = 0;
+        for (int j = 0; j < c; ++j) {
+            int32_t u = nb[j];
+            int earlier = descending ? (O[u] > O[v]) : (O[u] < O[v]);
+            if (!earlier) continue;
+            int64_t r = uf_find64(par, u);
+            int dup = 0;
+            for (int q = 0; q < nr; ++q) if (roots[q] == r) dup = 1;
+            if (!dup) roots[nr++] = r;
+        }
+        par[v] = v;
+        if (nr == 0) { best[v] = v; continue; }       /* v is an extremum: birth */
+        /* the oldest component survives (highest maximum / lowest minimum) */
+        int64_t keep = roots[0];
+        for (int q = 1; q < nr; ++q) {
+            int32_t a = best[roots[q]], b = best[keep];
+            int older = descending ? (O[a] > O[b]) : (O[a] < O[b]);
+            if (older) keep = roots[q];
+        }
+        for (int q = 0; q < nr; ++q) {
+            if (roots[q] == keep) continue;
+            int32_t m = best[roots[q]];
+            pers[m] = fabs((double)f[m] - (double)f[v]);
+            par[roots[q]] = keep;
+        }
+        par[v] = keep;
+    }
+    /* the global extremum of this kind gets the function range */
+    int32_t g = descending ? perm[n - 1] : perm[0];
+    pers[g] = range;
+    free(par); free(best);
+    return ORC_OK;
+}
+
+int orc_persistence(int ndim, const int64_t* dims, const float* f, const int32_t* O,
+                    double* pers_min, double* pers_max) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * G.n);
+    if (!perm) return ORC_ERR_OOM;
+    for (int64_t v = 0; v < G.n; ++v) perm[O[v]] = (int32_t)v;
+    st = persistence_one(&G, f, O, perm, 0, pers_min);
+    if (!st) st = persistence_one(&G, f, O, perm, 1, pers_max);
+    free(perm);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binary heap of (key, vertex), largest key first.                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { int64_t key; int32_t v; } hitem;
+typedef struct { hitem* a; int64_t n, cap; } heap_t;
+
+static int heap_push(heap_t* h, int64_t key, int32_t v) {
+    if (h->n == h->cap) {
+        int64_t nc = h->cap ? 2 * h->cap : 16;
+        hitem* na = (hitem*)realloc(h->a, sizeof(hitem) * nc);
+        if (!na) return ORC_ERR_OOM;
+        h->a = na; h->cap = nc;
+    }
+    int64_t i = h->n++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h->a[p].key >= key) break;
+        h->a[i] = h->a[p];
+        i = p;
+    }
+    h->a[i].key = key; h->a[i].v = v;
+    return ORC_OK;
+}
+
+static hitem heap_pop(heap_t* h) {
+    hitem top = h->a[0];
+    hitem last = h->a[--h->n];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        int64_t mk = last.key;
+        if (l < h->n && h->a[l].key > mk) { m = l; mk = h->a[l].key; }
+        if (r < h->n && h->a[r].key > mk) { m = r; }
+        if (m == i) break;
+        h->a[i] = h->a[m];
+        i = m;
+    }
+    if (h->n > 0) h->a[i] = last;
+    return top;
+}
+
+static void heap_free(heap_t* h) { free(h->a); h->a = NULL; h->n = h->cap = 0; }
+
+/* meld: every entry of src goes into dst; src is emptied */
+static int heap_meld(heap_t* dst, heap_t* src) {
+    for (int64_t i = 0; i < src->n; ++i) {
+        int st = heap_push(dst, src->a[i].key, src->a[i].v);
+        if (st) return st;
+    }
+    heap_free(src);
+    return ORC_OK;
+}
+
+/* small deterministic generator for the shuffled schedules (splitmix64) */
+static uint64_t sm64(uint64_t* s) {
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 1 with hill chains, method A: one superlevel set propagation per     */
+/* unauthorized maximum (Sec. 4.2 step 1, Sec. 4.3, Sec. 4.4).                */
+/*                                                                            */
+/* Everything works on an order field Od whose maxima are the extrema to     */
+/* treat: Od = O for the maxima pass, Od = N-1-O for the minima pass.         */
+/*                                                                            */
+/* Output (canonical): regions sorted by (Od(saddle), Od(top)); region_of[v]  */
+/* is the region of every member vertex (saddles excluded), -1 otherwise.     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const grid_t* G;
+    const int32_t* Od;
+    int32_t* owner;     /* class that first popped the vertex, or -1 */
+    int32_t* cnt;       /* higher neighbours whose class has not arrived; -1 = unset */
+    int32_t* wait_head; /* classes waiting at the vertex (linked list), -1 = none */
+    int32_t* wait_next;
+    int32_t* parent;    /* union-find over classes */
+    heap_t* heap;
+} flood_t;
+
+static int32_t cls_find(int32_t* p, int32_t a) {
+    while (p[a] != a) { p[a] = p[p[a]]; a = p[a]; }
+    return a;
+}
+
+static int push_lower_not_in(flood_t* F, int32_t v, int32_t c) {
+    int32_t nb[14];
+    int k = nbrs(F->G, v, nb);
+    for (int j = 0; j < k; ++j) {
+        int32_t u = nb[j];
+        if (F->Od[u] >= F->Od[v]) continue;
+        if (F->owner[u] >= 0 && cls_find(F->parent, F->owner[u]) == c) continue;
+        int st = heap_push(&F->heap[c], F->Od[u], u);
+        if (st) return st;
+    }
+    return ORC_OK;
+}
+
+/* Runs class *pc for at most `budget` pops (budget < 0: unlimited).
+ * Returns 0 when the class waits at a saddle (its task ends), 1 when the
+ * budget ran out (the task goes back to the queue), or an error. */
+static int flood_run(flood_t* F, int32_t* pc, int64_t budget) {
+    int32_t c = *pc;
+    for (;;) {
+        if (budget == 0) { *pc = c; return 1; }
+        if (budget > 0) --budget;
+        if (F->heap[c].n == 0) return -ORC_ERR_INTERNAL;
+        hitem it = heap_pop(&F->heap[c]);
+        int32_t v = it.v;
+        if (F->owner[v] >= 0 && cls_find(F->parent, F->owner[v]) == c) continue;
+        if (F->owner[v] < 0) F->owner[v] = c;
+        int32_t nb[14];
+        int kn = nbrs(F->G, v, nb);
+        int h = 0, k = 0;
+        for (int j = 0; j < kn; ++j) {
+            int32_t u = nb[j];
+            if (F->Od[u] <= F->Od[v]) continue;
+            ++h;
+            if (F->owner[u] >= 0 && cls_find(F->parent, F->owner[u]) == c) ++k;
+        }
+        if (k == h) {                       /* regular for this propagation */
+            int st = push_lower_not_in(F, v, c);
+            if (st) return -st;
+            continue;
+        }
+        /* arrival at the saddle v */
+        if (F->cnt[v] < 0) F->cnt[v] = h;
+        F->cnt[v] -= k;
+        F->wait_next[c] = F->wait_head[v];
+        F->wait_head[v] = c;
+        if (F->cnt[v] > 0) { *pc = c; return 0; }   /* a higher neighbour is still unvisited: stop */
+        /* last arrival: merge all propagations stopped here, meld their queues */
+        int32_t root = c;
+        for (int32_t w = F->wait_head[v]; w >= 0; w = F->wait_next[w]) {
+            if (w == root) continue;
+            int32_t a = cls_find(F->parent, w), b = cls_find(F->parent, root);
+            if (a == b) continue;
+            /* the class with the larger queue absorbs the other */
+            if (F->heap[a].n > F->heap[b].n) { int32_t t = a; a = b; b = t; }
+            int st = heap_meld(&F->heap[b], &F->heap[a]);
+            if (st) return -st;
+            F->parent[a] = b;
+            root = b;
+        }
+        F->wait_head[v] = -1;
+        c = cls_find(F->parent, root);
+        int st = push_lower_not_in(F, v, c);
+        if (st) return -st;
+    }
+}
+
+typedef struct { int32_t saddle, top; int64_t key_s, key_t; int32_t cls; } reg_t;
+
+static int cmp_reg(const void* pa, const void* pb) {
+    const reg_t* a = (const reg_t*)pa;
+    const reg_t* b = (const reg_t*)pb;
+    if (a->key_s != b->key_s) return a->key_s < b->key_s ? -1 : 1;
+    if (a->key_t != b->key_t) return a->key_t < b->key_t ? -1 : 1;
+    return 0;
+}
+
+static int auth_has_protected(const grid_t* G, const int32_t* Od, const uint8_t* auth,
+                              int64_t* n_unauth) {
+    int any = 0;
+    int64_t cntu = 0;
+    for (int64_t v = 0; v < G->n; ++v) {
+        int32_t nb[14];
+        int k = nbrs(G, v, nb), ismax = 1;
+        for (int j = 0; j < k; ++j) if (Od[nb[j]] > Od[v]) { ismax = 0; break; }
+        if (!ismax) continue;
+        if (auth[v]) any = 1; else ++cntu;
+    }
+    *n_unauth = cntu;
+    return any;
+}
+
+static int regions_flood(const grid_t* G, const int32_t* Od, const uint8_t* auth, uint64_t seed,
+                         int32_t* region_of, int32_t* reg_saddle, int32_t* reg_top, int64_t* nreg_out) {
+    int64_t n = G->n;
+    /* unauthorized maxima, by decreasing order */
+    int64_t nu = 0;
+    int32_t* U = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * n);
+    if (!U || !perm) { free(U); free(perm); return ORC_ERR_OOM; }
+    for (int64_t v = 0; v < n; ++v) perm[Od[v]] = (int32_t)v;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int32_t v = perm[i];
+        int32_t nb[14];
+        int k = nbrs(G, v, nb), ismax = 1;
+        for (int j = 0; j < k; ++j) if (Od[nb[j]] > Od[v]) { ismax = 0; break; }
+        if (ismax && !auth[v]) U[nu++] = v;
+    }
+    free(perm);
+    for (int64_t v = 0; v < n; ++v) region_of[v] = -1;
+    if (nu == 0) { free(U); *nreg_out = 0; return ORC_OK; }
+    int64_t dummy;
+    if (!auth_has_protected(G, Od, auth, &dummy)) { free(U); return ORC_ERR_NO_AUTHORIZED; }
+
+    flood_t F;
+    F.G = G; F.Od = Od;
+    F.owner = (int32_t*)malloc(sizeof(int32_t) * n);
+    F.cnt = (int32_t*)malloc(sizeof(int32_t) * n);
+    F.wait_head = (int32_t*)malloc(sizeof(int32_t) * n);
+    F.wait_next = (int32_t*)malloc(sizeof(int32_t) * nu);
+    F.parent = (int32_t*)malloc(sizeof(int32_t) * nu);
+    F.heap = (heap_t*)calloc((size_t)nu, sizeof(heap_t));
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (nu + 1));
+    int st = ORC_OK;
+    if (!F.owner || !F.cnt || !F.wait_head || !F.wait_next || !F.parent || !F.heap || !queue) {
+        st = ORC_ERR_OOM; goto done;
+    }
+    for (int64_t v = 0; v < n; ++v) { F.owner[v] = -1; F.cnt[v] = -1; F.wait_head[v] = -1; }
+    for (int64_t c = 0; c < nu; ++c) {
+        F.parent[c] = (int32_t)c; F.wait_next[c] = -1;
+        st = heap_push(&F.heap[c], Od[U[c]], U[c]);
+        if (st) goto done;
+    }
+    /* task queue: initially every class, in decreasing order of its maximum, or shuffled */
+    for (int64_t c = 0; c < nu; ++c) queue[c] = (int32_t)c;
+    uint64_t rs = seed;
+    if (seed) {
+        for (int64_t i = nu - 1; i > 0; --i) {
+            int64_t j = (int64_t)(sm64(&rs) % (uint64_t)(i + 1));
+            int32_t t = queue[i]; queue[i] = queue[j]; queue[j] = t;
+        }
+    }
+    /* circular task queue; with a seed each task runs for a random slice */
+    int64_t qh = 0, qn = nu, qcap = nu + 1;
+    int32_t* q2 = (int32_t*)malloc(sizeof(int32_t) * qcap);
+    if (!q2) { st = ORC_ERR_OOM; goto done; }
+    for (int64_t i = 0; i < nu; ++i) q2[i] = queue[i];
+    while (qn > 0) {
+        int32_t c = q2[qh]; qh = (qh + 1) % qcap; --qn;
+        int64_t budget = seed ? (int64_t)(1 + sm64(&rs) % 7) : -1;
+        int r = flood_run(&F, &c, budget);
+        if (r < 0) { st = -r; free(q2); goto done; }
+        if (r == 1) { q2[(qh + qn) % qcap] = c; ++qn; }
+    }
+    free(q2);
+
+    /* final stops: every class still waiting at a saddle gives one region */
+    {
+        reg_t* R = (reg_t*)malloc(sizeof(reg_t) * nu);
+        int32_t* cls2reg = (int32_t*)malloc(sizeof(int32_t) * nu);
+        int32_t* topv = (int32_t*)malloc(sizeof(int32_t) * nu);
+        if (!R || !cls2reg || !topv) { free(R); free(cls2reg); free(topv); st = ORC_ERR_OOM; goto done; }
+        for (int64_t c = 0; c < nu; ++c) { cls2reg[c] = -1; topv[c] = -1; }
+        /* top of each class: its highest member */
+        for (int64_t v = 0; v < n; ++v) {
+            if (F.owner[v] < 0 || F.wait_head[v] >= 0) continue;
+            int32_t c = cls_find(F.parent, F.owner[v]);
+            if (topv[c] < 0 || Od[v] > Od[topv[c]]) topv[c] = (int32_t)v;
+        }
+        int64_t nr = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            for (int32_t w = F.wait_head[v]; w >= 0; w = F.wait_next[w]) {
+                if (F.cnt[v] <= 0 || cls_find(F.parent, w) != w) { st = ORC_ERR_INTERNAL; break; }
+                R[nr].saddle = (int32_t)v; R[nr].top = topv[w]; R[nr].cls = w;
+                R[nr].key_s = Od[v]; R[nr].key_t = Od[topv[w]];
+                ++nr;
+            }
+        }
+        if (!st) {
+            qsort(R, (size_t)nr, sizeof(reg_t), cmp_reg);
+            for (int64_t r = 0; r < nr; ++r) {
+                cls2reg[R[r].cls] = (int32_t)r;
+                reg_saddle[r] = R[r].saddle; reg_top[r] = R[r].top;
+            }
+            for (int64_t v = 0; v < n; ++v) {
+                if (F.owner[v] < 0 || F.wait_head[v] >= 0) continue;
+                int32_t c = cls_find(F.parent, F.owner[v]);
+                if (cls2reg[c] < 0) { st = ORC_ERR_INTERNAL; break; }
+                region_of[v] = cls2reg[c];
+            }
+            *nreg_out = nr;
+        }
+        free(R); free(cls2reg); free(topv);
+    }
+
+done:
+    if (F.heap) for (int64_t c = 0; c < nu; ++c) heap_free(&F.heap[c]);
+    free(F.owner); free(F.cnt); free(F.wait_head); free(F.wait_next); free(F.parent);
+    free(F.heap); free(queue); free(U);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 1, method B: a global join-tree sweep (superlevel set components by  */
+/* decreasing order, union-find over vertices).  A component is protected    */
+/* when it holds an authorized maximum.  At a vertex whose higher neighbours */
+/* lie in several components, at least one protected, every unprotected one */
+/* D yields the region D + {v}.  Used to cross-check method A.               */
+/* ------------------------------------------------------------------------ */
+
+static int regions_jointree(const grid_t* G, const int32_t* Od, const uint8_t* auth,
+                            int32_t* region_of, int32_t* reg_saddle, int32_t* reg_top, int64_t* nreg_out) {
+    int64_t n = G->n;
+    int64_t* par = (int64_t*)malloc(sizeof(int64_t) * n);
+    uint8_t* prot = (uint8_t*)malloc(n);
+    int32_t* head = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* tail = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* next = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* top = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * n);
+    reg_t* R = NULL;
+    int64_t nr = 0, rcap = 0;
+    int st = ORC_OK;
+    if (!par || !prot || !head || !tail || !next || !top || !perm) { st = ORC_ERR_OOM; goto out; }
+    for (int64_t v = 0; v < n; ++v) { par[v] = -1; perm[Od[v]] = (int32_t)v; region_of[v] = -1; }
+    int64_t nunauth = 0;
+    int anyprot = auth_has_protected(G, Od, auth, &nunauth);
+    if (nunauth > 0 && !anyprot) { st = ORC_ERR_NO_AUTHORIZED; goto out; }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int32_t v = perm[i];
+        int32_t nb[14];
+        int k = nbrs(G, v, nb);
+        int64_t roots[14]; int nroot = 0;
+        for (int j = 0; j < k; ++j) {
+            if (Od[nb[j]] <= Od[v]) continue;
+            int64_t r = uf_find64(par, nb[j]);
+            int dup = 0;
+            for (int q = 0; q < nroot; ++q) if (roots[q] == r) dup = 1;
+            if (!dup) roots[nroot++] = r;
+        }
+        par[v] = v; head[v] = v; tail[v] = v; next[v] = -1; top[v] = v;
+        if (nroot == 0) { prot[v] = auth[v] ? 1 : 0; continue; }
+        int any = 0;
+        for (int q = 0; q < nroot; ++q) any |= prot[roots[q]];
+        if (nroot >= 2 && any) {
+            for (int q = 0; q < nroot; ++q) {
+                int64_t r = roots[q];
+                if (prot[r]) continue;
+                if (nr == rcap) {
+                    rcap = rcap ? 2 * rcap : 64;
+                    reg_t* nR = (reg_t*)realloc(R, sizeof(reg_t) * rcap);
+                    if (!nR) { st = ORC_ERR_OOM; goto out; }
+                    R = nR;
+                }
+                R[nr].saddle = v; R[nr].top = top[r]; R[nr].key_s = Od[v]; R[nr].key_t = Od[top[r]];
+                R[nr].cls = (int32_t)nr;
+                for (int32_t u = head[r]; u >= 0; u = next[u]) region_of[u] = (int32_t)nr;
+                ++nr;
+            }
+        }
+        /* merge every component and v; the merged component is protected if any part was */
+        int64_t keep = roots[0];
+        for (int q = 1; q < nroot; ++q) {
+            int64_t r = roots[q];
+            par[r] = keep;
+            next[tail[keep]] = head[r];
+            tail[keep] = tail[r];
+            if (Od[top[r]] > Od[top[keep]]) top[keep] = top[r];
+        }
+        par[v] = keep;
+        next[tail[keep]] = v; tail[keep] = v;
+        prot[keep] = (uint8_t)any;
+    }
+    /* canonical numbering */
+    if (nr > 0) {
+        int32_t* remap = (int32_t*)malloc(sizeof(int32_t) * nr);
+        if (!remap) { st = ORC_ERR_OOM; goto out; }
+        qsort(R, (size_t)nr, sizeof(reg_t), cmp_reg);
+        for (int64_t r = 0; r < nr; ++r) { remap[R[r].cls] = (int32_t)r; reg_saddle[r] = R[r].saddle; reg_top[r] = R[r].top; }
+        for (int64_t v = 0; v < n; ++v) if (region_of[v] >= 0) region_of[v] = remap[region_of[v]];
+        free(remap);
+    }
+    *nreg_out = nr;
+out:
+    free(par); free(prot); free(head); free(tail); free(next); free(top); free(perm); free(R);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 2 (Sec. 4.2, Eq. 3-5): local order of one region R with saddle s.    */
+/*   l0 = Od on R, l0(s) = +inf, l0(a) = -inf for the boundary-adjacent       */
+/*   vertex a != s of lowest order.  Then alternate                           */
+/*   - a superlevel set propagation from s (largest first); the inverse of   */
+/*     the visiting order is the new local order;                            */
+/*   - if some minimum of it has no neighbour outside R, a sublevel set      */
+/*     propagation from every vertex of R\{s} that has one (smallest first); */
+/*     the visiting order is the new local order;                            */
+/*   until only authorized extrema remain.  Propagations use only edges      */
+/*   inside R.  lhat gets values 0..|R|-1 with s at |R|-1.                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const grid_t* G;
+    const int32_t* Od;
+    int32_t* loc;   /* vertex -> local index in the current region, -1 elsewhere */
+} lo_ctx;
+
+/* Articulation points of the graph induced on R (Tarjan's lowpoint method,
+ * iterative depth-first search from `root`): is_cut[i] = 1 when removing
+ * vertex i disconnects the rest of R. */
+static int cut_vertices(const int32_t* adj, const int8_t* deg, int32_t r, int32_t root, uint8_t* is_cut) {
+    int32_t* disc = (int32_t*)malloc(sizeof(int32_t) * (size_t)r);
+    int32_t* low = (int32_t*)malloc(sizeof(int32_t) * (size_t)r);
+    int32_t* par = (int32_t*)malloc(sizeof(int32_t) * (size_t)r);
+    int8_t* it = (int8_t*)malloc((size_t)r);
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)r);
+    if (!disc || !low || !par || !it || !stack) {
+        free(disc); free(low); free(par); free(it); free(stack);
+        return ORC_ERR_OOM;
+    }
+    for (int32_t i = 0; i < r; ++i) { disc[i] = -1; is_cut[i] = 0; it[i] = 0; par[i] = -1; }
+    int32_t t = 0, sp = 0, root_children = 0;
+    disc[root] = low[root] = t++;
+    stack[sp++] = root;
+    while (sp > 0) {
+        int32_t u = stack[sp - 1];
+        if (it[u] < deg[u]) {
+            int32_t w = adj[14 * (size_t)u + it[u]++];
+            if (disc[w] < 0) {
+                par[w] = u;
+                disc[w] = low[w] = t++;
+                stack[sp++] = w;
+                if (u == root) ++root_children;
+            } else if (w != par[u] && disc[w] < low[u]) {
+                low[u] = disc[w];
+            }
+        } else {
+            --sp;
+            int32_t p = par[u];
+            if (p >= 0) {
+                if (low[u] < low[p]) low[p] = low[u];
+                if (p != root && low[u] >= disc[p]) is_cut[p] = 1;
+            }
+        }
+    }
+    if (root_children > 1) is_cut[root] = 1;
+    free(disc); free(low); free(par); free(it); free(stack);
+    return ORC_OK;
+}
+
+static int local_order_one(lo_ctx* C, const int32_t* verts, int32_t r, int32_t sidx,
+                           int32_t* lhat_local, int32_t* floods_out) {
+    int st = ORC_OK;
+    int32_t* adj = (int32_t*)malloc(sizeof(int32_t) * 14 * (size_t)r);
+    int8_t* deg = (int8_t*)malloc((size_t)r);
+    uint8_t* bnd = (uint8_t*)malloc((size_t)r);
+    int64_t* L = (int64_t*)malloc(sizeof(int64_t) * (size_t)r);
+    int64_t* L2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)r);
+    uint8_t* vis = (uint8_t*)malloc((size_t)r);
+    heap_t H = {0, 0, 0};
+    if (!adj || !deg || !bnd || !L || !L2 || !vis) { st = ORC_ERR_OOM; goto out; }
+    for (int32_t i = 0; i < r; ++i) {
+        int32_t nb[14];
+        int k = nbrs(C->G, verts[i], nb);
+        deg[i] = 0; bnd[i] = 0;
+        for (int j = 0; j < k; ++j) {
+            int32_t li = C->loc[nb[j]];
+            if (li < 0) bnd[i] = 1; else adj[14 * (size_t)i + deg[i]++] = li;
+        }
+    }
+    /* l0.  The vertex set to minus infinity must be visited last by the
+     * first superlevel set propagation from s, otherwise it does not end up
+     * as a minimum and no authorized minimum is left; this holds exactly when
+     * its removal leaves R connected.  Such a boundary-adjacent vertex always
+     * exists because the grid graph is 2-connected. */
+    if ((st = cut_vertices(adj, deg, r, sidx, vis))) goto out;
+    int32_t a = -1;
+    for (int32_t i = 0; i < r; ++i) {
+        L[i] = C->Od[verts[i]];
+        if (i != sidx && bnd[i] && !vis[i] && (a < 0 || C->Od[verts[i]] < C->Od[verts[a]])) a = i;
+    }
+    if (a < 0) { st = ORC_ERR_INTERNAL; goto out; }
+    L[sidx] = INT64_MAX;
+    L[a] = INT64_MIN;
+
+    int32_t floods = 0;
+    int64_t cap = 2 * (int64_t)r + 2;
+    for (;;) {
+        /* superlevel set propagation from s */
+        if (++floods > cap) { st = ORC_ERR_INTERNAL; goto out; }
+        memset(vis, 0, (size_t)r);
+        H.n = 0;
+        if ((st = heap_push(&H, L[sidx], sidx))) goto out;
+        int64_t i = 0;
+        while (H.n > 0) {
+            hitem it = heap_pop(&H);
+            if (vis[it.v]) continue;
+            vis[it.v] = 1;
+            L2[it.v] = (int64_t)r - 1 - i;
+            ++i;
+            for (int j = 0; j < deg[it.v]; ++j) {
+                int32_t u = adj[14 * (size_t)it.v + j];
+                if (!vis[u] && (st = heap_push(&H, L[u], u))) goto out;
+            }
+        }
+        if (i != r) { st = ORC_ERR_INTERNAL; goto out; }
+        memcpy(L, L2, sizeof(int64_t) * (size_t)r);
+        /* unauthorized minima: minima of L on R without a neighbour outside R */
+        int bad = 0;
+        for (int32_t u = 0; u < r && !bad; ++u) {
+            if (bnd[u] || u == a) continue;
+            int ismin = 1;
+            for (int j = 0; j < deg[u]; ++j) if (L[adj[14 * (size_t)u + j]] < L[u]) { ismin = 0; break; }
+            if (ismin) bad = 1;
+        }
+        if (!bad) break;
+
+        /* sublevel set propagation from every vertex allowed to be a minimum:
+         * all vertices of R other than s with a neighbour outside R */
+        if (++floods > cap) { st = ORC_ERR_INTERNAL; goto out; }
+        memset(vis, 0, (size_t)r);
+        H.n = 0;
+        for (int32_t u = 0; u < r; ++u) {
+            if (u == sidx || !bnd[u]) continue;
+            if ((st = heap_push(&H, -L[u], u))) goto out;
+        }
+        i = 0;
+        while (H.n > 0) {
+            hitem it = heap_pop(&H);
+            if (vis[it.v]) continue;
+            vis[it.v] = 1;
+            L2[it.v] = i;
+            ++i;
+            for (int j = 0; j < deg[it.v]; ++j) {
+                int32_t u = adj[14 * (size_t)it.v + j];
+                if (!vis[u] && (st = heap_push(&H, -L[u], u))) goto out;
+            }
+        }
+        if (i != r) { st = ORC_ERR_INTERNAL; goto out; }
+        memcpy(L, L2, sizeof(int64_t) * (size_t)r);
+        /* unauthorized maxima: maxima of L on R other than s */
+        bad = 0;
+        for (int32_t u = 0; u < r && !bad; ++u) {
+            if (u == sidx) continue;
+            int ismax = 1;
+            for (int j = 0; j < deg[u]; ++j) if (L[adj[14 * (size_t)u + j]] > L[u]) { ismax = 0; break; }
+            if (ismax) bad = 1;
+        }
+        if (!bad) break;
+    }
+    for (int32_t u = 0; u < r; ++u) lhat_local[u] = (int32_t)L[u];
+    *floods_out = floods;
+out:
+    free(adj); free(deg); free(bnd); free(L); free(L2); free(vis); heap_free(&H);
+    return st;
+}
+
+/* Local orders of all regions.  lhat[v] for every member v (saddles keep -1). */
+static int local_orders(const grid_t* G, const int32_t* Od, const int32_t* region_of,
+                        const int32_t* reg_saddle, int64_t nreg, int32_t* lhat, int32_t* reg_floods) {
+    int64_t n = G->n;
+    int st = ORC_OK;
+    int64_t* start = (int64_t*)calloc((size_t)nreg + 1, sizeof(int64_t));
+    int32_t* members = NULL;
+    int32_t* loc = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* verts = NULL;
+    int32_t* ll = NULL;
+    if (!start || !loc) { st = ORC_ERR_OOM; goto out; }
+    for (int64_t v = 0; v < n; ++v) { loc[v] = -1; lhat[v] = -1; }
+    for (int64_t v = 0; v < n; ++v) if (region_of[v] >= 0) start[region_of[v] + 1]++;
+    for (int64_t r = 0; r < nreg; ++r) start[r + 1] += start[r];
+    members = (int32_t*)malloc(sizeof(int32_t) * (start[nreg] + 1));
+    if (!members) { st = ORC_ERR_OOM; goto out; }
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nreg + 1));
+        if (!fill) { st = ORC_ERR_OOM; goto out; }
+        memcpy(fill, start, sizeof(int64_t) * ((size_t)nreg + 1));
+        for (int64_t v = 0; v < n; ++v) if (region_of[v] >= 0) members[fill[region_of[v]]++] = (int32_t)v;
+        free(fill);
+    }
+    int64_t maxr = 0;
+    for (int64_t r = 0; r < nreg; ++r) if (start[r + 1] - start[r] > maxr) maxr = start[r + 1] - start[r];
+    verts = (int32_t*)malloc(sizeof(int32_t) * (maxr + 1));
+    ll = (int32_t*)malloc(sizeof(int32_t) * (maxr + 1));
+    if (!verts || !ll) { st = ORC_ERR_OOM; goto out; }
+    lo_ctx C; C.G = G; C.Od = Od; C.loc = loc;
+    for (int64_t r = 0; r < nreg; ++r) {
+        int32_t m = (int32_t)(start[r + 1] - start[r]);
+        for (int32_t i = 0; i < m; ++i) { verts[i] = members[start[r] + i]; loc[verts[i]] = i; }
+        verts[m] = reg_saddle[r];
+        loc[reg_saddle[r]] = m;
+        int32_t fl = 0;
+        st = local_order_one(&C, verts, m + 1, m, ll, &fl);
+        for (int32_t i = 0; i <= m; ++i) loc[verts[i]] = -1;
+        if (st) goto out;
+        for (int32_t i = 0; i < m; ++i) lhat[verts[i]] = ll[i];
+        reg_floods[r] = fl;
+    }
+out:
+    free(start); free(members); free(loc); free(verts); free(ll);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 3 (Sec. 4.2, Eq. 6): new global order.  Sort key                     */
+/*   non-member u (saddles included): (Od(u), 1, 0, 0)                        */
+/*   member v of region R:            (Od(s_R), 0, Od(top_R), lhat(v))        */
+/* so every region forms a contiguous block right before its saddle, sibling */
+/* blocks of one saddle ordered by their highest vertex.                     */
+/* Step 4 (zeta = 0): g(v) = g(s_R) for members.                             */
+/* ------------------------------------------------------------------------ */
+
+static const int32_t* s_k_od;
+static const int32_t* s_k_reg;
+static const int32_t* s_k_sad;
+static const int32_t* s_k_top;
+static const int32_t* s_k_lhat;
+
+static void key_of(int32_t v, int64_t* k) {
+    int32_t r = s_k_reg[v];
+    if (r < 0) { k[0] = s_k_od[v]; k[1] = 1; k[2] = 0; k[3] = 0; }
+    else { k[0] = s_k_od[s_k_sad[r]]; k[1] = 0; k[2] = s_k_od[s_k_top[r]]; k[3] = s_k_lhat[v]; }
+}
+
+static int cmp_pair_order(const void* pa, const void* pb) {
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    int64_t ka[4], kb[4];
+    key_of(a, ka); key_of(b, kb);
+    for (int i = 0; i < 4; ++i) if (ka[i] != kb[i]) return ka[i] < kb[i] ? -1 : 1;
+    return 0;
+}
+
+static int apply_pass(const grid_t* G, const int32_t* Od, const int32_t* region_of,
+                      const int32_t* reg_saddle, const int32_t* reg_top, const int32_t* lhat,
+                      int32_t* Od_out, const float* g_in, float* g_out) {
+    int64_t n = G->n;
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * n);
+    if (!idx) return ORC_ERR_OOM;
+    for (int64_t v = 0; v < n; ++v) idx[v] = (int32_t)v;
+    s_k_od = Od; s_k_reg = region_of; s_k_sad = reg_saddle; s_k_top = reg_top; s_k_lhat = lhat;
+    qsort(idx, (size_t)n, sizeof(int32_t), cmp_pair_order);
+    for (int64_t i = 0; i < n; ++i) Od_out[idx[i]] = (int32_t)i;
+    free(idx);
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t r = region_of[v];
+        g_out[v] = (r < 0) ? g_in[v] : g_in[reg_saddle[r]];
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public stage entry points (all on the pass-oriented order Od).            */
+/* ------------------------------------------------------------------------ */
+
+int orc_regions(int ndim, const int64_t* dims, const int32_t* Od, const uint8_t* auth, int method,
+                uint64_t seed, int32_t* region_of, int32_t* reg_saddle, int32_t* reg_top, int64_t* nreg) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    if (method == 0) return regions_flood(&G, Od, auth, seed, region_of, reg_saddle, reg_top, nreg);
+    return regions_jointree(&G, Od, auth, region_of, reg_saddle, reg_top, nreg);
+}
+
+int orc_local_orders(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* region_of,
+                     const int32_t* reg_saddle, int64_t nreg, int32_t* lhat, int32_t* reg_floods) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    return local_orders(&G, Od, region_of, reg_saddle, nreg, lhat, reg_floods);
+}
+
+int orc_apply(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* region_of,
+              const int32_t* reg_saddle, const int32_t* reg_top, const int32_t* lhat,
+              const float* g_in, int32_t* Od_out, float* g_out) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    return apply_pass(&G, Od, region_of, reg_saddle, reg_top, lhat, Od_out, g_in, g_out);
+}
+
+/* One pass on (g, O).  dir = +1: maxima pass; dir = -1: minima pass, run as a
+ * maxima pass on the mirrored order N-1-O and mirrored back (Sec. 4:
+ * minima are processed symmetrically). */
+static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, uint64_t seed,
+                    float* g, int32_t* O, orc_stats* S) {
+    int64_t n = G->n;
+    int st = ORC_OK;
+    int32_t* Od = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* region_of = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* reg_saddle = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* reg_top = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* lhat = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* reg_floods = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* Od2 = (int32_t*)malloc(sizeof(int32_t) * n);
+    float* g2 = (float*)malloc(sizeof(float) * n);
+    int64_t nreg = 0;
+    int side = dir > 0 ? 1 : 0;
+    if (!Od || !region_of || !reg_saddle || !reg_top || !lhat || !reg_floods || !Od2 || !g2) {
+        st = ORC_ERR_OOM; goto out;
+    }
+    for (int64_t v = 0; v < n; ++v) Od[v] = dir > 0 ? O[v] : (int32_t)(n - 1 - O[v]);
+    {
+        int64_t nun = 0;
+        auth_has_protected(G, Od, auth, &nun);
+        if (S) S->removed[side] = nun;
+    }
+    st = method == 0 ? regions_flood(G, Od, auth, seed, region_of, reg_saddle, reg_top, &nreg)
+                     : regions_jointree(G, Od, auth, region_of, reg_saddle, reg_top, &nreg);
+    if (st) goto out;
+    st = local_orders(G, Od, region_of, reg_saddle, nreg, lhat, reg_floods);
+    if (st) goto out;
+    st = apply_pass(G, Od, region_of, reg_saddle, reg_top, lhat, Od2, g, g2);
+    if (st) goto out;
+    for (int64_t v = 0; v < n; ++v) {
+        O[v] = dir > 0 ? Od2[v] : (int32_t)(n - 1 - Od2[v]);
+        g[v] = g2[v];
+    }
+    if (S) {
+        int64_t mem = 0, maxr = 0;
+        int32_t mf = 0; int64_t tf = 0;
+        int64_t* sz = (int64_t*)calloc((size_t)nreg + 1, sizeof(int64_t));
+        if (!sz) { st = ORC_ERR_OOM; goto out; }
+        for (int64_t v = 0; v < n; ++v) if (region_of[v] >= 0) { ++mem; ++sz[region_of[v]]; }
+        for (int64_t r = 0; r < nreg; ++r) {
+            if (sz[r] > maxr) maxr = sz[r];
+            if (reg_floods[r] > mf) mf = reg_floods[r];
+            tf += reg_floods[r];
+        }
+        free(sz);
+        S->regions[side] = nreg; S->region_vertices[side] = mem; S->max_region[side] = maxr;
+        S->max_local_floods[side] = mf; S->total_local_floods[side] = tf;
+    }
+out:
+    free(Od); free(region_of); free(reg_saddle); free(reg_top); free(lhat); free(reg_floods);
+    free(Od2); free(g2);
+    return st;
+}
+
+/* Full LTS: O = order field of f, g = f; then the minima pass and/or the
+ * maxima pass.  auth_ids lists the authorized extrema (minima and maxima
+ * together; an id that is not an extremum of a pass's kind is ignored by
+ * that pass; duplicates are allowed). */
+int orc_lts(int ndim, const int64_t* dims, const float* f, const int32_t* auth_ids, int64_t n_auth,
+            int mode, float* g, int32_t* O, orc_stats* S, int method, uint64_t seed) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    if (mode < ORC_MODE_MIN || mode > ORC_MODE_BOTH) return ORC_ERR_ARG;
+    if (n_auth < 0 || (n_auth > 0 && !auth_ids)) return ORC_ERR_ARG;
+    for (int64_t i = 0; i < n_auth; ++i)
+        if (auth_ids[i] < 0 || auth_ids[i] >= G.n) return ORC_ERR_ARG;
+    if (S) { memset(S, 0, sizeof *S); S->n_vertices = G.n; }
+    st = orc_order_field(ndim, dims, f, O);
+    if (st) return st;
+    uint8_t* auth = (uint8_t*)calloc((size_t)G.n, 1);
+    if (!auth) return ORC_ERR_OOM;
+    for (int64_t i = 0; i < n_auth; ++i) auth[auth_ids[i]] = 1;
+    memcpy(g, f, sizeof(float) * G.n);
+    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, method, seed, g, O, S);
+    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, method, seed, g, O, S);
+    free(auth);
+    return st;
+}
+
+/* One pass on a given (g, O), for stage-wise checks. */
+int orc_pass(int ndim, const int64_t* dims, int dir, const int32_t* auth_ids, int64_t n_auth,
+             float* g, int32_t* O, orc_stats* S, int method, uint64_t seed) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    uint8_t* auth = (uint8_t*)calloc((size_t)G.n, 1);
+    if (!auth) return ORC_ERR_OOM;
+    for (int64_t i = 0; i < n_auth; ++i) {
+        if (auth_ids[i] < 0 || auth_ids[i] >= G.n) { free(auth); return ORC_ERR_ARG; }
+        auth[auth_ids[i]] = 1;
+    }
+    if (S) { memset(S, 0, sizeof *S); S->n_vertices = G.n; }
+    st = one_pass(&G, dir, auth, method, seed, g, O, S);
+    free(auth);
+    return st;
+}
