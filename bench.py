@@ -1,0 +1,314 @@
+"""Benchmark of the LTS hot path on GB300 (one JSON line on stdout).
+
+Workload (default): the 512^3 box-noise field (white noise box-filtered with
+radius 2, quantized to 1024 levels, 134,217,728 vertices), authorized extrema
+= persistence above 10% of the range (stored list), mode both (minima pass,
+then maxima pass).  A step is one full lts_simplify call: order field,
+classification, propagations, local orders, reorder and flatten, for both
+passes.  Inputs are 512 MB, larger than L2, so no flush is needed between
+steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (launched by torchrun) every rank simplifies its own replica of
+the field (no collective on the data path: a single field does not shard);
+the value is the vertices of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2009_00083_gb300 import workloads as W  # noqa: E402
+
+METRIC = "LTS Mvertices/s (bit-exact vs oracle), batched vs plain per-field; serve p50/p99"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per vertex of each stage of one call in mode both
+# (every array touched once at its minimal width):
+#   order field: read f (4) + copy to g (4) + a 32-bit LSD sort with 11-bit
+#     digits: 3 passes x (read 8 + write 8) + rank write (4) + keep (4)
+#   classify:    read the order field once per pass (2 x 4)
+#   reorder:     read + write the order field per pass (2 x 8)
+BYTES_PER_VERTEX = {"order_field": 4 + 4 + 48 + 8, "classify": 8, "reorder": 16}
+PATH_BYTES_PER_VERTEX = 100   # sort + classify + flatten, both passes
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="lts", choices=["lts", "reference"])
+    p.add_argument("--workload", default="boxnoise3d_512")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def load_workload(name):
+    from tests.golden import make_golden as mg
+
+    rec = mg.load_record(name)
+    ids = mg.load_authorized(name)
+    f = W.make_config_field(rec["config"], shape=tuple(rec["shape"]))
+    if W.sha256_of(f) != rec["field_sha256"]:
+        raise RuntimeError("generated field does not match the stored hash")
+    return rec, f, ids
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sample_side=160):
+    """The oracle, as it stands, single-threaded on the host: same recipe on a
+    bounded sample (a sample_side^3 field), authorized list precomputed, mode
+    both, wall clock of the whole method (order field included)."""
+    import oracle
+
+    f = W.make_config_field(2, shape=(sample_side,) * 3)
+    ids = oracle.authorized_by_persistence(f, W.CONFIGS[2]["thr"])
+    t = time.perf_counter()
+    oracle.lts(f, ids, mode="both")
+    dt = time.perf_counter() - t
+    return {"value": round(f.size / dt / 1e6, 3), "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
+            "sample": f"box-noise recipe at {sample_side}^3 ({f.size} vertices), mode both, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle on the host, on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    side = 128
+    f = W.make_config_field(2, shape=(side,) * 3)
+    ids = oracle.authorized_by_persistence(f, W.CONFIGS[2]["thr"])
+    for _ in range(args.warmup):
+        oracle.lts(f, ids, mode="both")
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.lts(f, ids, mode="both")
+    dt = (time.perf_counter() - t) / max(1, args.steps)
+    value = f.size / dt / 1e6
+    sample = f"box-noise recipe at {side}^3 ({f.size} vertices) per step, mode both, single-threaded oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mvertices/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": args.workload, "reference_sample": f"{side}^3"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "Mvertices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2009_00083_gb300 as lts
+
+    rec, f, ids = load_workload(args.workload)
+    n = f.size
+    stream = torch.cuda.current_stream(dev)
+    ctx = lts.Context(n, device=local, stream=stream)
+    fd = torch.from_numpy(f).to(dev)
+    idd = torch.from_numpy(ids).to(dev)
+    g = torch.empty_like(fd)
+    o = torch.empty(f.shape, dtype=torch.int32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        ctx.simplify(fd, idd, "both", out_field=g, out_order=o, with_stats=False)
+    # parity of the timed configuration against the stored oracle hashes
+    _, _, st = ctx.simplify(fd, idd, "both", out_field=g, out_order=o, with_stats=True)
+    torch.cuda.synchronize(dev)
+    parity = (W.sha256_of(o.cpu().numpy()) == rec["order_sha256"]
+              and W.sha256_of(g.cpu().numpy()) == rec["g_sha256"])
+
+    stage_us = {k: 0.0 for k in st["stage_us"]}
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, _, s = ctx.simplify(fd, idd, "both", out_field=g, out_order=o, with_stats=True)
+            for k, v in s["stage_us"].items():
+                stage_us[k] += v
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stage_us = {k: v / args.steps for k, v in stage_us.items()}
+    value = world * n / (ms / 1e3) / 1e6
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(f).pin_memory()
+        ih = torch.from_numpy(ids).pin_memory()
+        gh = torch.empty(f.shape, dtype=torch.float32).pin_memory()
+        oh = torch.empty(f.shape, dtype=torch.int32).pin_memory()
+        fd2 = torch.empty_like(fd)
+        id2 = torch.empty_like(idd)
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                barrier()
+                e0.record(stream)
+            fd2.copy_(fh, non_blocking=True)
+            id2.copy_(ih, non_blocking=True)
+            ctx.simplify(fd2, id2, "both", out_field=g, out_order=o, with_stats=False)
+            gh.copy_(g, non_blocking=True)
+            oh.copy_(o, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / args.steps
+        if dist is not None:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": round(world * n / (ms_e2e / 1e3) / 1e6, 3), "unit": "Mvertices/s",
+               "h2d_bytes_per_step": int(f.nbytes + ids.nbytes), "d2h_bytes_per_step": int(2 * f.nbytes),
+               "ms_per_step": round(ms_e2e, 3)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peak, kind = peaks()
+    # dominant stage by device time, and its algorithmic bytes
+    dom = max(BYTES_PER_VERTEX, key=lambda k: stage_us.get(k, 0.0))
+    dom_us = stage_us[dom]
+    achieved = BYTES_PER_VERTEX[dom] * n / (dom_us * 1e-6) / 1e9
+    path_achieved = PATH_BYTES_PER_VERTEX * n / (ms * 1e-3) / 1e9
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mvertices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": args.workload, "shape": list(f.shape), "vertices": n,
+                   "authorized": int(ids.size), "mode": "both", "l2": "inputs (512 MB) larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "parity_vs_oracle": bool(parity),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_kind": kind, "bytes_per_vertex": BYTES_PER_VERTEX[dom]},
+        "path_roofline": {"bytes_per_vertex": PATH_BYTES_PER_VERTEX, "achieved": round(path_achieved, 1),
+                          "peak": peak, "unit": "GB/s", "frac": round(path_achieved / peak, 4)},
+        "stage_us": {k: round(v, 1) for k, v in stage_us.items()},
+        "stats": {k: st[k] for k in ("removed", "regions", "region_vertices", "max_region",
+                                     "max_local_floods", "heap_spills")},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": int(st.get("launches", 0)) * args.steps,
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

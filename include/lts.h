@@ -1,0 +1,126 @@
+/*
+ * lts.h - C ABI of the GB300 library for Localized Topological Simplification
+ * (LTS) of scalar fields on Freudenthal-triangulated 2D and 3D regular grids.
+ *
+ * The method (Lukasczyk, Garth, Maciejewski, Tierny): given a scalar field f
+ * and a list of authorized extrema, compute the order field (Sec. 4.1), find
+ * the unauthorized extrema, flood a region from each one up to its first
+ * saddle, merging floods that collide (Sec. 4.2 step 1, Sec. 4.3, Sec. 4.4),
+ * give every region a local order with only authorized extrema (Sec. 4.2
+ * step 2, Eq. 3-5), splice the regions into the global order right before
+ * their saddle (Sec. 4.2 step 3, Eq. 6) and flatten their values to the
+ * saddle's value (Sec. 4.2 step 4 with zeta = 0).  Minima are processed
+ * first, then maxima (Sec. 4: minima are handled symmetrically).
+ *
+ * Conventions for every entry point
+ *   - A grid has dims (X, Y, Z) with Z = 1 in 2D; vertex (x, y, z) has id
+ *     x + X*(y + Y*z), i.e. x varies fastest.  Every dim must be >= 2
+ *     (except Z = 1 in 2D) and X*Y*Z must be < 2^31.
+ *   - Neighbours (Freudenthal / Kuhn triangulation): every vertex whose
+ *     offset lies in {0,1}^d or -{0,1}^d, 6 in 2D and 14 in 3D; neighbours
+ *     outside the grid are dropped.
+ *   - Ties in f are broken by vertex id; -0.0 equals +0.0; a NaN is an error.
+ *   - Data pointers marked d_ are DEVICE pointers owned by the caller; the
+ *     library never frees or keeps them past the call.  A context owns only
+ *     its device workspace.
+ *   - Work is enqueued on the context's CUDA stream.  Calls on one context
+ *     must not run concurrently (the context is not thread-safe); separate
+ *     contexts are independent.
+ *   - Errors are returned as lts_status codes; nothing aborts or throws
+ *     across this boundary.  lts_last_error() gives a message.
+ */
+#ifndef LTS_H
+#define LTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lts_ctx lts_ctx;
+
+typedef enum {
+    LTS_OK = 0,
+    LTS_ERR_ARG = 1,            /* bad dims, sizes, pointers, aliasing, ids out of range */
+    LTS_ERR_NAN = 2,            /* the field holds a NaN                                */
+    LTS_ERR_NO_AUTHORIZED = 3,  /* a pass has unauthorized extrema but no authorized    */
+                                /* extremum of its kind: its floods could never stop    */
+    LTS_ERR_OOM = 4,            /* workspace allocation failed or a pool was exhausted  */
+    LTS_ERR_CUDA = 5,           /* a CUDA runtime call failed                           */
+    LTS_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired                   */
+    LTS_ERR_INTERNAL = 7        /* an internal consistency check failed                 */
+} lts_status;
+
+typedef enum {
+    LTS_MODE_MIN = 1,           /* minima pass only                 */
+    LTS_MODE_MAX = 2,           /* maxima pass only                 */
+    LTS_MODE_BOTH = 3           /* minima pass, then maxima pass    */
+} lts_mode;
+
+typedef struct {
+    int32_t ndim;               /* 2 or 3                            */
+    int64_t dims[3];            /* X, Y, Z (Z = 1 when ndim == 2)    */
+} lts_grid;
+
+/* Per-call statistics ([0] = minima pass, [1] = maxima pass). */
+typedef struct {
+    int64_t n_vertices;
+    int64_t removed[2];          /* unauthorized extrema flooded                    */
+    int64_t regions[2];          /* regions (one per hill chain)                    */
+    int64_t region_vertices[2];  /* vertices moved (region members, saddles apart)  */
+    int64_t max_region[2];       /* members of the largest region                   */
+    int32_t max_local_floods[2]; /* most propagations one region needed in step 2   */
+    int64_t total_local_floods[2];
+    int64_t heap_spills[2];      /* floods whose priority queue left shared memory  */
+    float stage_us[8];           /* device time per stage: order field, classify,   */
+                                 /* propagation, regions, local order, reorder      */
+                                 /* (summed over passes); [6] total; [7] unused     */
+    int64_t kernel_launches;     /* CUDA kernels this call launched                 */
+} lts_stats;
+
+/* Creates a context on CUDA device `device` whose workspace fits grids of up
+ * to `max_vertices` vertices.  `cuda_stream` is a cudaStream_t (NULL: the
+ * legacy default stream) on which all work of the context is enqueued.
+ * On success *out receives the context.
+ * Errors: LTS_ERR_ARG (out NULL, max_vertices < 4 or >= 2^31),
+ *         LTS_ERR_CUDA (device), LTS_ERR_OOM (workspace allocation). */
+lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cuda_stream);
+
+/* Device workspace bytes a context needs for grid g (0 if g is invalid);
+ * for admission control before lts_create. */
+size_t lts_workspace_bytes(const lts_grid* g);
+
+/* Simplifies one field.
+ *   g              grid (see conventions); N = X*Y*Z <= the context's max_vertices
+ *   d_field        device float32[N], the input f (not modified)
+ *   d_authorized   device int32[n_authorized]: ids of authorized extrema, minima
+ *                  and maxima together; an id that is not an extremum of a
+ *                  pass's kind is ignored by that pass; duplicates allowed.
+ *                  May be NULL when n_authorized == 0.
+ *   mode           LTS_MODE_MIN / MAX / BOTH
+ *   d_out_field    device float32[N]: g, the simplified field (step 4, zeta = 0:
+ *                  every moved vertex takes its saddle's value bit for bit)
+ *   d_out_order    device int32[N]: the new order field (a permutation of 0..N-1)
+ *   opt_stats      if non-NULL, filled after the call completes.
+ * The outputs must not overlap the input or each other (LTS_ERR_ARG).
+ * The call enqueues its kernels and then waits for them (one small read of
+ * the status word), so on return the outputs are final and the status holds
+ * any device-side error (NaN, no authorized extremum, timeout, pool overflow).
+ * Authorized ids outside [0, N) give LTS_ERR_ARG (detected on the device). */
+lts_status lts_simplify(lts_ctx* ctx, const lts_grid* g, const float* d_field,
+                        const int32_t* d_authorized, int64_t n_authorized, lts_mode mode,
+                        float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats);
+
+/* Message describing the last error on this context ("" if none). */
+const char* lts_last_error(const lts_ctx* ctx);
+
+/* Frees the context and its workspace; NULL is ignored. */
+void lts_destroy(lts_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LTS_H */

@@ -1,0 +1,152 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lts.h"
+
+namespace lts {
+
+// ---------------------------------------------------------------------------
+// Grid geometry: Freudenthal neighbours are the offsets in {0,1}^d and
+// -{0,1}^d.  Offset k < nn/2 is the k+1-th non-zero 0/1 vector (bit b = axis b)
+// and offset k + nn/2 its negative.
+// ---------------------------------------------------------------------------
+struct Geom {
+    int ndim;
+    int nn;            // 6 or 14
+    int X, Y, Z;       // Z = 1 in 2D
+    int n;             // X*Y*Z
+    int XY;
+};
+
+// Neighbour k of (x,y,z): returns its id, or -1 outside the grid.
+__device__ __forceinline__ int nbr_of(const Geom& g, int x, int y, int z, int k) {
+    const int half = g.nn >> 1;
+    const int m = (k < half ? k : k - half) + 1;
+    const int s = k < half ? 1 : -1;
+    const int dx = (m & 1) * s, dy = ((m >> 1) & 1) * s, dz = ((m >> 2) & 1) * s;
+    const int a = x + dx, b = y + dy, c = z + dz;
+    if ((unsigned)a >= (unsigned)g.X || (unsigned)b >= (unsigned)g.Y || (unsigned)c >= (unsigned)g.Z) return -1;
+    return a + g.X * b + g.XY * c;
+}
+
+__device__ __forceinline__ void coords_of(const Geom& g, int v, int& x, int& y, int& z) {
+    z = v / g.XY;
+    int r = v - z * g.XY;
+    y = r / g.X;
+    x = r - y * g.X;
+}
+
+// Pass-oriented order: the maxima pass works on O, the minima pass on N-1-O,
+// so that every pass treats maxima.
+template <int DIR>
+__device__ __forceinline__ int od(int o, int n) { return DIR > 0 ? o : n - 1 - o; }
+
+// ---------------------------------------------------------------------------
+// Device status word: the first error wins.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+__device__ __forceinline__ bool failed(const int* st) { return *(volatile const int*)st != 0; }
+
+// Bounded spin budget for every device-side wait on another block.
+constexpr long long kSpinLimit = 1LL << 26;
+
+// Scalars produced and consumed on the device, read back once per call.
+struct DevCounters {
+    int status;
+    int n_unauth;          // |U| of the current pass
+    int n_auth_ext;        // authorized extrema present in the current pass
+    int n_regions;
+    int n_saddles;         // distinct saddles (head regions)
+    int log_cursor;        // visited-vertex log length (chunk reserved)
+    int seed_cursor;
+    int spill_cursor;
+    long long heap_cursor; // lane heap pool (entries)
+    int max_region;
+    int max_floods;
+    long long region_vertices;
+    long long total_floods;
+    int heap_spills;
+    int pad;
+};
+
+// Per-pass statistics accumulated into the host stats.
+struct PassStats {
+    long long removed, regions, region_vertices, max_region, max_floods, total_floods, heap_spills;
+};
+
+// Rank-space block (64 ranks): members and saddles present, and prefix counts.
+struct RankBlk {
+    unsigned long long mmask;
+    unsigned long long smask;
+    unsigned int mpre;
+    unsigned int spre;
+};
+
+// ---------------------------------------------------------------------------
+// Workspace (all device memory, sized for max_vertices).
+// ---------------------------------------------------------------------------
+struct Work {
+    int nmax;
+    int max_tiles;
+    // order field (radix sort)
+    unsigned int* keyA; unsigned int* valA; unsigned int* keyB; unsigned int* valB;
+    unsigned long long* sort_status;     // tiles x 256 look-back words
+    unsigned int* sort_hist;             // 4 x 256
+    unsigned int* sort_offsets;          // 4 x 256
+    unsigned int* tile_counter;          // 4
+    unsigned int epoch;
+    // authorized bitmap
+    unsigned int* authbits;              // ceil(n/32)
+    // propagation
+    int* owner;                          // per vertex: class, region tag, or -1
+    int* loc;                            // per vertex: local index within its region
+    int* U;                              // unauthorized extrema
+    int* parent; int* wait_v; int* cnt; int* listhead; int* next_w;
+    int* spill_base; int* spill_n;
+    int* spill_pool; long long spill_cap;
+    unsigned long long* heap_pool; long long heap_cap;
+    int* vlog; long long log_cap;
+    // regions
+    int* class2reg; int* reg_class; int* reg_saddle; int* reg_size; int* reg_start;
+    int* reg_top; int* reg_sod; int* reg_place; int* reg_head; int* reg_att; int* reg_floods;
+    int* members; int* lhat;
+    // local-order scratch (slots: members + one saddle per region)
+    int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
+    long long lo_cap;
+    // reorder
+    RankBlk* rblk; int nblk; int nblk_cur;
+    int* sad_att; int* cumA;
+    // scans
+    unsigned long long* scan_tmp; int scan_tmp_cap;
+    // counters
+    DevCounters* ctr;
+    PassStats* pstats;                   // [0] minima pass, [1] maxima pass
+    DevCounters* h_ctr;                  // pinned host copy (followed by two PassStats)
+    int lanes;                           // propagation lanes (threads)
+    int class_cap;                       // capacity of the class and region arrays
+    long long launches;                  // kernels launched by the current call
+};
+
+// ---- launch helpers (defined in the .cu files) ----
+cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int* O, cudaStream_t s);
+cudaError_t build_authbits(Work& w, const Geom& g, const int* ids, long long nids, cudaStream_t s);
+template <int DIR>
+cudaError_t classify(Work& w, const Geom& g, const int* O, cudaStream_t s);
+template <int DIR>
+cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
+template <int DIR>
+cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
+template <int DIR>
+cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
+template <int DIR>
+cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms, cudaStream_t s);
+cudaError_t pass_reset(Work& w, cudaStream_t s);
+
+// device-wide exclusive scan of `count` values (count read on the device)
+cudaError_t scan_excl_i32(Work& w, const int* in, int* out, const int* d_count, int max_count,
+                          cudaStream_t s);
+
+}  // namespace lts

@@ -1,0 +1,294 @@
+// Order field (Sec. 4.1): vertices sorted by (f, vertex id); O(v) = rank.
+//
+// Onesweep LSD radix sort of 32-bit order-preserving keys with the vertex id
+// as value: one histogram pass over f (which also copies f into the output
+// field g), then four 8-bit digit passes.  Each pass takes tiles in launch
+// order from an atomic counter, ranks its keys with warp match-any groups,
+// finds its global digit offsets by decoupled look-back over the tiles before
+// it (bounded spins), and scatters through shared memory so that every digit
+// run is written contiguously.  The last pass writes O[id] = rank directly.
+#include "lts_internal.cuh"
+
+namespace lts {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;   // 4096 keys
+constexpr int kWarps = kThreads / 32;
+
+// IEEE order as unsigned order; -0.0 is folded onto +0.0.
+__device__ __forceinline__ unsigned order_key(float x, int* st) {
+    unsigned u = __float_as_uint(x);
+    if ((u & 0x7fffffffu) > 0x7f800000u) set_status(st, LTS_ERR_NAN);
+    if (u == 0x80000000u) u = 0u;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Histograms of the four digits; each thread walks 16 consecutive keys and
+// flushes a digit count only when the digit changes (runs of equal high
+// digits are common in smooth fields, so this avoids contended atomics).
+__global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __restrict__ f, float* __restrict__ gout,
+                                                             int n, unsigned* __restrict__ hist, int* st) {
+    __shared__ unsigned sh[4][256];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    const long long chunk = 16;
+    const long long nchunks = (n + chunk - 1) / chunk;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nchunks;
+         c += (long long)gridDim.x * blockDim.x) {
+        const long long b = c * chunk;
+        unsigned cur[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+        unsigned cc[4] = {0, 0, 0, 0};
+        const bool vec = ((reinterpret_cast<unsigned long long>(f) | reinterpret_cast<unsigned long long>(gout)) & 15ull) == 0;
+        if (vec && b + chunk <= n) {
+            const float4* p = reinterpret_cast<const float4*>(f + b);
+            float4* q = reinterpret_cast<float4*>(gout + b);
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float4 t = __ldcs(p + j);
+                __stcs(q + j, t);
+                v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                unsigned k = order_key(v[j], st);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    unsigned dg = (k >> (8 * d)) & 255u;
+                    if (dg != cur[d]) {
+                        if (cc[d]) atomicAdd(&sh[d][cur[d]], cc[d]);
+                        cur[d] = dg; cc[d] = 0;
+                    }
+                    ++cc[d];
+                }
+            }
+        } else {
+            for (long long i = b; i < n; ++i) {
+                float x = f[i];
+                gout[i] = x;
+                unsigned k = order_key(x, st);
+                for (int d = 0; d < 4; ++d) {
+                    unsigned dg = (k >> (8 * d)) & 255u;
+                    if (dg != cur[d]) {
+                        if (cc[d]) atomicAdd(&sh[d][cur[d]], cc[d]);
+                        cur[d] = dg; cc[d] = 0;
+                    }
+                    ++cc[d];
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+            if (cc[d]) atomicAdd(&sh[d][cur[d]], cc[d]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+        unsigned v = (&sh[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// Exclusive prefix of each digit's histogram: global start of every bucket.
+__global__ void digit_offsets_kernel(const unsigned* __restrict__ hist, unsigned* __restrict__ off) {
+    const int d = blockIdx.x;          // 4 blocks of 256 threads
+    const int t = threadIdx.x;
+    __shared__ unsigned s[256];
+    s[t] = hist[d * 256 + t];
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        unsigned v = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    off[d * 256 + t] = s[t] - hist[d * 256 + t];
+}
+
+__device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsigned flag, unsigned val) {
+    return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | val;
+}
+
+// One digit pass.  FIRST: keys come from f and values are the indices.
+// LAST: instead of writing the sorted pairs, write O[value] = rank.
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(kThreads) onesweep_kernel(
+    const float* __restrict__ f, const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
+    unsigned* __restrict__ kout, unsigned* __restrict__ vout, int* __restrict__ Oout, int n, int shift,
+    const unsigned* __restrict__ goff, unsigned long long* status, unsigned* tile_ctr, unsigned epoch, int* st) {
+    __shared__ unsigned s_tile;
+    __shared__ unsigned wh[kWarps][256];
+    __shared__ unsigned s_gstart[256];
+    __shared__ unsigned s_lstart[256];
+    __shared__ unsigned s_wsum[kWarps];
+    __shared__ unsigned skey[LAST ? 1 : kTile];
+    __shared__ unsigned sval[LAST ? 1 : kTile];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int i = tid; i < kWarps * 256; i += kThreads) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned tile = s_tile;
+    const long long base = (long long)tile * kTile + warp * (32 * kItems);
+
+    unsigned key[kItems], val[kItems], rank[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const long long idx = base + i * 32 + lane;
+        if (idx < n) {
+            if (FIRST) { key[i] = order_key(__ldg(f + idx), st); val[i] = (unsigned)idx; }
+            else { key[i] = __ldcs(kin + idx); val[i] = __ldcs(vin + idx); }
+        } else {
+            key[i] = 0xffffffffu; val[i] = 0xffffffffu;   // sorts last within the tile, never written
+        }
+    }
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const unsigned d = (key[i] >> shift) & 255u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        unsigned b = 0;
+        if (lane == leader) { b = wh[warp][d]; wh[warp][d] = b + __popc(peers); }
+        b = __shfl_sync(0xffffffffu, b, leader);
+        rank[i] = b + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive offsets of the warps, tile count
+    const int d = tid;
+    unsigned run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) { unsigned t = wh[w][d]; wh[w][d] = run; run += t; }
+    const unsigned cnt = run;
+    // publish the aggregate (tile 0 publishes its inclusive prefix right away)
+    volatile unsigned long long* vs = status;
+    if (tile == 0) vs[d] = pack_status(epoch, 2u, cnt);
+    else vs[(long long)tile * 256 + d] = pack_status(epoch, 1u, cnt);
+    unsigned excl = 0;
+    if (tile > 0) {
+        long long t = (long long)tile - 1;
+        long long spins = 0;
+        while (t >= 0) {
+            unsigned long long w = vs[t * 256 + d];
+            const unsigned e = (unsigned)(w >> 34), fl = (unsigned)(w >> 32) & 3u;
+            if (e != epoch || fl == 0u) {
+                if (++spins > kSpinLimit) { set_status(st, LTS_ERR_TIMEOUT); break; }
+                continue;
+            }
+            excl += (unsigned)w;
+            if (fl == 2u) break;
+            --t;
+        }
+        __threadfence();
+        vs[(long long)tile * 256 + d] = pack_status(epoch, 2u, excl + cnt);
+    }
+    s_gstart[d] = goff[d] + excl;
+    // tile-local start of every digit (block-wide exclusive scan of cnt)
+    unsigned x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    unsigned wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+    s_lstart[d] = wpre + x - cnt;
+    __syncthreads();
+
+    if (LAST) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const long long idx = base + i * 32 + lane;
+            if (idx < n) {
+                const unsigned dg = (key[i] >> shift) & 255u;
+                const unsigned gp = s_gstart[dg] + wh[warp][dg] + rank[i];
+                if (gp < (unsigned)n) Oout[val[i]] = (int)gp;   // out of range only after a timeout
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const unsigned dg = (key[i] >> shift) & 255u;
+            const unsigned lp = s_lstart[dg] + wh[warp][dg] + rank[i];
+            skey[lp] = key[i];
+            sval[lp] = val[i];
+        }
+        __syncthreads();
+        const long long tb = (long long)tile * kTile;
+        const int valid = (int)min((long long)kTile, (long long)n - tb);
+        for (int j = tid; j < valid; j += kThreads) {
+            const unsigned k = skey[j];
+            const unsigned dg = (k >> shift) & 255u;
+            const unsigned gp = s_gstart[dg] + (unsigned)j - s_lstart[dg];
+            if (gp >= (unsigned)n) continue;                   // only after a look-back timeout
+            __stcs(kout + gp, k);
+            __stcs(vout + gp, sval[j]);
+        }
+    }
+}
+
+__global__ void authbits_kernel(const int* __restrict__ ids, long long nids, int n, unsigned* bits, int* st) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nids; i += (long long)gridDim.x * blockDim.x) {
+        const int v = ids[i];
+        if (v < 0 || v >= n) { set_status(st, LTS_ERR_ARG); continue; }
+        atomicOr(&bits[v >> 5], 1u << (v & 31));
+    }
+}
+
+}  // namespace
+
+cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int* O, cudaStream_t s) {
+    const int n = g.n;
+    const int tiles = (n + kTile - 1) / kTile;
+    int* st = &w.ctr->status;
+    cudaMemsetAsync(w.sort_hist, 0, 1024 * sizeof(unsigned), s);
+    cudaMemsetAsync(w.tile_counter, 0, 4 * sizeof(unsigned), s);
+    {
+        long long nch = (n + 15) / 16;
+        int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, 152LL * 8);
+        hist_copy_kernel<<<blocks, kThreads, 0, s>>>(f, gout, n, w.sort_hist, st);
+    }
+    digit_offsets_kernel<<<4, 256, 0, s>>>(w.sort_hist, w.sort_offsets);
+    w.launches += 6;
+    for (int p = 0; p < 4; ++p) {
+        unsigned epoch = ++w.epoch;
+        if (w.epoch >= (1u << 30) - 8) {   // epoch wrap: clear the look-back words
+            cudaMemsetAsync(w.sort_status, 0, (size_t)w.max_tiles * 256 * sizeof(unsigned long long), s);
+            w.epoch = 1;
+            epoch = 1;
+        }
+        const unsigned* goff = w.sort_offsets + 256 * p;
+        unsigned* tc = w.tile_counter + p;
+        if (p == 0)
+            onesweep_kernel<true, false><<<tiles, kThreads, 0, s>>>(f, nullptr, nullptr, w.keyA, w.valA, nullptr, n, 0,
+                                                                    goff, w.sort_status, tc, epoch, st);
+        else if (p == 1)
+            onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB, nullptr, n,
+                                                                     8, goff, w.sort_status, tc, epoch, st);
+        else if (p == 2)
+            onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyB, w.valB, w.keyA, w.valA, nullptr, n,
+                                                                     16, goff, w.sort_status, tc, epoch, st);
+        else
+            onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, nullptr, nullptr, O, n, 24,
+                                                                    goff, w.sort_status, tc, epoch, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t build_authbits(Work& w, const Geom& g, const int* ids, long long nids, cudaStream_t s) {
+    const size_t words = ((size_t)g.n + 31) / 32;
+    cudaMemsetAsync(w.authbits, 0, words * sizeof(unsigned), s);
+    if (nids > 0) {
+        int blocks = (int)std::min<long long>((nids + 255) / 256, 1024);
+        authbits_kernel<<<blocks, 256, 0, s>>>(ids, nids, g.n, w.authbits, &w.ctr->status);
+        w.launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lts

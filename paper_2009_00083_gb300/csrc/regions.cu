@@ -1,0 +1,164 @@
+// Regions after step 1 (Sec. 4.3: one region per hill chain).
+//
+// Every class still waiting when the propagation kernel ends is a region:
+// its saddle is where it waits and its members are the vertices it (or the
+// classes it absorbed) claimed, apart from final saddles.  Regions get dense
+// ids, member lists (CSR), their highest member's order (to order regions
+// that share a saddle, the reading that makes Eq. 6 a total order), and, per
+// saddle, the offset of each sibling block and the block total.
+#include "lts_internal.cuh"
+
+namespace lts {
+
+namespace {
+
+__device__ __forceinline__ int warp_reserve(int* counter, bool want) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    int b = 0;
+    if (lane == 0 && m) b = atomicAdd(counter, __popc(m));
+    b = __shfl_sync(0xffffffffu, b, 0);
+    return b + __popc(m & ((1u << lane) - 1u));
+}
+
+// flatten the class forest: parent[c] = root
+__global__ void flatten_kernel(int* parent, const DevCounters* ctr) {
+    const int nU = ctr->n_unauth;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nU; c += gridDim.x * blockDim.x) {
+        int r = c;
+        while (parent[r] != r) r = parent[r];
+        parent[c] = r;
+    }
+}
+
+template <int DIR>
+__global__ void roots_kernel(Geom g, const int* __restrict__ O, const int* __restrict__ parent,
+                             const int* __restrict__ wait_v, const int* __restrict__ owner, int* class2reg,
+                             int* reg_class, int* reg_saddle, int* reg_size, int* reg_top, int* reg_sod, int* reg_head,
+                             DevCounters* ctr) {
+    const int nU = ctr->n_unauth;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < nU; b += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(b + threadIdx.x);
+        const bool root = c < nU && parent[c] == c;
+        const int rid = warp_reserve(&ctr->n_regions, root);
+        if (c >= nU) continue;
+        if (!root) { class2reg[c] = -1; continue; }
+        const int sv = wait_v[c];
+        if (sv < 0) { set_status(&ctr->status, LTS_ERR_INTERNAL); class2reg[c] = -1; continue; }
+        class2reg[c] = rid;
+        reg_class[rid] = c;
+        reg_saddle[rid] = sv;
+        reg_size[rid] = 0;
+        reg_top[rid] = -1;
+        reg_sod[rid] = od<DIR>(O[sv], g.n);
+        reg_head[rid] = owner[sv] == c;
+    }
+}
+
+template <int DIR>
+__global__ void members_count_kernel(Geom g, const int* __restrict__ O, const int* __restrict__ vlog,
+                                     const int* __restrict__ parent, int* owner, int* loc,
+                                     const int* __restrict__ class2reg, const int* __restrict__ reg_saddle,
+                                     int* reg_size, int* reg_top, DevCounters* ctr) {
+    const int nlog = ctr->log_cursor;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlog; i += gridDim.x * blockDim.x) {
+        const int u = vlog[i];
+        if (u < 0) continue;
+        const int ow = owner[u];
+        const int rid = class2reg[parent[ow]];
+        if (rid < 0) { set_status(&ctr->status, LTS_ERR_INTERNAL); continue; }
+        if (reg_saddle[rid] == u) continue;                // a final saddle, not a member
+        loc[u] = atomicAdd(reg_size + rid, 1);
+        atomicMax(reg_top + rid, od<DIR>(O[u], g.n));
+        owner[u] = -2 - rid;                                // region tag
+    }
+}
+
+template <int DIR>
+__global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int* __restrict__ vlog,
+                                    const int* __restrict__ owner, const int* __restrict__ loc,
+                                    const int* __restrict__ reg_start, int* members, RankBlk* rblk,
+                                    DevCounters* ctr) {
+    const int nlog = ctr->log_cursor;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlog; i += gridDim.x * blockDim.x) {
+        const int u = vlog[i];
+        if (u < 0) continue;
+        const int t = owner[u];
+        if (t > -2) continue;
+        const int rid = -2 - t;
+        members[reg_start[rid] + loc[u]] = u;
+        const int j = od<DIR>(O[u], g.n);
+        atomicOr(&rblk[j >> 6].mmask, 1ull << (j & 63));
+    }
+}
+
+// Per saddle (run by its head region): order the sibling regions by their
+// highest member and give each the offset of its block below the saddle.
+__global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __restrict__ reg_head,
+                                const int* __restrict__ reg_sod, const int* __restrict__ reg_size,
+                                const int* __restrict__ reg_top, const int* __restrict__ listhead,
+                                const int* __restrict__ next_w, const int* __restrict__ class2reg, int* reg_place,
+                                int* reg_att, RankBlk* rblk, DevCounters* ctr) {
+    const int nreg = ctr->n_regions;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+        const int sz = reg_size[r];
+        atomicMax(&ctr->max_region, sz);
+        if (!reg_head[r]) continue;
+        // siblings: the head class and the chain of classes that joined it
+        int total = 0;
+        int cur = reg_class[r];
+        bool first = true;
+        while (cur >= 0) {
+            const int rr = class2reg[cur];
+            total += reg_size[rr];
+            cur = first ? listhead[reg_class[r]] : next_w[cur];
+            first = false;
+        }
+        cur = reg_class[r];
+        first = true;
+        while (cur >= 0) {
+            const int rr = class2reg[cur];
+            const int t = reg_top[rr];
+            int below = 0;                               // sizes of siblings with a lower top
+            int c2 = reg_class[r];
+            bool f2 = true;
+            while (c2 >= 0) {
+                const int r2 = class2reg[c2];
+                if (reg_top[r2] < t) below += reg_size[r2];
+                c2 = f2 ? listhead[reg_class[r]] : next_w[c2];
+                f2 = false;
+            }
+            reg_place[rr] = below - total;
+            cur = first ? listhead[reg_class[r]] : next_w[cur];
+            first = false;
+        }
+        reg_att[r] = total;
+        const int j = reg_sod[r];
+        atomicOr(&rblk[j >> 6].smask, 1ull << (j & 63));
+        atomicAdd(&ctr->n_saddles, 1);
+    }
+}
+
+}  // namespace
+
+template <int DIR>
+cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s) {
+    const int T = 256;
+    const int B = sms * 8;
+    flatten_kernel<<<B, T, 0, s>>>(w.parent, w.ctr);
+    roots_kernel<DIR><<<B, T, 0, s>>>(g, O, w.parent, w.wait_v, w.owner, w.class2reg, w.reg_class, w.reg_saddle,
+                                      w.reg_size, w.reg_top, w.reg_sod, w.reg_head, w.ctr);
+    members_count_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.parent, w.owner, w.loc, w.class2reg, w.reg_saddle,
+                                              w.reg_size, w.reg_top, w.ctr);
+    scan_excl_i32(w, w.reg_size, w.reg_start, &w.ctr->n_regions, g.n / 2 + 1, s);
+    members_fill_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.owner, w.loc, w.reg_start, w.members, w.rblk, w.ctr);
+    siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.listhead, w.next_w,
+                                    w.class2reg, w.reg_place, w.reg_att, w.rblk, w.ctr);
+    w.launches += 5;
+    return cudaGetLastError();
+}
+
+template cudaError_t extract_regions<1>(Work&, const Geom&, const int*, int, cudaStream_t);
+template cudaError_t extract_regions<-1>(Work&, const Geom&, const int*, int, cudaStream_t);
+
+}  // namespace lts
