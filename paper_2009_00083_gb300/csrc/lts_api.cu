@@ -11,6 +11,7 @@ namespace lts {
 int propagate_lanes(int sms);
 long long propagate_log_slack(int lanes);
 long long propagate_spill_slack(int lanes);
+long long propagate_heap_slack(int lanes);
 int scan_tiles_for(long long max_count);
 }  // namespace lts
 
@@ -43,7 +44,7 @@ Sizes sizes_for(long long n, int sms) {
     z.tiles = (n + 4095) / 4096;
     z.log_cap = n + propagate_log_slack((int)z.lanes);
     z.spill_cap = std::min<long long>(2 * n + propagate_spill_slack((int)z.lanes), (1LL << 31) - 1);
-    z.heap_cap = std::max<long long>(n, 1 << 20);
+    z.heap_cap = 2 * n + propagate_heap_slack((int)z.lanes);
     z.lo_cap = n + z.half;
     z.nblk = (n + 63) / 64;
     z.scan_tiles = std::max<long long>(scan_tiles_for(z.half + 1), (z.nblk + 4095) / 4096 + 1);
@@ -55,7 +56,7 @@ size_t bytes_for(const Sizes& z) {
     b += 4 * 4 * (size_t)z.n;                       // sort key/value double buffers
     b += (size_t)z.tiles * 256 * 8 + 4096 * 3;      // look-back words, histograms
     b += ((size_t)z.n + 31) / 32 * 4;               // authorized bitmap
-    b += 2 * 4 * (size_t)z.n;                       // owner, loc
+    b += 2 * 4 * (size_t)z.n + 8 * (size_t)z.n;     // owner, loc, qmark
     b += 8 * 4 * (size_t)z.half;                    // U and class records
     b += 4 * (size_t)z.spill_cap + 8 * (size_t)z.heap_cap + 4 * (size_t)z.log_cap;
     b += 11 * 4 * (size_t)z.half;                   // region records
@@ -173,7 +174,7 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     ok = ok && dev_alloc(c, &w.sort_status, (size_t)z.tiles * 256) && dev_alloc(c, &w.sort_hist, 1024) &&
          dev_alloc(c, &w.sort_offsets, 1024) && dev_alloc(c, &w.tile_counter, 4);
     ok = ok && dev_alloc(c, &w.authbits, (z.n + 31) / 32);
-    ok = ok && dev_alloc(c, &w.owner, z.n) && dev_alloc(c, &w.loc, z.n);
+    ok = ok && dev_alloc(c, &w.owner, z.n) && dev_alloc(c, &w.loc, z.n) && dev_alloc(c, &w.qmark, z.n);
     ok = ok && dev_alloc(c, &w.U, z.half) && dev_alloc(c, &w.parent, z.half) && dev_alloc(c, &w.wait_v, z.half) &&
          dev_alloc(c, &w.cnt, z.half) && dev_alloc(c, &w.listhead, z.half) && dev_alloc(c, &w.next_w, z.half) &&
          dev_alloc(c, &w.spill_base, z.half) && dev_alloc(c, &w.spill_n, z.half);
@@ -199,6 +200,8 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     for (auto& e : c->ev) cudaEventCreate(&e);
     c->events = true;
     cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, c->stream);
+    cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, c->stream);
+    w.pass_tag = 0;
     cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), c->stream);
     w.epoch = 0;

@@ -102,6 +102,8 @@ struct Work {
     unsigned int* authbits;              // ceil(n/32)
     // propagation
     int* owner;                          // per vertex: class, region tag, or -1
+    unsigned long long* qmark;           // per vertex: last (pass tag, class) that queued it
+    unsigned int pass_tag;
     int* loc;                            // per vertex: local index within its region
     int* U;                              // unauthorized extrema
     int* parent; int* wait_v; int* cnt; int* listhead; int* next_w;

@@ -35,6 +35,8 @@ constexpr int kSpillChunk = 256;
 struct PropArgs {
     const int* U;
     int* owner;
+    unsigned long long* qmark;   // (pass tag << 32 | class) of the last class that queued the vertex
+    unsigned long long tag;      // this pass's tag, in the high 32 bits
     int* parent;
     int* wait_v;
     int* cnt;
@@ -51,9 +53,14 @@ struct PropArgs {
     DevCounters* ctr;
 };
 
+// A lane's priority queue: in its shared-memory slice (stride = block size)
+// until it outgrows it, then in an HBM block that the lane keeps for its
+// later propagations and enlarges when needed.
 struct Heap {
     unsigned long long* h;
     int n, cap, stride;
+    unsigned long long* gblk;    // the lane's HBM block (or null)
+    int gcap;
 };
 
 __device__ __forceinline__ unsigned long long& at(Heap& H, int i) { return H.h[(long long)i * H.stride]; }
@@ -76,13 +83,16 @@ __device__ __forceinline__ bool in_class(int* parent, int ow, int c) {
 }
 
 __device__ bool heap_grow(Heap& H, const PropArgs& a) {
-    const int ncap = H.cap * 4;
-    const long long off = atomicAdd((unsigned long long*)&a.ctr->heap_cursor, (unsigned long long)ncap);
-    if (off + ncap > a.heap_cap) { set_status(&a.ctr->status, LTS_ERR_OOM); return false; }
-    unsigned long long* nh = a.heap_pool + off;
-    for (int i = 0; i < H.n; ++i) nh[i] = at(H, i);
+    if (H.gblk == nullptr || H.gcap <= H.cap) {
+        const int ncap = max(4 * H.cap, 256);
+        const long long off = atomicAdd((unsigned long long*)&a.ctr->heap_cursor, (unsigned long long)ncap);
+        if (off + ncap > a.heap_cap) { set_status(&a.ctr->status, LTS_ERR_OOM); return false; }
+        H.gblk = a.heap_pool + off;
+        H.gcap = ncap;
+    }
     if (H.stride != 1) atomicAdd(&a.ctr->heap_spills, 1);
-    H.h = nh; H.cap = ncap; H.stride = 1;
+    for (int i = 0; i < H.n; ++i) H.gblk[i] = at(H, i);   // forward copy: safe within the same block
+    H.h = H.gblk; H.cap = H.gcap; H.stride = 1;
     return true;
 }
 
@@ -123,6 +133,14 @@ __device__ __forceinline__ unsigned long long heap_pop(Heap& H) {
     return top;
 }
 
+// Queue vertex u (order ou) for class c unless c queued it already.
+__device__ __forceinline__ bool enqueue(Heap& H, const PropArgs& a, int u, int ou, int c) {
+    const unsigned long long mark = a.tag | (unsigned)c;
+    if (__ldcg(a.qmark + u) == mark) return true;
+    __stcg(a.qmark + u, mark);
+    return heap_push(H, ((unsigned long long)ou << 32) | (unsigned)u, a);
+}
+
 template <int DIR>
 __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
     extern __shared__ unsigned long long sheap[];
@@ -136,6 +154,7 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
     int seed_lo = 0, seed_hi = 0;
     long long log_pos = 0, log_end = 0;
     long long sp_pos = 0, sp_end = 0;
+    Heap H{myslice, 0, kHCap, kThreads, nullptr, 0};
 
     for (;;) {
         if (seed_lo == seed_hi) {
@@ -145,13 +164,13 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
             seed_hi = min(b + kSeedBatch, nU);
         }
         int c = seed_lo++;
-        Heap H{myslice, 0, kHCap, kThreads};
+        H.h = myslice; H.n = 0; H.cap = kHCap; H.stride = kThreads;
         {
             const int m = __ldg(a.U + c);
-            heap_push(H, ((unsigned long long)od<DIR>(__ldg(O + m), g.n) << 32) | (unsigned)m, a);
+            enqueue(H, a, m, od<DIR>(__ldg(O + m), g.n), c);
         }
         for (;;) {                                   // run class c until it stops at a saddle
-            if (H.n == 0) { set_status(st, LTS_ERR_INTERNAL); return; }
+            if (H.n == 0) { set_status(st, LTS_ERR_INTERNAL); goto bail; }
             const unsigned long long e = heap_pop(H);
             const int v = (int)(e & 0xffffffffu);
             const int kv = (int)(e >> 32);
@@ -166,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
                     if (log_pos == log_end) {
                         log_pos = atomicAdd(&ctr->log_cursor, kLogChunk);
                         log_end = log_pos + kLogChunk;
-                        if (log_end > a.log_cap) { set_status(st, LTS_ERR_OOM); return; }
+                        if (log_end > a.log_cap) { log_pos = log_end = 0; set_status(st, LTS_ERR_OOM); goto bail; }
                     }
                     a.vlog[log_pos++] = v;
                 } else {
@@ -194,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
                     const int nb = nbv[q];
                     if (nb < 0 || nbo[q] > kv) continue;
                     if (in_class(a.parent, __ldcg(a.owner + nb), c)) continue;
-                    if (!heap_push(H, ((unsigned long long)nbo[q] << 32) | (unsigned)nb, a)) return;
+                    if (!enqueue(H, a, nb, nbo[q], c)) goto bail;
                 }
                 continue;
             }
@@ -209,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
                 const int want = max(H.n, kSpillChunk);
                 sp_pos = atomicAdd(&ctr->spill_cursor, want);
                 sp_end = sp_pos + want;
-                if (sp_end > a.spill_cap) { set_status(st, LTS_ERR_OOM); return; }
+                if (sp_end > a.spill_cap) { set_status(st, LTS_ERR_OOM); goto bail; }
             }
             for (int i = 0; i < H.n; ++i) __stcg(a.spill_pool + sp_pos + i, (int)(at(H, i) & 0xffffffffu));
             __stcg(a.spill_base + c, (int)sp_pos);
@@ -229,8 +248,7 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
                     const int sb = __ldcg(a.spill_base + cur), sn = __ldcg(a.spill_n + cur);
                     for (int i = 0; i < sn; ++i) {
                         const int u = __ldcg(a.spill_pool + sb + i);
-                        if (!heap_push(H, ((unsigned long long)od<DIR>(__ldg(O + u), g.n) << 32) | (unsigned)u, a))
-                            return;
+                        if (!enqueue(H, a, u, od<DIR>(__ldg(O + u), g.n), c)) goto bail;
                     }
                 }
                 cur = first ? __ldcg(a.listhead + head) : __ldcg(a.next_w + cur);
@@ -243,10 +261,12 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
                 const int nb = nbv[q];
                 if (nb < 0 || nbo[q] > kv) continue;
                 if (in_class(a.parent, __ldcg(a.owner + nb), c)) continue;
-                if (!heap_push(H, ((unsigned long long)nbo[q] << 32) | (unsigned)nb, a)) return;
+                if (!enqueue(H, a, nb, nbo[q], c)) goto bail;
             }
         }
     }
+bail:
+    // every reserved log slot must hold a vertex or -1
     while (log_pos < log_end) a.vlog[log_pos++] = -1;
 }
 
@@ -255,16 +275,12 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* 
 template <int DIR>
 cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s) {
     PropArgs a;
-    a.U = w.U; a.owner = w.owner; a.parent = w.parent; a.wait_v = w.wait_v; a.cnt = w.cnt;
+    a.U = w.U; a.owner = w.owner; a.qmark = w.qmark; a.tag = (unsigned long long)(++w.pass_tag) << 32;
+    a.parent = w.parent; a.wait_v = w.wait_v; a.cnt = w.cnt;
     a.listhead = w.listhead; a.next_w = w.next_w; a.spill_base = w.spill_base; a.spill_n = w.spill_n;
     a.spill_pool = w.spill_pool; a.spill_cap = w.spill_cap; a.heap_pool = w.heap_pool; a.heap_cap = w.heap_cap;
     a.vlog = w.vlog; a.log_cap = w.log_cap; a.ctr = w.ctr;
     const size_t smem = (size_t)kThreads * kHCap * sizeof(unsigned long long);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(propagate_kernel<DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
     const int blocks = w.lanes / kThreads;
     propagate_kernel<DIR><<<blocks, kThreads, smem, s>>>(g, O, a);
     w.launches += 1;
@@ -274,6 +290,7 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
 int propagate_lanes(int sms) { return sms * 6 * kThreads; }
 long long propagate_log_slack(int lanes) { return (long long)lanes * kLogChunk; }
 long long propagate_spill_slack(int lanes) { return (long long)lanes * kSpillChunk; }
+long long propagate_heap_slack(int lanes) { return (long long)lanes * 512; }
 
 template cudaError_t propagate<1>(Work&, const Geom&, const int*, int, cudaStream_t);
 template cudaError_t propagate<-1>(Work&, const Geom&, const int*, int, cudaStream_t);

@@ -23,6 +23,7 @@ __device__ __forceinline__ int warp_reserve(int* counter, bool want) {
 
 // flatten the class forest: parent[c] = root
 __global__ void flatten_kernel(int* parent, const DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
     const int nU = ctr->n_unauth;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nU; c += gridDim.x * blockDim.x) {
         int r = c;
@@ -36,6 +37,7 @@ __global__ void roots_kernel(Geom g, const int* __restrict__ O, const int* __res
                              const int* __restrict__ wait_v, const int* __restrict__ owner, int* class2reg,
                              int* reg_class, int* reg_saddle, int* reg_size, int* reg_top, int* reg_sod, int* reg_head,
                              DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
     const int nU = ctr->n_unauth;
     for (long long b = (long long)blockIdx.x * blockDim.x; b < nU; b += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(b + threadIdx.x);
@@ -60,6 +62,7 @@ __global__ void members_count_kernel(Geom g, const int* __restrict__ O, const in
                                      const int* __restrict__ parent, int* owner, int* loc,
                                      const int* __restrict__ class2reg, const int* __restrict__ reg_saddle,
                                      int* reg_size, int* reg_top, DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
     const int nlog = ctr->log_cursor;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlog; i += gridDim.x * blockDim.x) {
         const int u = vlog[i];
@@ -79,6 +82,7 @@ __global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int
                                     const int* __restrict__ owner, const int* __restrict__ loc,
                                     const int* __restrict__ reg_start, int* members, RankBlk* rblk,
                                     DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
     const int nlog = ctr->log_cursor;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlog; i += gridDim.x * blockDim.x) {
         const int u = vlog[i];
@@ -99,6 +103,7 @@ __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __
                                 const int* __restrict__ reg_top, const int* __restrict__ listhead,
                                 const int* __restrict__ next_w, const int* __restrict__ class2reg, int* reg_place,
                                 int* reg_att, RankBlk* rblk, DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
         const int sz = reg_size[r];

@@ -89,6 +89,7 @@ __global__ void blk_apply_kernel(RankBlk* b, int nb, const unsigned long long* _
 __global__ void saddle_index_kernel(const RankBlk* __restrict__ rb, const int* __restrict__ reg_head,
                                     const int* __restrict__ reg_sod, const int* __restrict__ reg_att, int* sad_att,
                                     const DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
         if (!reg_head[r]) continue;
