@@ -185,7 +185,7 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
          dev_alloc(c, &w.reg_start, z.half + 1) && dev_alloc(c, &w.reg_top, z.half) &&
          dev_alloc(c, &w.reg_sod, z.half) && dev_alloc(c, &w.reg_place, z.half) && dev_alloc(c, &w.reg_head, z.half) &&
          dev_alloc(c, &w.reg_att, z.half) && dev_alloc(c, &w.reg_floods, z.half);
-    ok = ok && dev_alloc(c, &w.members, z.n) && dev_alloc(c, &w.lhat, z.n);
+    ok = ok && dev_alloc(c, &w.members, z.n) && dev_alloc(c, &w.lhat, z.n) && dev_alloc(c, &w.tier_list, z.half);
     ok = ok && dev_alloc(c, &w.lo_v, z.lo_cap) && dev_alloc(c, &w.lo_L, z.lo_cap) && dev_alloc(c, &w.lo_L2, z.lo_cap) &&
          dev_alloc(c, &w.lo_heap, z.lo_cap) && dev_alloc(c, &w.lo_flag, z.lo_cap);
     ok = ok && dev_alloc(c, &w.rblk, z.nblk) && dev_alloc(c, &w.sad_att, z.half) && dev_alloc(c, &w.cumA, z.half + 1);

@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/lts.h"
+#include "lts.h"
 
 namespace lts {
 
@@ -69,6 +69,8 @@ struct DevCounters {
     long long region_vertices;
     long long total_floods;
     int heap_spills;
+    int n_med;             // regions for the warp tier of step 2
+    int n_big;             // regions for the HBM tier of step 2
     int pad;
 };
 
@@ -115,6 +117,7 @@ struct Work {
     int* class2reg; int* reg_class; int* reg_saddle; int* reg_size; int* reg_start;
     int* reg_top; int* reg_sod; int* reg_place; int* reg_head; int* reg_att; int* reg_floods;
     int* members; int* lhat;
+    int* tier_list;                      // [0, cap/2): warp tier; [cap/2, cap): HBM tier
     // local-order scratch (slots: members + one saddle per region)
     int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
     long long lo_cap;
@@ -146,6 +149,22 @@ cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStre
 template <int DIR>
 cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms, cudaStream_t s);
 cudaError_t pass_reset(Work& w, cudaStream_t s);
+int local_order_tiny_max();
+int local_order_med_max();
+
+// warp-level reductions before one atomic (all 32 lanes must call)
+__device__ __forceinline__ void warp_atomic_max(int* dst, int v) {
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(dst, v);
+}
+__device__ __forceinline__ void warp_atomic_add(int* dst, int v) {
+    v = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+__device__ __forceinline__ void warp_atomic_add64(long long* dst, long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long*)dst, (unsigned long long)v);
+}
 
 // device-wide exclusive scan of `count` values (count read on the device)
 cudaError_t scan_excl_i32(Work& w, const int* in, int* out, const int* d_count, int max_count,

@@ -2,14 +2,17 @@
 // superlevel set propagation per unauthorized maximum, all in one persistent
 // kernel.
 //
-// Each lane runs one propagation (a "class") at a time.  Its priority queue
-// is a binary max-heap of (Od, vertex) in the lane's slice of shared memory;
-// when it outgrows that slice it moves to a block of an HBM pool and keeps
-// growing there.  Popping v:
+// Each propagation (a "class") is run by a team of lanes (16 in 3D, 8 in
+// 2D; two or four teams per warp): team lane q handles neighbour q of the
+// popped vertex, so the loads of all neighbours go out in one round trip and
+// every branch is uniform within the team.  The priority queue of the class
+// is a top-K frontier in the team's registers (E slots per lane), popped with
+// a team max-reduction; entries that do not fit go to a per-team binary heap
+// in an HBM pool.  Popping v:
 //   - v already in the class: skip;
 //   - claim v (atomicCAS on owner[v]); the vertex log records every claim;
 //   - k = higher neighbours of v in the class, h = all higher neighbours;
-//     k == h: v is regular for the class, push its lower neighbours;
+//     k == h: v is regular for the class, queue its lower neighbours;
 //   - otherwise v is a saddle for the class (an arrival): the class links
 //     itself into v's wait list (headed by the class that claimed v), copies
 //     its queue to the spill pool, and adds k to the arrival counter of v.
@@ -18,8 +21,12 @@
 //     queues into its own and continues below v.  Any other arrival stops.
 // A class thus only passes a saddle once every higher neighbour belongs to a
 // class that has arrived there, so the regions do not depend on the order in
-// which lanes run.  Nothing here waits on another lane: a stopped class just
+// which teams run.  Nothing here waits on another team: a stopped class just
 // ends its task, and the kernel ends when every seed has been taken.
+// Decisions that read shared mutable state (owner[], parent[]) are taken by
+// one lane and broadcast, so a team never diverges.
+#include <climits>
+
 #include "lts_internal.cuh"
 
 namespace lts {
@@ -27,10 +34,13 @@ namespace lts {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kHCap = 32;          // shared-memory queue entries per lane
 constexpr int kSeedBatch = 2;
 constexpr int kLogChunk = 64;
-constexpr int kSpillChunk = 256;
+constexpr int kSpillChunk = 512;
+
+template <int NN> struct TeamCfg;
+template <> struct TeamCfg<14> { static constexpr int TS = 16; static constexpr int E = 6; };
+template <> struct TeamCfg<6> { static constexpr int TS = 8; static constexpr int E = 8; };
 
 struct PropArgs {
     const int* U;
@@ -53,18 +63,6 @@ struct PropArgs {
     DevCounters* ctr;
 };
 
-// A lane's priority queue: in its shared-memory slice (stride = block size)
-// until it outgrows it, then in an HBM block that the lane keeps for its
-// later propagations and enlarges when needed.
-struct Heap {
-    unsigned long long* h;
-    int n, cap, stride;
-    unsigned long long* gblk;    // the lane's HBM block (or null)
-    int gcap;
-};
-
-__device__ __forceinline__ unsigned long long& at(Heap& H, int i) { return H.h[(long long)i * H.stride]; }
-
 // Union-find root with path halving; parent links only ever point to
 // ancestors, so the benign races of halving keep every path valid.
 __device__ __forceinline__ int find_root(int* parent, int x) {
@@ -82,192 +80,403 @@ __device__ __forceinline__ bool in_class(int* parent, int ow, int c) {
     return ow >= 0 && (ow == c || find_root(parent, ow) == c);
 }
 
-__device__ bool heap_grow(Heap& H, const PropArgs& a) {
-    if (H.gblk == nullptr || H.gcap <= H.cap) {
+// Neighbour q of (x,y,z) for a compile-time neighbour count NN.
+template <int NN>
+__device__ __forceinline__ int nbr_q(const Geom& g, int x, int y, int z, int q) {
+    constexpr int half = NN / 2;
+    const int m = (q < half ? q : q - half) + 1;
+    const int sgn = q < half ? 1 : -1;
+    const int a = x + (m & 1) * sgn, b = y + ((m >> 1) & 1) * sgn, c = z + ((m >> 2) & 1) * sgn;
+    if ((unsigned)a >= (unsigned)g.X || (unsigned)b >= (unsigned)g.Y || (unsigned)c >= (unsigned)g.Z) return -1;
+    return a + g.X * b + g.XY * c;
+}
+
+__device__ __forceinline__ unsigned long long pack(int key, int v) {
+    return ((unsigned long long)(unsigned)key << 32) | (unsigned)v;
+}
+
+// The overflow heap of a team (binary max-heap in HBM), used by lane 0 only.
+struct Overflow {
+    unsigned long long* h;
+    int n, cap;
+};
+
+__device__ bool ov_push(Overflow& H, unsigned long long e, const PropArgs& a) {
+    if (H.n == H.cap) {
         const int ncap = max(4 * H.cap, 256);
         const long long off = atomicAdd((unsigned long long*)&a.ctr->heap_cursor, (unsigned long long)ncap);
         if (off + ncap > a.heap_cap) { set_status(&a.ctr->status, LTS_ERR_OOM); return false; }
-        H.gblk = a.heap_pool + off;
-        H.gcap = ncap;
+        unsigned long long* nh = a.heap_pool + off;
+        for (int i = 0; i < H.n; ++i) nh[i] = H.h[i];
+        if (H.cap == 0) atomicAdd(&a.ctr->heap_spills, 1);
+        H.h = nh;
+        H.cap = ncap;
     }
-    if (H.stride != 1) atomicAdd(&a.ctr->heap_spills, 1);
-    for (int i = 0; i < H.n; ++i) H.gblk[i] = at(H, i);   // forward copy: safe within the same block
-    H.h = H.gblk; H.cap = H.gcap; H.stride = 1;
-    return true;
-}
-
-__device__ __forceinline__ bool heap_push(Heap& H, unsigned long long e, const PropArgs& a) {
-    if (H.n == H.cap && !heap_grow(H, a)) return false;
     int i = H.n++;
     while (i > 0) {
         const int p = (i - 1) >> 1;
-        const unsigned long long pe = at(H, p);
+        const unsigned long long pe = H.h[p];
         if (pe >= e) break;
-        at(H, i) = pe;
+        H.h[i] = pe;
         i = p;
     }
-    at(H, i) = e;
+    H.h[i] = e;
     return true;
 }
 
-__device__ __forceinline__ unsigned long long heap_pop(Heap& H) {
-    const unsigned long long top = at(H, 0);
+__device__ unsigned long long ov_pop(Overflow& H) {
+    const unsigned long long top = H.h[0];
     const int n = --H.n;
     if (n == 0) return top;
-    const unsigned long long last = at(H, n);
+    const unsigned long long last = H.h[n];
     int i = 0;
     for (;;) {
         const int l = 2 * i + 1;
         if (l >= n) break;
         int c = l;
-        unsigned long long ce = at(H, l);
-        if (l + 1 < n) {
-            const unsigned long long re = at(H, l + 1);
-            if (re > ce) { c = l + 1; ce = re; }
-        }
+        unsigned long long ce = H.h[l];
+        if (l + 1 < n && H.h[l + 1] > ce) { c = l + 1; ce = H.h[l + 1]; }
         if (ce <= last) break;
-        at(H, i) = ce;
+        H.h[i] = ce;
         i = c;
     }
-    at(H, i) = last;
+    H.h[i] = last;
     return top;
 }
 
-// Queue vertex u (order ou) for class c unless c queued it already.
-__device__ __forceinline__ bool enqueue(Heap& H, const PropArgs& a, int u, int ou, int c) {
-    const unsigned long long mark = a.tag | (unsigned)c;
-    if (__ldcg(a.qmark + u) == mark) return true;
-    __stcg(a.qmark + u, mark);
-    return heap_push(H, ((unsigned long long)ou << 32) | (unsigned)u, a);
+template <int NN>
+struct TeamState {
+    static constexpr int TS = TeamCfg<NN>::TS;
+    static constexpr int E = TeamCfg<NN>::E;
+    int sk[E];        // frontier slots: key (Od), -1 = empty
+    int sv[E];        //                 vertex
+    int rot;          // rotation of the slot assignment (spreads entries over lanes)
+    unsigned tmask;
+    int tb, lane;
+    Overflow ov;      // meaningful in team lane 0
+    int ovn;          // uniform copy of ov.n
+    int ov_top;       // uniform: key on top of the overflow heap, -1 if empty
+};
+
+template <int NN>
+__device__ __forceinline__ void ov_sync(TeamState<NN>& T) {
+    int n = T.ov.n;
+    int top = n > 0 ? (int)(T.ov.h[0] >> 32) : -1;
+    T.ovn = __shfl_sync(T.tmask, n, T.tb);
+    T.ov_top = __shfl_sync(T.tmask, top, T.tb);
 }
 
-template <int DIR>
-__global__ void __launch_bounds__(kThreads) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
-    extern __shared__ unsigned long long sheap[];
+// Adds one candidate per lane (has, key, vert) to the team frontier.
+// Returns false (uniformly) if the overflow pool is exhausted.
+template <int NN>
+__device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, const PropArgs& a) {
+    constexpr int TS = TeamState<NN>::TS, E = TeamState<NN>::E;
+    const int tl = T.lane - T.tb;
+    const int src = T.tb + ((tl - T.rot) & (TS - 1));
+    const bool hc = __shfl_sync(T.tmask, has, src);
+    const int ck = __shfl_sync(T.tmask, key, src);
+    const int cv = __shfl_sync(T.tmask, vert, src);
+    T.rot = (T.rot + NN) & (TS - 1);
+    bool need = false;
+    if (hc) {
+        bool placed = false;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (!placed && T.sk[e] < 0) { T.sk[e] = ck; T.sv[e] = cv; placed = true; }
+        need = !placed;
+    }
+    unsigned um = __ballot_sync(T.tmask, need);
+    bool ok = true;
+    while (um) {
+        const int L = __ffs(um) - 1;
+        um &= um - 1;
+        const int k2 = __shfl_sync(T.tmask, ck, L);
+        const int v2 = __shfl_sync(T.tmask, cv, L);
+        bool free_here = false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) free_here |= T.sk[e] < 0;
+        const unsigned fm = __ballot_sync(T.tmask, free_here);
+        if (fm) {
+            if (T.lane == __ffs(fm) - 1) {
+                bool placed = false;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (!placed && T.sk[e] < 0) { T.sk[e] = k2; T.sv[e] = v2; placed = true; }
+            }
+            continue;
+        }
+        // the frontier is full: the smallest of (team minimum, candidate) goes to HBM
+        int mk = INT_MAX, ms = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (T.sk[e] < mk) { mk = T.sk[e]; ms = e; }
+        const int MK = __reduce_min_sync(T.tmask, mk);
+        unsigned long long out;
+        if (k2 < MK) {
+            out = pack(k2, v2);
+        } else {
+            const int M = __ffs(__ballot_sync(T.tmask, mk == MK)) - 1;
+            int ev = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e == ms) ev = T.sv[e];
+            ev = __shfl_sync(T.tmask, ev, M);
+            if (T.lane == M) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (e == ms) { T.sk[e] = k2; T.sv[e] = v2; }
+            }
+            out = pack(MK, ev);
+        }
+        int r = 1;
+        if (T.lane == T.tb) r = ov_push(T.ov, out, a) ? 1 : 0;
+        r = __shfl_sync(T.tmask, r, T.tb);
+        ov_sync(T);
+        if (!r) { ok = false; break; }
+    }
+    return ok;
+}
+
+template <int DIR, int NN>
+__global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
+    constexpr int TS = TeamCfg<NN>::TS, E = TeamCfg<NN>::E;
     DevCounters* ctr = a.ctr;
     int* st = &ctr->status;
     if (failed(st)) return;
     const int nU = *(volatile int*)&ctr->n_unauth;
-    if (nU > 0 && *(volatile int*)&ctr->n_auth_ext == 0) { set_status(st, LTS_ERR_NO_AUTHORIZED); return; }
+    if (nU > 0 && *(volatile int*)&ctr->n_auth_ext == 0) {
+        if (threadIdx.x == 0) set_status(st, LTS_ERR_NO_AUTHORIZED);
+        return;
+    }
+    TeamState<NN> T;
+    T.lane = threadIdx.x & 31;
+    T.tb = T.lane & ~(TS - 1);
+    T.tmask = (TS == 32) ? 0xffffffffu : (((1u << TS) - 1u) << T.tb);
+    const int tl = T.lane - T.tb;
+    const bool leader = tl == 0;
+    T.rot = 0;
+    T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0;
+    T.ovn = 0; T.ov_top = -1;
+#pragma unroll
+    for (int e = 0; e < E; ++e) { T.sk[e] = -1; T.sv[e] = 0; }
 
-    unsigned long long* const myslice = sheap + threadIdx.x;   // interleaved: entry i at [i * kThreads]
+    // team-leader state
     int seed_lo = 0, seed_hi = 0;
     long long log_pos = 0, log_end = 0;
     long long sp_pos = 0, sp_end = 0;
-    Heap H{myslice, 0, kHCap, kThreads, nullptr, 0};
+    int c = -1;
 
     for (;;) {
-        if (seed_lo == seed_hi) {
-            const int b = atomicAdd(&ctr->seed_cursor, kSeedBatch);
-            if (b >= nU) break;
-            seed_lo = b;
-            seed_hi = min(b + kSeedBatch, nU);
+        if (c < 0) {                                   // take the next seed
+            int nc = -1;
+            if (leader) {
+                if (seed_lo == seed_hi) {
+                    const int b = atomicAdd(&ctr->seed_cursor, kSeedBatch);
+                    seed_lo = b;
+                    seed_hi = min(b + kSeedBatch, nU);
+                }
+                if (seed_lo < seed_hi && !failed(st)) nc = seed_lo++;
+            }
+            nc = __shfl_sync(T.tmask, nc, T.tb);
+            if (nc < 0) break;
+            c = nc;
+#pragma unroll
+            for (int e = 0; e < E; ++e) T.sk[e] = -1;
+            T.ov.n = 0; T.ovn = 0; T.ov_top = -1;
+            if (leader) {
+                const int m = __ldg(a.U + c);
+                T.sk[0] = od<DIR>(__ldg(O + m), g.n);
+                T.sv[0] = m;
+                __stcg(a.qmark + m, a.tag | (unsigned)c);
+            }
         }
-        int c = seed_lo++;
-        H.h = myslice; H.n = 0; H.cap = kHCap; H.stride = kThreads;
-        {
-            const int m = __ldg(a.U + c);
-            enqueue(H, a, m, od<DIR>(__ldg(O + m), g.n), c);
+        const unsigned long long mark = a.tag | (unsigned)c;
+        // ---- pop the highest queued vertex ----
+        int bk = -1, bs = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (T.sk[e] > bk) { bk = T.sk[e]; bs = e; }
+        const int K = __reduce_max_sync(T.tmask, bk);
+        if (K < 0 && T.ov_top < 0) {                  // cannot happen with an authorized maximum
+            if (leader) set_status(st, LTS_ERR_INTERNAL);
+            break;
         }
-        for (;;) {                                   // run class c until it stops at a saddle
-            if (H.n == 0) { set_status(st, LTS_ERR_INTERNAL); goto bail; }
-            const unsigned long long e = heap_pop(H);
-            const int v = (int)(e & 0xffffffffu);
-            const int kv = (int)(e >> 32);
-            int o = __ldcg(a.owner + v);
-            if (in_class(a.parent, o, c)) continue;
-            bool claimed = false;
-            if (o < 0) {
+        int v, kv;
+        if (T.ov_top > K) {
+            unsigned long long e = 0;
+            if (leader) e = ov_pop(T.ov);
+            e = __shfl_sync(T.tmask, e, T.tb);
+            ov_sync(T);
+            v = (int)(e & 0xffffffffu);
+            kv = (int)(e >> 32);
+        } else {
+            const int L = __ffs(__ballot_sync(T.tmask, bk == K)) - 1;
+            int myv = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e == bs) myv = T.sv[e];
+            if (T.lane == L) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (e == bs) T.sk[e] = -1;
+            }
+            v = __shfl_sync(T.tmask, myv, L);
+            kv = K;
+        }
+        // ---- one round of loads: owner of v; order, owner, mark of every neighbour ----
+        int x, y, z;
+        coords_of(g, v, x, y, z);
+        const int nb = tl < NN ? nbr_q<NN>(g, x, y, z, tl) : -1;
+        int on = -1, ow = -1;
+        unsigned long long qm = 0;
+        if (nb >= 0) {
+            on = od<DIR>(__ldg(O + nb), g.n);
+            ow = __ldcg(a.owner + nb);
+            qm = __ldcg(a.qmark + nb);
+        }
+        // the leader decides skip / claim and broadcasts
+        int o = -1, decision = 0;     // decision: 0 skip, 1 claimed, 2 owned by another class
+        if (leader) {
+            o = __ldcg(a.owner + v);
+            if (in_class(a.parent, o, c)) {
+                decision = 0;
+            } else if (o < 0) {
                 const int prev = atomicCAS(a.owner + v, -1, c);
                 if (prev == -1) {
-                    claimed = true;
+                    decision = 1;
                     o = c;
                     if (log_pos == log_end) {
                         log_pos = atomicAdd(&ctr->log_cursor, kLogChunk);
                         log_end = log_pos + kLogChunk;
-                        if (log_end > a.log_cap) { log_pos = log_end = 0; set_status(st, LTS_ERR_OOM); goto bail; }
+                        if (log_end > a.log_cap) {
+                            log_pos = log_end = 0;
+                            set_status(st, LTS_ERR_OOM);
+                            decision = -1;
+                        }
                     }
-                    a.vlog[log_pos++] = v;
+                    if (decision == 1) a.vlog[log_pos++] = v;
                 } else {
                     o = prev;
-                    if (in_class(a.parent, o, c)) continue;
+                    decision = in_class(a.parent, o, c) ? 0 : 2;
                 }
+            } else {
+                decision = 2;
             }
-            int x, y, z;
-            coords_of(g, v, x, y, z);
-            int nbv[14], nbo[14];
-            int h = 0, k = 0;
-            for (int q = 0; q < g.nn; ++q) {
-                const int nb = nbr_of(g, x, y, z, q);
-                nbv[q] = nb;
-                if (nb < 0) continue;
-                const int onb = od<DIR>(__ldg(O + nb), g.n);
-                nbo[q] = onb;
-                if (onb > kv) {
-                    ++h;
-                    if (in_class(a.parent, __ldcg(a.owner + nb), c)) ++k;
-                }
-            }
-            if (k == h) {                            // regular for this class
-                for (int q = 0; q < g.nn; ++q) {
-                    const int nb = nbv[q];
-                    if (nb < 0 || nbo[q] > kv) continue;
-                    if (in_class(a.parent, __ldcg(a.owner + nb), c)) continue;
-                    if (!enqueue(H, a, nb, nbo[q], c)) goto bail;
-                }
-                continue;
-            }
+        }
+        decision = __shfl_sync(T.tmask, decision, T.tb);
+        if (decision < 0) break;
+        if (decision == 0) continue;
+        o = __shfl_sync(T.tmask, o, T.tb);
+        const bool claimed = decision == 1;
+        const bool higher = nb >= 0 && on > kv;
+        bool inC = nb >= 0 && in_class(a.parent, ow, c);
+        const int h = __popc(__ballot_sync(T.tmask, higher));
+        const int k = __popc(__ballot_sync(T.tmask, higher && inC));
+        if (k != h) {
             // ---- arrival at the saddle v ----
             const int head = claimed ? c : o;
-            if (!claimed) {
+            if (leader && !claimed) {
                 const int old = atomicExch(a.listhead + head, c);
                 __stcg(a.next_w + c, old);
             }
             // the queue must be readable by whoever releases this class
-            if (sp_end - sp_pos < H.n) {
-                const int want = max(H.n, kSpillChunk);
-                sp_pos = atomicAdd(&ctr->spill_cursor, want);
-                sp_end = sp_pos + want;
-                if (sp_end > a.spill_cap) { set_status(st, LTS_ERR_OOM); goto bail; }
+            int nreg = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) nreg += T.sk[e] >= 0;
+            const int total = __reduce_add_sync(T.tmask, nreg) + T.ovn;
+            long long base = 0;
+            int okr = 1;
+            if (leader) {
+                if (sp_end - sp_pos < total) {
+                    const int want = max(total, kSpillChunk);
+                    sp_pos = atomicAdd(&ctr->spill_cursor, want);
+                    sp_end = sp_pos + want;
+                    if (sp_end > a.spill_cap) { set_status(st, LTS_ERR_OOM); okr = 0; sp_pos = sp_end = 0; }
+                }
+                base = sp_pos;
+                sp_pos += total;
             }
-            for (int i = 0; i < H.n; ++i) __stcg(a.spill_pool + sp_pos + i, (int)(at(H, i) & 0xffffffffu));
-            __stcg(a.spill_base + c, (int)sp_pos);
-            __stcg(a.spill_n + c, H.n);
-            sp_pos += H.n;
-            __stcg(a.wait_v + c, v);
-            __threadfence();
-            const int tot = atomicAdd(a.cnt + head, k) + k;
-            if (tot < h) break;                      // a higher neighbour is still unvisited: stop
+            okr = __shfl_sync(T.tmask, okr, T.tb);
+            if (!okr) break;
+            base = __shfl_sync(T.tmask, base, T.tb);
+            long long pos = base;
+            const unsigned below = (1u << T.lane) - 1u;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const bool hs = T.sk[e] >= 0;
+                const unsigned m = __ballot_sync(T.tmask, hs);
+                if (hs) __stcg(a.spill_pool + pos + __popc(m & below), T.sv[e]);
+                pos += __popc(m);
+            }
+            if (T.ovn > 0) {
+                const unsigned long long* oh = reinterpret_cast<const unsigned long long*>(
+                    __shfl_sync(T.tmask, reinterpret_cast<unsigned long long>(T.ov.h), T.tb));
+                for (int i = tl; i < T.ovn; i += TS) __stcg(a.spill_pool + pos + i, (int)(oh[i] & 0xffffffffu));
+            }
+            __threadfence();                           // publish this lane's part of the spill
+            __syncwarp(T.tmask);
+            int tot = 0;
+            if (leader) {
+                __stcg(a.spill_base + c, (int)base);
+                __stcg(a.spill_n + c, total);
+                __stcg(a.wait_v + c, v);
+                __threadfence();
+                tot = atomicAdd(a.cnt + head, k) + k;
+            }
+            tot = __shfl_sync(T.tmask, tot, T.tb);
+            if (tot < h) { c = -1; continue; }        // a higher neighbour is still unvisited: stop
             // ---- last arrival: merge every class stopped at v ----
-            __threadfence();
+            __threadfence();                           // every lane reads the other classes' spills
+            __syncwarp(T.tmask);
             int cur = head;
             bool first = true;
-            while (cur >= 0) {
+            bool okm = true;
+            while (cur >= 0 && okm) {
                 if (cur != c) {
-                    __stcg(a.parent + cur, c);
-                    const int sb = __ldcg(a.spill_base + cur), sn = __ldcg(a.spill_n + cur);
-                    for (int i = 0; i < sn; ++i) {
-                        const int u = __ldcg(a.spill_pool + sb + i);
-                        if (!enqueue(H, a, u, od<DIR>(__ldg(O + u), g.n), c)) goto bail;
+                    int sb = 0, sn = 0;
+                    if (leader) {
+                        __stcg(a.parent + cur, c);
+                        sb = __ldcg(a.spill_base + cur);
+                        sn = __ldcg(a.spill_n + cur);
+                    }
+                    sb = __shfl_sync(T.tmask, sb, T.tb);
+                    sn = __shfl_sync(T.tmask, sn, T.tb);
+                    for (int i = 0; i < sn && okm; i += TS) {
+                        const int idx = i + tl;
+                        bool hs = idx < sn;
+                        int u = 0, ou = 0;
+                        if (hs) {
+                            u = __ldcg(a.spill_pool + sb + idx);
+                            ou = od<DIR>(__ldg(O + u), g.n);
+                            hs = __ldcg(a.qmark + u) != mark;
+                            if (hs) __stcg(a.qmark + u, mark);
+                        }
+                        okm = insert_batch(T, hs, ou, u, a);
                     }
                 }
-                cur = first ? __ldcg(a.listhead + head) : __ldcg(a.next_w + cur);
+                int nx = -1;
+                if (leader) nx = first ? __ldcg(a.listhead + head) : __ldcg(a.next_w + cur);
+                cur = __shfl_sync(T.tmask, nx, T.tb);
                 first = false;
             }
-            __stcg(a.wait_v + c, -1);
-            if (head == c) { __stcg(a.cnt + c, 0); __stcg(a.listhead + c, -1); }
-            __threadfence();
-            for (int q = 0; q < g.nn; ++q) {         // v now belongs to c: continue below it
-                const int nb = nbv[q];
-                if (nb < 0 || nbo[q] > kv) continue;
-                if (in_class(a.parent, __ldcg(a.owner + nb), c)) continue;
-                if (!enqueue(H, a, nb, nbo[q], c)) goto bail;
+            if (!okm) break;
+            if (leader) {
+                __stcg(a.wait_v + c, -1);
+                if (head == c) { __stcg(a.cnt + c, 0); __stcg(a.listhead + c, -1); }
+                __threadfence();
             }
+            __syncwarp(T.tmask);
+            // classes merged into c: recheck which neighbours are in c
+            inC = nb >= 0 && in_class(a.parent, ow, c);
         }
+        // ---- v belongs to c: queue its lower neighbours ----
+        const bool cand = nb >= 0 && on < kv && !inC && qm != mark;
+        if (cand) __stcg(a.qmark + nb, mark);
+        if (!insert_batch(T, cand, on, nb, a)) break;
     }
-bail:
     // every reserved log slot must hold a vertex or -1
-    while (log_pos < log_end) a.vlog[log_pos++] = -1;
+    if (leader)
+        while (log_pos < log_end) a.vlog[log_pos++] = -1;
 }
 
 }  // namespace
@@ -280,17 +489,17 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
     a.listhead = w.listhead; a.next_w = w.next_w; a.spill_base = w.spill_base; a.spill_n = w.spill_n;
     a.spill_pool = w.spill_pool; a.spill_cap = w.spill_cap; a.heap_pool = w.heap_pool; a.heap_cap = w.heap_cap;
     a.vlog = w.vlog; a.log_cap = w.log_cap; a.ctr = w.ctr;
-    const size_t smem = (size_t)kThreads * kHCap * sizeof(unsigned long long);
     const int blocks = w.lanes / kThreads;
-    propagate_kernel<DIR><<<blocks, kThreads, smem, s>>>(g, O, a);
+    if (g.nn == 14) propagate_kernel<DIR, 14><<<blocks, kThreads, 0, s>>>(g, O, a);
+    else propagate_kernel<DIR, 6><<<blocks, kThreads, 0, s>>>(g, O, a);
     w.launches += 1;
     return cudaGetLastError();
 }
 
-int propagate_lanes(int sms) { return sms * 6 * kThreads; }
+int propagate_lanes(int sms) { return sms * 8 * kThreads; }
 long long propagate_log_slack(int lanes) { return (long long)lanes * kLogChunk; }
 long long propagate_spill_slack(int lanes) { return (long long)lanes * kSpillChunk; }
-long long propagate_heap_slack(int lanes) { return (long long)lanes * 512; }
+long long propagate_heap_slack(int lanes) { return (long long)lanes * 64; }
 
 template cudaError_t propagate<1>(Work&, const Geom&, const int*, int, cudaStream_t);
 template cudaError_t propagate<-1>(Work&, const Geom&, const int*, int, cudaStream_t);

@@ -102,12 +102,18 @@ __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __
                                 const int* __restrict__ reg_sod, const int* __restrict__ reg_size,
                                 const int* __restrict__ reg_top, const int* __restrict__ listhead,
                                 const int* __restrict__ next_w, const int* __restrict__ class2reg, int* reg_place,
-                                int* reg_att, RankBlk* rblk, DevCounters* ctr) {
+                                int* reg_att, RankBlk* rblk, int* tier_list, int half, int tiny_max,
+                                int med_max, DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
+    int my_max = 0, my_sad = 0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
         const int sz = reg_size[r];
-        atomicMax(&ctr->max_region, sz);
+        my_max = max(my_max, sz);
+        if (sz + 1 > tiny_max) {
+            if (sz + 1 <= med_max) tier_list[atomicAdd(&ctr->n_med, 1)] = r;
+            else tier_list[half + atomicAdd(&ctr->n_big, 1)] = r;
+        }
         if (!reg_head[r]) continue;
         // siblings: the head class and the chain of classes that joined it
         int total = 0;
@@ -140,8 +146,10 @@ __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __
         reg_att[r] = total;
         const int j = reg_sod[r];
         atomicOr(&rblk[j >> 6].smask, 1ull << (j & 63));
-        atomicAdd(&ctr->n_saddles, 1);
+        ++my_sad;
     }
+    warp_atomic_max(&ctr->max_region, my_max);
+    warp_atomic_add(&ctr->n_saddles, my_sad);
 }
 
 }  // namespace
@@ -158,7 +166,8 @@ cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaS
     scan_excl_i32(w, w.reg_size, w.reg_start, &w.ctr->n_regions, g.n / 2 + 1, s);
     members_fill_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.owner, w.loc, w.reg_start, w.members, w.rblk, w.ctr);
     siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.listhead, w.next_w,
-                                    w.class2reg, w.reg_place, w.reg_att, w.rblk, w.ctr);
+                                    w.class2reg, w.reg_place, w.reg_att, w.rblk, w.tier_list, w.class_cap / 2,
+                                    local_order_tiny_max(), local_order_med_max(), w.ctr);
     w.launches += 5;
     return cudaGetLastError();
 }
