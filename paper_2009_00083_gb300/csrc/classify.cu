@@ -10,62 +10,88 @@ namespace lts {
 
 namespace {
 
+constexpr int kRun = 16;              // consecutive vertices per thread
+constexpr int kCT = 256;              // threads per block; a tile is kCT * kRun vertices
+
+// Every thread classifies a run of kRun consecutive vertices; the block
+// scans the per-thread counts and appends the whole tile's unauthorized
+// extrema with a single atomic (per-warp atomics on one counter serialise).
 template <int DIR>
-__global__ void __launch_bounds__(256) classify_kernel(Geom g, const int* __restrict__ O,
+__global__ void __launch_bounds__(kCT) classify_kernel(Geom g, const int* __restrict__ O,
                                                        const unsigned* __restrict__ authbits, int* __restrict__ U,
                                                        int* __restrict__ parent, int* __restrict__ wait_v,
                                                        int* __restrict__ cnt, int* __restrict__ listhead,
                                                        int* __restrict__ next_w, int* __restrict__ spill_n,
                                                        int cap, DevCounters* ctr) {
+    __shared__ int s_warp[kCT / 32];
+    __shared__ int s_base;
     if (failed(&ctr->status)) return;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long b = (long long)blockIdx.x * blockDim.x; b < g.n; b += stride) {
-        const long long vv = b + threadIdx.x;
-        bool ext = false;
-        int v = (int)vv;
-        if (vv < g.n) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int my_auth = 0;
+    for (long long tile = blockIdx.x;; tile += gridDim.x) {
+        const long long base = tile * (long long)(kCT * kRun);
+        if (base >= g.n) break;
+        const long long v0 = base + (long long)threadIdx.x * kRun;
+        unsigned mu = 0;
+#pragma unroll 4
+        for (int i = 0; i < kRun; ++i) {
+            const long long vv = v0 + i;
+            if (vv >= g.n) break;
+            const int v = (int)vv;
             const int ov = od<DIR>(__ldg(O + v), g.n);
             int x, y, z;
             coords_of(g, v, x, y, z);
-            ext = true;
+            bool ext = true;
             for (int k = 0; k < g.nn; ++k) {
                 const int nb = nbr_of(g, x, y, z, k);
                 if (nb >= 0 && od<DIR>(__ldg(O + nb), g.n) > ov) { ext = false; break; }
             }
+            if (!ext) continue;
+            if ((__ldg(authbits + (v >> 5)) >> (v & 31)) & 1u) ++my_auth;
+            else mu |= 1u << i;
         }
-        const bool auth = ext && ((__ldg(authbits + (v >> 5)) >> (v & 31)) & 1u);
-        const bool un = ext && !auth;
-        const unsigned ma = __ballot_sync(0xffffffffu, auth);
-        const unsigned mu = __ballot_sync(0xffffffffu, un);
-        int basepos = 0;
-        if (lane == 0) {
-            if (ma) atomicAdd(&ctr->n_auth_ext, __popc(ma));
-            if (mu) basepos = atomicAdd(&ctr->n_unauth, __popc(mu));
+        // block-wide exclusive scan of the per-thread counts
+        const int c = __popc(mu);
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        basepos = __shfl_sync(0xffffffffu, basepos, 0);
-        if (un) {
-            const int c = basepos + __popc(mu & lt);
-            if (c >= cap) { set_status(&ctr->status, LTS_ERR_INTERNAL); continue; }
-            U[c] = v;
-            parent[c] = c;
-            wait_v[c] = -1;
-            cnt[c] = 0;
-            listhead[c] = -1;
-            next_w[c] = -1;
-            spill_n[c] = 0;
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < kCT / 32; ++w) { const int t = s_warp[w]; s_warp[w] = run; run += t; }
+            s_base = run ? atomicAdd(&ctr->n_unauth, run) : 0;
         }
+        __syncthreads();
+        int pos = s_base + s_warp[warp] + x - c;
+        while (mu) {
+            const int i = __ffs(mu) - 1;
+            mu &= mu - 1;
+            const int cl = pos++;
+            if (cl >= cap) { set_status(&ctr->status, LTS_ERR_INTERNAL); continue; }
+            U[cl] = (int)(v0 + i);
+            parent[cl] = cl;
+            wait_v[cl] = -1;
+            cnt[cl] = 0;
+            listhead[cl] = -1;
+            next_w[cl] = -1;
+            spill_n[cl] = 0;
+        }
+        __syncthreads();
     }
+    warp_atomic_add(&ctr->n_auth_ext, my_auth);
 }
 
 }  // namespace
 
 template <int DIR>
 cudaError_t classify(Work& w, const Geom& g, const int* O, cudaStream_t s) {
-    const int threads = 256;
-    const long long blocks = std::min<long long>(((long long)g.n + threads - 1) / threads, 152LL * 16);
-    classify_kernel<DIR><<<(int)blocks, threads, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v, w.cnt,
+    const long long tiles = ((long long)g.n + kCT * kRun - 1) / (kCT * kRun);
+    const long long blocks = std::min<long long>(tiles, 152LL * 8);
+    classify_kernel<DIR><<<(int)blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v, w.cnt,
                                                          w.listhead, w.next_w, w.spill_n, w.class_cap, w.ctr);
     w.launches += 1;
     return cudaGetLastError();

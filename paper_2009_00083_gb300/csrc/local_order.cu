@@ -13,11 +13,14 @@
 //   while some vertex other than s is a maximum.
 // Propagations only use edges inside R.
 //
-// The algorithm is written once over a storage policy and run in three
-// tiers by region size: regions of at most 16 vertices (nearly all of them)
-// one per lane with every array in shared memory; up to 1024 vertices one
-// per warp, the adjacency built by the whole warp and the propagations run
-// by one lane in shared memory; larger ones one per lane in HBM scratch.
+// Tiers by region size r = |R|:
+//   r <= 16 and r <= 32: one region per team of 16 / 32 lanes, one vertex per
+//     lane in registers (adjacency as a bit mask over the team's lanes); a
+//     propagation step is one team max/min reduction over the frontier and
+//     one broadcast of the popped vertex's adjacency;
+//   r <= 1024: one region per warp, arrays in shared memory; each step scans
+//     the frontier densely (r/32 vertices per lane) and reduces over the warp;
+//   larger: one region per lane, binary heaps in HBM scratch.
 #include <climits>
 
 #include "lts_internal.cuh"
@@ -27,8 +30,6 @@ namespace lts {
 namespace {
 
 constexpr unsigned char kBnd = 1, kVis = 2, kTried = 4;
-constexpr int kTinyR = 16;
-constexpr int kTinyThreads = 128;
 constexpr int kMedR = 1024;
 constexpr int kNoNbr = 0xffff;
 
@@ -36,39 +37,6 @@ constexpr int kNoNbr = 0xffff;
 // storage policies: V (vertex), L / L2 (local orders), Hp (heap of local
 // indices), F (flags), nbr(i, q) (local index of neighbour q, or -1)
 // ---------------------------------------------------------------------------
-
-// one lane, shared memory, slot i of lane t at [i * stride + t]
-template <int NN>
-struct TinyStore {
-    int* v; int* l; int* l2; unsigned char* hp; unsigned char* f; unsigned char* adj;
-    int stride;
-    __device__ int& V(int i) const { return v[i * stride]; }
-    __device__ int& L(int i) const { return l[i * stride]; }
-    __device__ int& L2(int i) const { return l2[i * stride]; }
-    __device__ int hp_get(int i) const { return hp[i * stride]; }
-    __device__ void hp_set(int i, int x) const { hp[i * stride] = (unsigned char)x; }
-    __device__ unsigned char& F(int i) const { return f[i * stride]; }
-    __device__ int nbr(int i, int q) const {
-        const unsigned char x = adj[(i * NN + q) * stride];
-        return x == 0xff ? -1 : x;
-    }
-};
-
-// one warp per region, shared memory (unit stride)
-template <int NN>
-struct MedStore {
-    int* v; int* l; int* l2; unsigned short* hp; unsigned char* f; unsigned short* adj;
-    __device__ int& V(int i) const { return v[i]; }
-    __device__ int& L(int i) const { return l[i]; }
-    __device__ int& L2(int i) const { return l2[i]; }
-    __device__ int hp_get(int i) const { return hp[i]; }
-    __device__ void hp_set(int i, int x) const { hp[i] = (unsigned short)x; }
-    __device__ unsigned char& F(int i) const { return f[i]; }
-    __device__ int nbr(int i, int q) const {
-        const unsigned short x = adj[i * NN + q];
-        return x == kNoNbr ? -1 : x;
-    }
-};
 
 // HBM scratch; neighbours recomputed from the grid and the region tags
 template <int NN>
@@ -265,83 +233,246 @@ struct FloodStat {
     }
 };
 
-// ---- tier 1: one lane per region of at most kTinyR vertices ----
-template <int DIR, int NN>
-__global__ void __launch_bounds__(kTinyThreads) lo_tiny_kernel(Geom g, LOArgs a) {
-    extern __shared__ unsigned char smem[];
+// ---- tiers 1-2: one region per team of TS lanes (r <= TS), registers ----
+
+template <int TS>
+struct TeamLO {
+    unsigned tm;   // team mask
+    int tb, tl, lane;
+};
+
+// superlevel propagation from the lane holding s; returns the team lane of
+// the last visited vertex, -2 if R was not covered; l2 = inverse visit order
+template <int TS>
+__device__ __forceinline__ int team_max_flood(const TeamLO<TS>& T, bool act, int L, unsigned adj, int m, int r,
+                                              int& l2) {
+    bool inq = T.tl == m, vis = false;
+    int last = -2;
+    for (int step = 0; step < r; ++step) {
+        const int key = (act && inq && !vis) ? L : INT_MIN;
+        const int K = __reduce_max_sync(T.tm, key);
+        if (K == INT_MIN) return -2;
+        const int p = __ffs(__ballot_sync(T.tm, act && inq && !vis && key == K)) - 1;
+        if (T.lane == p) { vis = true; l2 = r - 1 - step; }
+        const unsigned ap = __shfl_sync(T.tm, adj, p);
+        if ((ap >> T.tl) & 1u) inq = true;
+        last = p - T.tb;
+    }
+    return last;
+}
+
+// sublevel propagation from every lane with an outside neighbour but s
+template <int TS>
+__device__ __forceinline__ bool team_min_flood(const TeamLO<TS>& T, bool act, int L, unsigned adj, bool seed,
+                                               int r, int& l2) {
+    bool inq = act && seed, vis = false;
+    for (int step = 0; step < r; ++step) {
+        const int key = (act && inq && !vis) ? L : INT_MAX;
+        const int K = __reduce_min_sync(T.tm, key);
+        if (K == INT_MAX) return false;
+        const int p = __ffs(__ballot_sync(T.tm, act && inq && !vis && key == K)) - 1;
+        if (T.lane == p) { vis = true; l2 = step; }
+        const unsigned ap = __shfl_sync(T.tm, adj, p);
+        if ((ap >> T.tl) & 1u) inq = true;
+    }
+    return true;
+}
+
+// is this lane's vertex a strict extremum of L among its neighbours in R
+template <int TS>
+__device__ __forceinline__ void team_extremum(const TeamLO<TS>& T, int L, unsigned adj, bool& is_min,
+                                              bool& is_max) {
+    is_min = true;
+    is_max = true;
+#pragma unroll
+    for (int q = 0; q < TS; ++q) {
+        const int lq = __shfl_sync(T.tm, L, T.tb + q);
+        if ((adj >> q) & 1u) {
+            if (lq < L) is_min = false;
+            if (lq > L) is_max = false;
+        }
+    }
+}
+
+template <int DIR, int NN, int TS>
+__global__ void __launch_bounds__(128, 4) lo_team_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
     if (failed(&a.ctr->status)) return;
-    const int t = threadIdx.x;
-    const int B = kTinyThreads;
-    int* sv = reinterpret_cast<int*>(smem);
-    int* sl = sv + kTinyR * B;
-    int* sl2 = sl + kTinyR * B;
-    unsigned char* shp = reinterpret_cast<unsigned char*>(sl2 + kTinyR * B);
-    unsigned char* sf = shp + kTinyR * B;
-    unsigned char* sadj = sf + kTinyR * B;
-    TinyStore<NN> T{sv + t, sl + t, sl2 + t, shp + t, sf + t, sadj + t, B};
-    FloodStat fs;
-    const int nreg = a.ctr->n_regions;
-    for (int rid = blockIdx.x * B + t; rid < nreg; rid += gridDim.x * B) {
+    TeamLO<TS> T;
+    T.lane = threadIdx.x & 31;
+    T.tb = T.lane & ~(TS - 1);
+    T.tl = T.lane - T.tb;
+    T.tm = TS == 32 ? 0xffffffffu : (((1u << TS) - 1u) << T.tb);
+    const int team = (blockIdx.x * blockDim.x + threadIdx.x) / TS;
+    const int nteams = gridDim.x * blockDim.x / TS;
+    const int cnt = list ? *d_count : a.ctr->n_regions;
+    int mx = 0;
+    long long tot = 0;
+    for (int k = team; k < cnt; k += nteams) {
+        const int rid = list ? list[k] : k;
         const int m = a.reg_size[rid];
-        if (m + 1 > kTinyR) continue;
+        const int r = m + 1;
+        if (r > TS) continue;
         const int s = a.reg_saddle[rid];
         const int tag = -2 - rid;
         const int st0 = a.reg_start[rid];
-        for (int i = 0; i < m; ++i) T.V(i) = a.members[st0 + i];
-        T.V(m) = s;
-        for (int i = 0; i <= m; ++i) {
-            const int vtx = T.V(i);
+        const bool act = T.tl < r;
+        const bool mem = T.tl < m;
+        int vtx = -1;
+        if (act) vtx = mem ? a.members[st0 + T.tl] : s;
+        unsigned adj = 0;
+        bool bnd = false;
+        int L = INT_MIN;
+        if (act) {
             int x, y, z;
             coords_of(g, vtx, x, y, z);
-            unsigned char fl = 0;
+            int nbv[NN], ow[NN];
 #pragma unroll
             for (int q = 0; q < NN; ++q) {
-                const int nb = nbr_of(g, x, y, z, q);
-                unsigned char li = 0xff;
-                if (nb >= 0) {
-                    if (nb == s) li = (unsigned char)m;
-                    else if (__ldg(a.owner + nb) == tag) li = (unsigned char)__ldg(a.loc + nb);
-                    else fl = kBnd;
-                }
-                sadj[((i * NN + q) * B) + t] = li;
+                nbv[q] = nbr_of(g, x, y, z, q);
+                ow[q] = (nbv[q] >= 0 && nbv[q] != s) ? __ldg(a.owner + nbv[q]) : 0;
             }
-            T.F(i) = fl;
-            T.L(i) = od<DIR>(__ldg(a.O + vtx), g.n);
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                const int nb = nbv[q];
+                if (nb < 0) continue;
+                if (nb == s) adj |= 1u << m;
+                else if (ow[q] == tag) adj |= 1u << __ldg(a.loc + nb);
+                else bnd = true;
+            }
+            L = mem ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
         }
-        T.L(m) = INT_MAX;
-        const int nfl = local_order_run<NN>(T, m);
-        fs.add(a.ctr, nfl);
-        if (nfl < 0) continue;
-        for (int i = 0; i < m; ++i) a.lhat[st0 + i] = T.L(i);
+        // the minus-infinity vertex: lowest boundary-adjacent non-cut member
+        bool tried = false, ok = false;
+        int l2 = 0;
+        const int keepL = L;
+        for (;;) {
+            const int ck = (mem && bnd && !tried) ? L : INT_MAX;
+            const int cmin = __reduce_min_sync(T.tm, ck);
+            if (cmin == INT_MAX) break;
+            const int ap = __ffs(__ballot_sync(T.tm, ck == cmin && mem && bnd && !tried)) - 1;
+            if (T.lane == ap) L = -1;               // -infinity: every Od is >= 0
+            const int last = team_max_flood(T, act, L, adj, m, r, l2);
+            if (last == -2) break;
+            if (last == ap - T.tb) { ok = true; break; }
+            if (T.lane == ap) { L = keepL; tried = true; }
+        }
+        int nfl = -1;
+        if (ok) {
+            L = l2;
+            nfl = 1;
+            const int cap = 2 * r + 2;
+            for (;;) {
+                bool mn, mxx;
+                team_extremum(T, L, adj, mn, mxx);
+                if (!__any_sync(T.tm, act && !bnd && mn)) break;
+                if (!team_min_flood(T, act, L, adj, mem && bnd, r, l2)) { nfl = -1; break; }
+                L = l2;
+                ++nfl;
+                team_extremum(T, L, adj, mn, mxx);
+                if (!__any_sync(T.tm, mem && mxx)) break;
+                if (team_max_flood(T, act, L, adj, m, r, l2) < 0) { nfl = -1; break; }
+                L = l2;
+                ++nfl;
+                if (nfl > cap) { nfl = -1; break; }
+            }
+        }
+        if (nfl < 0) {
+            if (T.tl == 0) set_status(&a.ctr->status, LTS_ERR_INTERNAL);
+            continue;
+        }
+        if (mem) a.lhat[st0 + T.tl] = L;
+        mx = max(mx, nfl);
+        tot += nfl;
     }
+    // one count per region: only the team's first lane reports
+    if (T.tl != 0) { mx = 0; tot = 0; }
     __syncwarp();
-    fs.flush(a.ctr);
+    warp_atomic_max(&a.ctr->max_floods, mx);
+    warp_atomic_add64(&a.ctr->total_floods, tot);
 }
 
-// ---- tier 2: one warp per region of at most kMedR vertices ----
+// ---- tier 3: one warp per region of at most kMedR vertices, dense scans ----
+
+template <int NN>
+struct Dense {
+    int* v; int* L; int* L2; unsigned short* adj; unsigned char* f;   // f: kBnd | kVis | kTried | kInq
+};
+constexpr unsigned char kInq = 8;
+
+// superlevel (MAXF) or sublevel propagation over the region; the frontier is
+// scanned densely: each lane takes the best of its vertices, the warp reduces.
+template <bool MAXF, int NN>
+__device__ __forceinline__ int dense_flood(const Dense<NN>& D, int r, int lane) {
+    int last = -2;
+    for (int step = 0; step < r; ++step) {
+        int best = MAXF ? INT_MIN : INT_MAX, bi = -1;
+        for (int i = lane; i < r; i += 32) {
+            const unsigned char fl = D.f[i];
+            if ((fl & (kInq | kVis)) != kInq) continue;
+            const int l = D.L[i];
+            if (MAXF ? l > best : l < best) { best = l; bi = i; }
+        }
+        const int K = MAXF ? __reduce_max_sync(0xffffffffu, best) : __reduce_min_sync(0xffffffffu, best);
+        if (K == (MAXF ? INT_MIN : INT_MAX)) return -2;
+        const int src = __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1;
+        const int p = __shfl_sync(0xffffffffu, bi, src);
+        if (lane == 0) {
+            D.f[p] |= kVis;
+            D.L2[p] = MAXF ? r - 1 - step : step;
+        }
+        if (lane < NN) {
+            const unsigned short j = D.adj[p * NN + lane];
+            if (j != kNoNbr) D.f[j] |= kInq;            // byte stores by distinct lanes to distinct vertices
+        }
+        __syncwarp();
+        last = p;
+    }
+    return last;
+}
+
+template <int NN>
+__device__ __forceinline__ void dense_checks(const Dense<NN>& D, int r, int m, int lane, bool& umin, bool& umax) {
+    bool a_min = false, a_max = false;
+    for (int i = lane; i < r; i += 32) {
+        const int l = D.L[i];
+        bool is_min = true, is_max = true;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const unsigned short j = D.adj[i * NN + q];
+            if (j == kNoNbr) continue;
+            const int lj = D.L[j];
+            if (lj < l) is_min = false;
+            if (lj > l) is_max = false;
+        }
+        if (is_min && !(D.f[i] & kBnd)) a_min = true;
+        if (is_max && i < m) a_max = true;
+    }
+    umin = __any_sync(0xffffffffu, a_min);
+    umax = __any_sync(0xffffffffu, a_max);
+}
+
 template <int DIR, int NN>
-__global__ void __launch_bounds__(32) lo_med_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
+__global__ void __launch_bounds__(32) lo_dense_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
     extern __shared__ unsigned char smem[];
     if (failed(&a.ctr->status)) return;
-    int* sv = reinterpret_cast<int*>(smem);
-    int* sl = sv + kMedR;
-    int* sl2 = sl + kMedR;
-    unsigned short* shp = reinterpret_cast<unsigned short*>(sl2 + kMedR);
-    unsigned short* sadj = shp + kMedR;
-    unsigned char* sf = reinterpret_cast<unsigned char*>(sadj + kMedR * NN);
-    MedStore<NN> T{sv, sl, sl2, shp, sf, sadj};
+    Dense<NN> D;
+    D.v = reinterpret_cast<int*>(smem);
+    D.L = D.v + kMedR;
+    D.L2 = D.L + kMedR;
+    D.adj = reinterpret_cast<unsigned short*>(D.L2 + kMedR);
+    D.f = reinterpret_cast<unsigned char*>(D.adj + kMedR * NN);
     const int lane = threadIdx.x;
     const int cnt = *d_count;
     for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int rid = list[k];
         const int m = a.reg_size[rid];
+        const int r = m + 1;
         const int s = a.reg_saddle[rid];
         const int tag = -2 - rid;
         const int st0 = a.reg_start[rid];
-        for (int i = lane; i <= m; i += 32) sv[i] = i < m ? a.members[st0 + i] : s;
-        __syncwarp();
-        for (int i = lane; i <= m; i += 32) {
-            const int vtx = sv[i];
+        for (int i = lane; i < r; i += 32) {
+            const int vtx = i < m ? a.members[st0 + i] : s;
+            D.v[i] = vtx;
             int x, y, z;
             coords_of(g, vtx, x, y, z);
             unsigned char fl = 0;
@@ -354,26 +485,70 @@ __global__ void __launch_bounds__(32) lo_med_kernel(Geom g, LOArgs a, const int*
                     else if (__ldg(a.owner + nb) == tag) li = (unsigned short)__ldg(a.loc + nb);
                     else fl = kBnd;
                 }
-                sadj[i * NN + q] = li;
+                D.adj[i * NN + q] = li;
             }
-            sf[i] = fl;
-            sl[i] = i < m ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
+            D.f[i] = fl;
+            D.L[i] = i < m ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
         }
         __syncwarp();
-        int nfl = 0;
+        // the minus-infinity vertex
+        bool ok = false;
+        for (;;) {
+            int best = INT_MAX, bi = -1;
+            for (int i = lane; i < m; i += 32)
+                if ((D.f[i] & (kBnd | kTried)) == kBnd && D.L[i] < best) { best = D.L[i]; bi = i; }
+            const int K = __reduce_min_sync(0xffffffffu, best);
+            if (K == INT_MAX) break;
+            const int src = __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1;
+            const int ai = __shfl_sync(0xffffffffu, bi, src);
+            const int keep = D.L[ai];
+            __syncwarp();
+            if (lane == 0) D.L[ai] = -1;
+            for (int i = lane; i < r; i += 32) D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
+            __syncwarp();
+            const int last = dense_flood<true, NN>(D, r, lane);
+            if (last == -2) break;
+            if (last == ai) { ok = true; break; }
+            if (lane == 0) { D.L[ai] = keep; D.f[ai] |= kTried; }
+            __syncwarp();
+        }
+        int nfl = -1;
+        if (ok) {
+            nfl = 1;
+            const int cap = 2 * r + 2;
+            for (;;) {
+                for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
+                __syncwarp();
+                bool umin, umax;
+                dense_checks(D, r, m, lane, umin, umax);
+                if (!umin) break;
+                for (int i = lane; i < r; i += 32)
+                    D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | ((i < m && (D.f[i] & kBnd)) ? kInq : 0));
+                __syncwarp();
+                if (dense_flood<false, NN>(D, r, lane) == -2) { nfl = -1; break; }
+                ++nfl;
+                for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
+                __syncwarp();
+                dense_checks(D, r, m, lane, umin, umax);
+                if (!umax) break;
+                for (int i = lane; i < r; i += 32)
+                    D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
+                __syncwarp();
+                if (dense_flood<true, NN>(D, r, lane) == -2) { nfl = -1; break; }
+                ++nfl;
+                if (nfl > cap) { nfl = -1; break; }
+            }
+        }
+        __syncwarp();
+        if (nfl < 0) {
+            if (lane == 0) set_status(&a.ctr->status, LTS_ERR_INTERNAL);
+            continue;
+        }
+        for (int i = lane; i < m; i += 32) a.lhat[st0 + i] = D.L[i];
         if (lane == 0) {
-            nfl = local_order_run<NN>(T, m);
-            FloodStat fs;
-            fs.add(a.ctr, nfl);
-            if (nfl >= 0) {
-                atomicMax(&a.ctr->max_floods, nfl);
-                atomicAdd((unsigned long long*)&a.ctr->total_floods, (unsigned long long)nfl);
-            }
+            atomicMax(&a.ctr->max_floods, nfl);
+            atomicAdd((unsigned long long*)&a.ctr->total_floods, (unsigned long long)nfl);
         }
-        nfl = __shfl_sync(0xffffffffu, nfl, 0);
-        __syncwarp();
-        if (nfl >= 0)
-            for (int i = lane; i < m; i += 32) a.lhat[st0 + i] = sl[i];
         __syncwarp();
     }
 }
@@ -417,17 +592,16 @@ __global__ void __launch_bounds__(128) lo_big_kernel(Geom g, LOArgs a, const int
 }
 
 template <int NN>
-constexpr size_t tiny_smem() { return (size_t)kTinyR * kTinyThreads * (3 * 4 + 2 + NN); }
-template <int NN>
-constexpr size_t med_smem() { return (size_t)kMedR * (3 * 4 + 2 + 2 * NN + 1); }
+constexpr size_t dense_smem() { return (size_t)kMedR * (3 * 4 + 2 * NN + 1); }
 
 template <int DIR, int NN>
 void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t s) {
-    cudaFuncSetAttribute(lo_tiny_kernel<DIR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiny_smem<NN>());
-    cudaFuncSetAttribute(lo_med_kernel<DIR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)med_smem<NN>());
-    lo_tiny_kernel<DIR, NN><<<sms * 4, kTinyThreads, tiny_smem<NN>(), s>>>(g, a);
-    lo_med_kernel<DIR, NN><<<sms * 4, 32, med_smem<NN>(), s>>>(g, a, w.tier_list, &w.ctr->n_med);
-    lo_big_kernel<DIR, NN><<<sms, 128, 0, s>>>(g, a, w.tier_list + w.class_cap / 2, &w.ctr->n_big);
+    const int q = w.class_cap / 4;
+    cudaFuncSetAttribute(lo_dense_kernel<DIR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem<NN>());
+    lo_team_kernel<DIR, NN, 16><<<sms * 4, 128, 0, s>>>(g, a, nullptr, nullptr);
+    lo_team_kernel<DIR, NN, 32><<<sms * 4, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t32);
+    lo_dense_kernel<DIR, NN><<<sms * 5, 32, dense_smem<NN>(), s>>>(g, a, w.tier_list + q, &w.ctr->n_med);
+    lo_big_kernel<DIR, NN><<<sms, 128, 0, s>>>(g, a, w.tier_list + 2 * q, &w.ctr->n_big);
 }
 
 }  // namespace
@@ -438,14 +612,14 @@ cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStre
              w.lo_v, w.lo_L, w.lo_L2, w.lo_heap, w.lo_flag, w.tier_list, w.ctr};
     if (g.nn == 14) launch_tiers<DIR, 14>(w, g, a, sms, s);
     else launch_tiers<DIR, 6>(w, g, a, sms, s);
-    w.launches += 3;
+    w.launches += 4;
     return cudaGetLastError();
 }
 
 template cudaError_t local_orders<1>(Work&, const Geom&, const int*, int, cudaStream_t);
 template cudaError_t local_orders<-1>(Work&, const Geom&, const int*, int, cudaStream_t);
 
-int local_order_tiny_max() { return kTinyR; }
+int local_order_tiny_max() { return 16; }
 int local_order_med_max() { return kMedR; }
 
 }  // namespace lts

@@ -260,6 +260,8 @@ lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, co
     g.X = (int)gr->dims[0]; g.Y = (int)gr->dims[1]; g.Z = (int)gr->dims[2];
     g.n = (int)n;
     g.XY = g.X * g.Y;
+    g.dX = make_fastdiv((unsigned)g.X);
+    g.dXY = make_fastdiv((unsigned)g.XY);
     w.nblk_cur = (int)((n + 63) / 64);
     const int sms = c->sms;
     int* O = d_out_order;

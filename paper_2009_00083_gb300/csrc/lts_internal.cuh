@@ -13,12 +13,36 @@ namespace lts {
 // -{0,1}^d.  Offset k < nn/2 is the k+1-th non-zero 0/1 vector (bit b = axis b)
 // and offset k + nn/2 its negative.
 // ---------------------------------------------------------------------------
+// Division by a run-time constant d >= 2 as a multiply-high and shifts
+// (the round-up method of Granlund and Montgomery, exact for every 32-bit
+// unsigned numerator): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> 1)) >> (l - 1) with t = mulhi(m, n).
+struct FastDiv {
+    unsigned d, m, l;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    FastDiv f;
+    f.d = d;
+    unsigned l = 0;
+    while ((1ull << l) < d) ++l;
+    f.l = l;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+    const unsigned t = __umulhi(f.m, n);
+    return (t + ((n - t) >> 1)) >> (f.l - 1);
+}
+
 struct Geom {
     int ndim;
     int nn;            // 6 or 14
     int X, Y, Z;       // Z = 1 in 2D
     int n;             // X*Y*Z
     int XY;
+    FastDiv dX, dXY;
 };
 
 // Neighbour k of (x,y,z): returns its id, or -1 outside the grid.
@@ -33,9 +57,9 @@ __device__ __forceinline__ int nbr_of(const Geom& g, int x, int y, int z, int k)
 }
 
 __device__ __forceinline__ void coords_of(const Geom& g, int v, int& x, int& y, int& z) {
-    z = v / g.XY;
-    int r = v - z * g.XY;
-    y = r / g.X;
+    z = (int)fdiv((unsigned)v, g.dXY);
+    const int r = v - z * g.XY;
+    y = (int)fdiv((unsigned)r, g.dX);
     x = r - y * g.X;
 }
 
@@ -69,6 +93,7 @@ struct DevCounters {
     long long region_vertices;
     long long total_floods;
     int heap_spills;
+    int n_t32;             // regions for the 32-lane team tier of step 2
     int n_med;             // regions for the warp tier of step 2
     int n_big;             // regions for the HBM tier of step 2
     int pad;
@@ -117,7 +142,7 @@ struct Work {
     int* class2reg; int* reg_class; int* reg_saddle; int* reg_size; int* reg_start;
     int* reg_top; int* reg_sod; int* reg_place; int* reg_head; int* reg_att; int* reg_floods;
     int* members; int* lhat;
-    int* tier_list;                      // [0, cap/2): warp tier; [cap/2, cap): HBM tier
+    int* tier_list;                      // quarters of the class capacity: 32-lane, warp, HBM tiers
     // local-order scratch (slots: members + one saddle per region)
     int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
     long long lo_cap;

@@ -2,8 +2,8 @@
 // superlevel set propagation per unauthorized maximum, all in one persistent
 // kernel.
 //
-// Each propagation (a "class") is run by a team of lanes (16 in 3D, 8 in
-// 2D; two or four teams per warp): team lane q handles neighbour q of the
+// Each propagation (a "class") is run by a team of lanes (a whole warp, so
+// that no two propagations share an instruction stream): lane q handles neighbour q of the
 // popped vertex, so the loads of all neighbours go out in one round trip and
 // every branch is uniform within the team.  The priority queue of the class
 // is a top-K frontier in the team's registers (E slots per lane), popped with
@@ -27,6 +27,8 @@
 // one lane and broadcast, so a team never diverges.
 #include <climits>
 
+#include <cuda/atomic>
+
 #include "lts_internal.cuh"
 
 namespace lts {
@@ -34,13 +36,13 @@ namespace lts {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kSeedBatch = 2;
+constexpr int kSeedBatch = 16;
 constexpr int kLogChunk = 64;
-constexpr int kSpillChunk = 512;
+constexpr int kSpillChunk = 4096;
 
 template <int NN> struct TeamCfg;
-template <> struct TeamCfg<14> { static constexpr int TS = 16; static constexpr int E = 6; };
-template <> struct TeamCfg<6> { static constexpr int TS = 8; static constexpr int E = 8; };
+template <> struct TeamCfg<14> { static constexpr int TS = 32; static constexpr int E = 4; };
+template <> struct TeamCfg<6> { static constexpr int TS = 32; static constexpr int E = 4; };
 
 struct PropArgs {
     const int* U;
@@ -265,6 +267,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
     long long log_pos = 0, log_end = 0;
     long long sp_pos = 0, sp_end = 0;
     int c = -1;
+    bool merged = false;     // c has absorbed other classes: membership needs find_root
 
     for (;;) {
         if (c < 0) {                                   // take the next seed
@@ -280,6 +283,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             nc = __shfl_sync(T.tmask, nc, T.tb);
             if (nc < 0) break;
             c = nc;
+            merged = false;
 #pragma unroll
             for (int e = 0; e < E; ++e) T.sk[e] = -1;
             T.ov.n = 0; T.ovn = 0; T.ov_top = -1;
@@ -323,7 +327,10 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             v = __shfl_sync(T.tmask, myv, L);
             kv = K;
         }
-        // ---- one round of loads: owner of v; order, owner, mark of every neighbour ----
+        // the leader claims v first, so that the atomic overlaps the neighbour loads
+        int prev = 0;
+        if (leader) prev = atomicCAS(a.owner + v, -1, c);
+        // ---- one round of loads: order, owner, mark of every neighbour ----
         int x, y, z;
         coords_of(g, v, x, y, z);
         const int nb = tl < NN ? nbr_q<NN>(g, x, y, z, tl) : -1;
@@ -334,33 +341,25 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             ow = __ldcg(a.owner + nb);
             qm = __ldcg(a.qmark + nb);
         }
-        // the leader decides skip / claim and broadcasts
+        // the leader claims v (or learns its owner) and broadcasts the outcome
         int o = -1, decision = 0;     // decision: 0 skip, 1 claimed, 2 owned by another class
         if (leader) {
-            o = __ldcg(a.owner + v);
-            if (in_class(a.parent, o, c)) {
-                decision = 0;
-            } else if (o < 0) {
-                const int prev = atomicCAS(a.owner + v, -1, c);
-                if (prev == -1) {
-                    decision = 1;
-                    o = c;
-                    if (log_pos == log_end) {
-                        log_pos = atomicAdd(&ctr->log_cursor, kLogChunk);
-                        log_end = log_pos + kLogChunk;
-                        if (log_end > a.log_cap) {
-                            log_pos = log_end = 0;
-                            set_status(st, LTS_ERR_OOM);
-                            decision = -1;
-                        }
+            if (prev == -1) {
+                decision = 1;
+                o = c;
+                if (log_pos == log_end) {
+                    log_pos = atomicAdd(&ctr->log_cursor, kLogChunk);
+                    log_end = log_pos + kLogChunk;
+                    if (log_end > a.log_cap) {
+                        log_pos = log_end = 0;
+                        set_status(st, LTS_ERR_OOM);
+                        decision = -1;
                     }
-                    if (decision == 1) a.vlog[log_pos++] = v;
-                } else {
-                    o = prev;
-                    decision = in_class(a.parent, o, c) ? 0 : 2;
                 }
+                if (decision == 1) a.vlog[log_pos++] = v;
             } else {
-                decision = 2;
+                o = prev;
+                decision = (prev == c || (merged && find_root(a.parent, prev) == c)) ? 0 : 2;
             }
         }
         decision = __shfl_sync(T.tmask, decision, T.tb);
@@ -369,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
         o = __shfl_sync(T.tmask, o, T.tb);
         const bool claimed = decision == 1;
         const bool higher = nb >= 0 && on > kv;
-        bool inC = nb >= 0 && in_class(a.parent, ow, c);
+        bool inC = nb >= 0 && ow >= 0 && (ow == c || (merged && find_root(a.parent, ow) == c));
         const int h = __popc(__ballot_sync(T.tmask, higher));
         const int k = __popc(__ballot_sync(T.tmask, higher && inC));
         if (k != h) {
@@ -413,21 +412,22 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                     __shfl_sync(T.tmask, reinterpret_cast<unsigned long long>(T.ov.h), T.tb));
                 for (int i = tl; i < T.ovn; i += TS) __stcg(a.spill_pool + pos + i, (int)(oh[i] & 0xffffffffu));
             }
-            __threadfence();                           // publish this lane's part of the spill
-            __syncwarp(T.tmask);
+            __syncwarp(T.tmask);                       // orders the team's spill writes before the leader's fence
             int tot = 0;
             if (leader) {
                 __stcg(a.spill_base + c, (int)base);
                 __stcg(a.spill_n + c, total);
                 __stcg(a.wait_v + c, v);
-                __threadfence();
-                tot = atomicAdd(a.cnt + head, k) + k;
+                // release: this class's spill and records; acquire: those of the
+                // classes that arrived before
+                cuda::atomic_ref<int, cuda::thread_scope_device> counter(a.cnt[head]);
+                tot = counter.fetch_add(k, cuda::memory_order_acq_rel) + k;
             }
             tot = __shfl_sync(T.tmask, tot, T.tb);
             if (tot < h) { c = -1; continue; }        // a higher neighbour is still unvisited: stop
             // ---- last arrival: merge every class stopped at v ----
-            __threadfence();                           // every lane reads the other classes' spills
             __syncwarp(T.tmask);
+            merged = true;
             int cur = head;
             bool first = true;
             bool okm = true;

@@ -96,6 +96,26 @@ __global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int
     }
 }
 
+// Step-2 tier lists by region size r = members + 1 (r <= 16 needs no list).
+__global__ void tiers_kernel(const int* __restrict__ reg_size, int* tier_list, int q, int med_max,
+                             DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
+    const int nreg = ctr->n_regions;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < nreg; b += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(b + threadIdx.x);
+        const int sz = r < nreg ? reg_size[r] + 1 : 0;
+        const bool t32 = sz > 16 && sz <= 32;
+        const bool med = sz > 32 && sz <= med_max;
+        const bool big = sz > med_max;
+        const int p32 = warp_reserve(&ctr->n_t32, t32);
+        const int pm = warp_reserve(&ctr->n_med, med);
+        const int pb = warp_reserve(&ctr->n_big, big);
+        if (t32) tier_list[p32] = r;
+        if (med) tier_list[q + pm] = r;
+        if (big) tier_list[2 * q + pb] = r;
+    }
+}
+
 // Per saddle (run by its head region): order the sibling regions by their
 // highest member and give each the offset of its block below the saddle.
 __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __restrict__ reg_head,
@@ -110,10 +130,6 @@ __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
         const int sz = reg_size[r];
         my_max = max(my_max, sz);
-        if (sz + 1 > tiny_max) {
-            if (sz + 1 <= med_max) tier_list[atomicAdd(&ctr->n_med, 1)] = r;
-            else tier_list[half + atomicAdd(&ctr->n_big, 1)] = r;
-        }
         if (!reg_head[r]) continue;
         // siblings: the head class and the chain of classes that joined it
         int total = 0;
@@ -168,7 +184,8 @@ cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaS
     siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.listhead, w.next_w,
                                     w.class2reg, w.reg_place, w.reg_att, w.rblk, w.tier_list, w.class_cap / 2,
                                     local_order_tiny_max(), local_order_med_max(), w.ctr);
-    w.launches += 5;
+    tiers_kernel<<<B, T, 0, s>>>(w.reg_size, w.tier_list, w.class_cap / 4, local_order_med_max(), w.ctr);
+    w.launches += 6;
     return cudaGetLastError();
 }
 
