@@ -451,19 +451,26 @@ __device__ __forceinline__ void dense_checks(const Dense<NN>& D, int r, int m, i
     umax = __any_sync(0xffffffffu, a_max);
 }
 
-template <int DIR, int NN>
-__global__ void __launch_bounds__(32) lo_dense_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
+template <int NN, int RMAX>
+__host__ __device__ constexpr size_t dense_smem_per_warp() { return (size_t)RMAX * (3 * 4 + 2 * NN + 1) + 16; }
+
+// one region per warp, WPB warps per block, regions of at most RMAX vertices
+template <int DIR, int NN, int RMAX, int WPB>
+__global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
     extern __shared__ unsigned char smem[];
     if (failed(&a.ctr->status)) return;
+    const int wib = threadIdx.x >> 5;
+    unsigned char* mine = smem + (size_t)wib * dense_smem_per_warp<NN, RMAX>();
     Dense<NN> D;
-    D.v = reinterpret_cast<int*>(smem);
-    D.L = D.v + kMedR;
-    D.L2 = D.L + kMedR;
-    D.adj = reinterpret_cast<unsigned short*>(D.L2 + kMedR);
-    D.f = reinterpret_cast<unsigned char*>(D.adj + kMedR * NN);
-    const int lane = threadIdx.x;
+    D.v = reinterpret_cast<int*>(mine);
+    D.L = D.v + RMAX;
+    D.L2 = D.L + RMAX;
+    D.adj = reinterpret_cast<unsigned short*>(D.L2 + RMAX);
+    D.f = reinterpret_cast<unsigned char*>(D.adj + RMAX * NN);
+    const int lane = threadIdx.x & 31;
     const int cnt = *d_count;
-    for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
+    const int gw = blockIdx.x * WPB + wib, nw = gridDim.x * WPB;
+    for (int k = gw; k < cnt; k += nw) {
         const int rid = list[k];
         const int m = a.reg_size[rid];
         const int r = m + 1;
@@ -591,17 +598,19 @@ __global__ void __launch_bounds__(128) lo_big_kernel(Geom g, LOArgs a, const int
     fs.flush(a.ctr);
 }
 
-template <int NN>
-constexpr size_t dense_smem() { return (size_t)kMedR * (3 * 4 + 2 * NN + 1); }
-
 template <int DIR, int NN>
 void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t s) {
     const int q = w.class_cap / 4;
-    cudaFuncSetAttribute(lo_dense_kernel<DIR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem<NN>());
-    lo_team_kernel<DIR, NN, 16><<<sms * 4, 128, 0, s>>>(g, a, nullptr, nullptr);
-    lo_team_kernel<DIR, NN, 32><<<sms * 4, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t32);
-    lo_dense_kernel<DIR, NN><<<sms * 5, 32, dense_smem<NN>(), s>>>(g, a, w.tier_list + q, &w.ctr->n_med);
-    lo_big_kernel<DIR, NN><<<sms, 128, 0, s>>>(g, a, w.tier_list + 2 * q, &w.ctr->n_big);
+    constexpr size_t small = 4 * dense_smem_per_warp<NN, 128>();
+    constexpr size_t large = dense_smem_per_warp<NN, kMedR>();
+    cudaFuncSetAttribute(lo_dense_kernel<DIR, NN, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
+    cudaFuncSetAttribute(lo_dense_kernel<DIR, NN, kMedR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large);
+    const int* tl = w.tier_list + w.class_cap;
+    lo_team_kernel<DIR, NN, 16><<<sms * 4, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t16);
+    lo_team_kernel<DIR, NN, 32><<<sms * 4, 128, 0, s>>>(g, a, tl, &w.ctr->n_t32);
+    lo_dense_kernel<DIR, NN, 128, 4><<<sms * 4, 128, small, s>>>(g, a, tl + q, &w.ctr->n_med);
+    lo_dense_kernel<DIR, NN, kMedR, 1><<<sms * 5, 32, large, s>>>(g, a, tl + 2 * q, &w.ctr->n_large);
+    lo_big_kernel<DIR, NN><<<sms, 128, 0, s>>>(g, a, tl + 3 * q, &w.ctr->n_big);
 }
 
 }  // namespace
@@ -612,7 +621,7 @@ cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStre
              w.lo_v, w.lo_L, w.lo_L2, w.lo_heap, w.lo_flag, w.tier_list, w.ctr};
     if (g.nn == 14) launch_tiers<DIR, 14>(w, g, a, sms, s);
     else launch_tiers<DIR, 6>(w, g, a, sms, s);
-    w.launches += 4;
+    w.launches += 5;
     return cudaGetLastError();
 }
 

@@ -43,10 +43,10 @@ Sizes sizes_for(long long n, int sms) {
     z.lanes = propagate_lanes(sms);
     z.tiles = (n + 4095) / 4096;
     z.log_cap = n + propagate_log_slack((int)z.lanes);
-    z.spill_cap = std::min<long long>(2 * n + propagate_spill_slack((int)z.lanes), (1LL << 31) - 1);
+    z.spill_cap = std::min<long long>(4 * n + propagate_spill_slack((int)z.lanes), (1LL << 31) - 1);
     z.heap_cap = 2 * n + propagate_heap_slack((int)z.lanes);
     z.lo_cap = n + z.half;
-    z.nblk = (n + 63) / 64;
+    z.nblk = (n + 31) / 32;
     z.scan_tiles = std::max<long long>(scan_tiles_for(z.half + 1), (z.nblk + 4095) / 4096 + 1);
     return z;
 }
@@ -172,7 +172,8 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     ok = ok && dev_alloc(c, &w.keyA, z.n) && dev_alloc(c, &w.valA, z.n) && dev_alloc(c, &w.keyB, z.n) &&
          dev_alloc(c, &w.valB, z.n);
     ok = ok && dev_alloc(c, &w.sort_status, (size_t)z.tiles * 256) && dev_alloc(c, &w.sort_hist, 1024) &&
-         dev_alloc(c, &w.sort_offsets, 1024) && dev_alloc(c, &w.tile_counter, 4);
+         dev_alloc(c, &w.sort_offsets, 1024) && dev_alloc(c, &w.tile_counter, 4) &&
+         dev_alloc(c, &w.bin_cursor, 1024);
     ok = ok && dev_alloc(c, &w.authbits, (z.n + 31) / 32);
     ok = ok && dev_alloc(c, &w.owner, z.n) && dev_alloc(c, &w.loc, z.n) && dev_alloc(c, &w.qmark, z.n);
     ok = ok && dev_alloc(c, &w.U, z.half) && dev_alloc(c, &w.parent, z.half) && dev_alloc(c, &w.wait_v, z.half) &&
@@ -185,7 +186,8 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
          dev_alloc(c, &w.reg_start, z.half + 1) && dev_alloc(c, &w.reg_top, z.half) &&
          dev_alloc(c, &w.reg_sod, z.half) && dev_alloc(c, &w.reg_place, z.half) && dev_alloc(c, &w.reg_head, z.half) &&
          dev_alloc(c, &w.reg_att, z.half) && dev_alloc(c, &w.reg_floods, z.half);
-    ok = ok && dev_alloc(c, &w.members, z.n) && dev_alloc(c, &w.lhat, z.n) && dev_alloc(c, &w.tier_list, z.half);
+    ok = ok && dev_alloc(c, &w.members, z.n) && dev_alloc(c, &w.lhat, z.n) && dev_alloc(c, &w.tier_list, 2 * z.half) &&
+         dev_alloc(c, &w.member_reg, z.n);
     ok = ok && dev_alloc(c, &w.lo_v, z.lo_cap) && dev_alloc(c, &w.lo_L, z.lo_cap) && dev_alloc(c, &w.lo_L2, z.lo_cap) &&
          dev_alloc(c, &w.lo_heap, z.lo_cap) && dev_alloc(c, &w.lo_flag, z.lo_cap);
     ok = ok && dev_alloc(c, &w.rblk, z.nblk) && dev_alloc(c, &w.sad_att, z.half) && dev_alloc(c, &w.cumA, z.half + 1);
@@ -200,9 +202,9 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     for (auto& e : c->ev) cudaEventCreate(&e);
     c->events = true;
     cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, c->stream);
+    cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, c->stream);
     w.pass_tag = 0;
-    cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), c->stream);
     w.epoch = 0;
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -262,7 +264,7 @@ lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, co
     g.XY = g.X * g.Y;
     g.dX = make_fastdiv((unsigned)g.X);
     g.dXY = make_fastdiv((unsigned)g.XY);
-    w.nblk_cur = (int)((n + 63) / 64);
+    w.nblk_cur = (int)((n + 31) / 32);
     const int sms = c->sms;
     int* O = d_out_order;
     float* gout = d_out_field;

@@ -93,8 +93,10 @@ struct DevCounters {
     long long region_vertices;
     long long total_floods;
     int heap_spills;
+    int n_t16;             // regions for the 16-lane team tier of step 2 (3 <= r <= 16)
     int n_t32;             // regions for the 32-lane team tier of step 2
-    int n_med;             // regions for the warp tier of step 2
+    int n_med;             // regions for the small dense warp tier of step 2
+    int n_large;           // regions for the large dense warp tier of step 2
     int n_big;             // regions for the HBM tier of step 2
     int pad;
 };
@@ -104,13 +106,15 @@ struct PassStats {
     long long removed, regions, region_vertices, max_region, max_floods, total_floods, heap_spills;
 };
 
-// Rank-space block (64 ranks): members and saddles present, and prefix counts.
-struct RankBlk {
-    unsigned long long mmask;
-    unsigned long long smask;
+// Rank-space block of 32 ranks (16 bytes, one vector load): members and
+// saddles present, and the counts of members and saddles before the block.
+struct __align__(16) RankBlk {
+    unsigned int mmask;
+    unsigned int smask;
     unsigned int mpre;
     unsigned int spre;
 };
+constexpr int kRankShift = 5;
 
 // ---------------------------------------------------------------------------
 // Workspace (all device memory, sized for max_vertices).
@@ -124,6 +128,7 @@ struct Work {
     unsigned int* sort_hist;             // 4 x 256
     unsigned int* sort_offsets;          // 4 x 256
     unsigned int* tile_counter;          // 4
+    unsigned int* bin_cursor;            // id bins of the last radix pass
     unsigned int epoch;
     // authorized bitmap
     unsigned int* authbits;              // ceil(n/32)
@@ -141,8 +146,8 @@ struct Work {
     // regions
     int* class2reg; int* reg_class; int* reg_saddle; int* reg_size; int* reg_start;
     int* reg_top; int* reg_sod; int* reg_place; int* reg_head; int* reg_att; int* reg_floods;
-    int* members; int* lhat;
-    int* tier_list;                      // quarters of the class capacity: 32-lane, warp, HBM tiers
+    int* members; int* lhat; int* member_reg;   // CSR members, their local order, their region
+    int* tier_list;                      // [0,cap): 16-lane tier; then quarters of cap: 32-lane, dense <=128, dense <=1024, HBM
     // local-order scratch (slots: members + one saddle per region)
     int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
     long long lo_cap;

@@ -6,7 +6,11 @@
 // order from an atomic counter, ranks its keys with warp match-any groups,
 // finds its global digit offsets by decoupled look-back over the tiles before
 // it (bounded spins), and scatters through shared memory so that every digit
-// run is written contiguously.  The last pass writes O[id] = rank directly.
+// run is written contiguously.  The last pass does not scatter O[id] = rank
+// over the whole array (random 4-byte writes cost a read-modify-write of a
+// DRAM sector each): it appends the (id, rank) pairs to bins of 2^22 ids,
+// and an inverse pass then writes O bin by bin, so that the random writes of
+// one bin stay inside a 16 MB window of O that L2 merges into full sectors.
 #include "lts_internal.cuh"
 
 namespace lts {
@@ -17,6 +21,8 @@ constexpr int kThreads = 256;
 constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems;   // 4096 keys
 constexpr int kWarps = kThreads / 32;
+constexpr int kBinShift = 22;
+constexpr int kMaxBins = 1 << (31 - kBinShift);
 
 // IEEE order as unsigned order; -0.0 is folded onto +0.0.
 __device__ __forceinline__ unsigned order_key(float x, int* st) {
@@ -116,15 +122,17 @@ __device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsign
 template <bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kThreads) onesweep_kernel(
     const float* __restrict__ f, const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
-    unsigned* __restrict__ kout, unsigned* __restrict__ vout, int* __restrict__ Oout, int n, int shift,
+    unsigned* __restrict__ kout, unsigned* __restrict__ vout, unsigned* bin_cursor, int n, int shift,
     const unsigned* __restrict__ goff, unsigned long long* status, unsigned* tile_ctr, unsigned epoch, int* st) {
     __shared__ unsigned s_tile;
     __shared__ unsigned wh[kWarps][256];
     __shared__ unsigned s_gstart[256];
     __shared__ unsigned s_lstart[256];
     __shared__ unsigned s_wsum[kWarps];
-    __shared__ unsigned skey[LAST ? 1 : kTile];
-    __shared__ unsigned sval[LAST ? 1 : kTile];
+    __shared__ unsigned skey[kTile];
+    __shared__ unsigned sval[kTile];
+    __shared__ unsigned s_bcnt[LAST ? kMaxBins : 1];
+    __shared__ unsigned s_bstart[LAST ? kMaxBins : 1];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
@@ -151,10 +159,9 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         unsigned b = 0;
-        if (lane == leader) { b = wh[warp][d]; wh[warp][d] = b + __popc(peers); }
+        if (lane == leader) b = atomicAdd(&wh[warp][d], (unsigned)__popc(peers));
         b = __shfl_sync(0xffffffffu, b, leader);
         rank[i] = b + __popc(peers & lt);
-        __syncwarp();
     }
     __syncthreads();
     // per digit: exclusive offsets of the warps, tile count
@@ -201,14 +208,55 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(
     __syncthreads();
 
     if (LAST) {
+        // group the tile's (id, rank) pairs by id bin in shared memory
+        const int nbins = (int)(((unsigned)n + (1u << kBinShift) - 1) >> kBinShift);
+        for (int b = tid; b < nbins; b += kThreads) s_bcnt[b] = 0;
+        __syncthreads();
+        unsigned lidx[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            // few bins: aggregate per warp before the shared atomic
+            const long long idx = base + i * 32 + lane;
+            const unsigned bin = idx < n ? (val[i] >> kBinShift) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            const int leader = __ffs(peers) - 1;
+            unsigned b = 0;
+            if (lane == leader && bin != 0xffffffffu) b = atomicAdd(&s_bcnt[bin], (unsigned)__popc(peers));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            lidx[i] = b + __popc(peers & lt);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned run = 0;
+            for (int b = 0; b < nbins; ++b) { const unsigned c = s_bcnt[b]; s_bstart[b] = run; run += c; }
+        }
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const long long idx = base + i * 32 + lane;
             if (idx < n) {
                 const unsigned dg = (key[i] >> shift) & 255u;
                 const unsigned gp = s_gstart[dg] + wh[warp][dg] + rank[i];
-                if (gp < (unsigned)n) Oout[val[i]] = (int)gp;   // out of range only after a timeout
+                const unsigned lp = s_bstart[val[i] >> kBinShift] + lidx[i];
+                sval[lp] = val[i];
+                skey[lp] = gp;
             }
+        }
+        __syncthreads();
+        // one atomic per non-empty bin reserves the tile's run in that bin
+        for (int b = tid; b < nbins; b += kThreads) {
+            const unsigned c = s_bcnt[b];
+            s_bcnt[b] = c ? atomicAdd(&bin_cursor[b], c) - s_bstart[b] : 0u;   // global start minus local start
+        }
+        __syncthreads();
+        const long long tb = (long long)tile * kTile;
+        const int valid = (int)min((long long)kTile, (long long)n - tb);
+        for (int j = tid; j < valid; j += kThreads) {
+            const unsigned id = sval[j];
+            const unsigned gpos = s_bcnt[id >> kBinShift] + (unsigned)j;
+            if (gpos >= (unsigned)n || skey[j] >= (unsigned)n) continue;   // only after a look-back timeout
+            __stcs(kout + gpos, id);
+            __stcs(vout + gpos, skey[j]);
         }
     } else {
 #pragma unroll
@@ -229,6 +277,22 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(
             __stcs(kout + gp, k);
             __stcs(vout + gp, sval[j]);
         }
+    }
+}
+
+// bins of 2^kBinShift ids: bin b is filled from position b << kBinShift
+__global__ void bin_init_kernel(unsigned* bin_cursor, int nbins) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbins) bin_cursor[b] = (unsigned)b << kBinShift;
+}
+
+// O[id] = rank for the binned pairs, walked in bin order
+__global__ void __launch_bounds__(256) inverse_kernel(const unsigned* __restrict__ ids, const unsigned* __restrict__ ranks,
+                                                      int* __restrict__ O, int n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned id = __ldcs(ids + i);
+        if (id < (unsigned)n) O[id] = (int)__ldcs(ranks + i);
     }
 }
 
@@ -254,7 +318,9 @@ cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int
         hist_copy_kernel<<<blocks, kThreads, 0, s>>>(f, gout, n, w.sort_hist, st);
     }
     digit_offsets_kernel<<<4, 256, 0, s>>>(w.sort_hist, w.sort_offsets);
-    w.launches += 6;
+    const int nbins = (int)(((unsigned)n + (1u << kBinShift) - 1) >> kBinShift);
+    bin_init_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(w.bin_cursor, nbins);
+    w.launches += 8;
     for (int p = 0; p < 4; ++p) {
         unsigned epoch = ++w.epoch;
         if (w.epoch >= (1u << 30) - 8) {   // epoch wrap: clear the look-back words
@@ -274,9 +340,11 @@ cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int
             onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyB, w.valB, w.keyA, w.valA, nullptr, n,
                                                                      16, goff, w.sort_status, tc, epoch, st);
         else
-            onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, nullptr, nullptr, O, n, 24,
-                                                                    goff, w.sort_status, tc, epoch, st);
+            onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB,
+                                                                    w.bin_cursor, n, 24, goff, w.sort_status, tc,
+                                                                    epoch, st);
     }
+    inverse_kernel<<<152 * 8, 256, 0, s>>>(w.keyB, w.valB, O, n);
     return cudaGetLastError();
 }
 

@@ -240,7 +240,7 @@ __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, cons
 }
 
 template <int DIR, int NN>
-__global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
+__global__ void __launch_bounds__(kThreads, 12) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
     constexpr int TS = TeamCfg<NN>::TS, E = TeamCfg<NN>::E;
     DevCounters* ctr = a.ctr;
     int* st = &ctr->status;
@@ -274,9 +274,13 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             int nc = -1;
             if (leader) {
                 if (seed_lo == seed_hi) {
-                    const int b = atomicAdd(&ctr->seed_cursor, kSeedBatch);
+                    // guided batches: large while many seeds remain, single ones at the end
+                    const int rem = nU - *(volatile int*)&ctr->seed_cursor;
+                    const int nwarps = gridDim.x * (blockDim.x / 32);
+                    const int bsz = max(1, min(kSeedBatch, rem / (4 * nwarps)));
+                    const int b = atomicAdd(&ctr->seed_cursor, bsz);
                     seed_lo = b;
-                    seed_hi = min(b + kSeedBatch, nU);
+                    seed_hi = min(b + bsz, nU);
                 }
                 if (seed_lo < seed_hi && !failed(st)) nc = seed_lo++;
             }
@@ -287,12 +291,31 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
 #pragma unroll
             for (int e = 0; e < E; ++e) T.sk[e] = -1;
             T.ov.n = 0; T.ovn = 0; T.ov_top = -1;
+            // The seed is a maximum: no other class can reach it (classes only queue
+            // lower neighbours) and all its neighbours are lower, so it is claimed
+            // with a plain store and every neighbour is queued at once.
+            const int m = __ldg(a.U + c);
+            int okl = 1;
             if (leader) {
-                const int m = __ldg(a.U + c);
-                T.sk[0] = od<DIR>(__ldg(O + m), g.n);
-                T.sv[0] = m;
-                __stcg(a.qmark + m, a.tag | (unsigned)c);
+                __stcg(a.owner + m, c);
+                if (log_pos == log_end) {
+                    log_pos = atomicAdd(&ctr->log_cursor, kLogChunk);
+                    log_end = log_pos + kLogChunk;
+                    if (log_end > a.log_cap) { log_pos = log_end = 0; set_status(st, LTS_ERR_OOM); okl = 0; }
+                }
+                if (okl) a.vlog[log_pos++] = m;
             }
+            if (!__shfl_sync(T.tmask, okl, T.tb)) break;
+            int mx, my, mz;
+            coords_of(g, m, mx, my, mz);
+            const int mnb = tl < NN ? nbr_q<NN>(g, mx, my, mz, tl) : -1;
+            const unsigned long long mk = a.tag | (unsigned)c;
+            int mo = 0;
+            if (mnb >= 0) {
+                mo = od<DIR>(__ldg(O + mnb), g.n);
+                __stcg(a.qmark + mnb, mk);
+            }
+            if (!insert_batch(T, mnb >= 0, mo, mnb, a)) break;
         }
         const unsigned long long mark = a.tag | (unsigned)c;
         // ---- pop the highest queued vertex ----
@@ -386,14 +409,14 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             long long base = 0;
             int okr = 1;
             if (leader) {
-                if (sp_end - sp_pos < total) {
-                    const int want = max(total, kSpillChunk);
+                if (sp_end - sp_pos < 2 * total) {
+                    const int want = max(2 * total, kSpillChunk);
                     sp_pos = atomicAdd(&ctr->spill_cursor, want);
                     sp_end = sp_pos + want;
                     if (sp_end > a.spill_cap) { set_status(st, LTS_ERR_OOM); okr = 0; sp_pos = sp_end = 0; }
                 }
                 base = sp_pos;
-                sp_pos += total;
+                sp_pos += 2 * total;
             }
             okr = __shfl_sync(T.tmask, okr, T.tb);
             if (!okr) break;
@@ -404,13 +427,20 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             for (int e = 0; e < E; ++e) {
                 const bool hs = T.sk[e] >= 0;
                 const unsigned m = __ballot_sync(T.tmask, hs);
-                if (hs) __stcg(a.spill_pool + pos + __popc(m & below), T.sv[e]);
-                pos += __popc(m);
+                if (hs) {
+                    const long long at2 = pos + 2 * __popc(m & below);
+                    __stcg(a.spill_pool + at2, T.sv[e]);
+                    __stcg(a.spill_pool + at2 + 1, T.sk[e]);
+                }
+                pos += 2 * __popc(m);
             }
             if (T.ovn > 0) {
                 const unsigned long long* oh = reinterpret_cast<const unsigned long long*>(
                     __shfl_sync(T.tmask, reinterpret_cast<unsigned long long>(T.ov.h), T.tb));
-                for (int i = tl; i < T.ovn; i += TS) __stcg(a.spill_pool + pos + i, (int)(oh[i] & 0xffffffffu));
+                for (int i = tl; i < T.ovn; i += TS) {
+                    __stcg(a.spill_pool + pos + 2 * i, (int)(oh[i] & 0xffffffffu));
+                    __stcg(a.spill_pool + pos + 2 * i + 1, (int)(oh[i] >> 32));
+                }
             }
             __syncwarp(T.tmask);                       // orders the team's spill writes before the leader's fence
             int tot = 0;
@@ -446,10 +476,9 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                         bool hs = idx < sn;
                         int u = 0, ou = 0;
                         if (hs) {
-                            u = __ldcg(a.spill_pool + sb + idx);
-                            ou = od<DIR>(__ldg(O + u), g.n);
-                            hs = __ldcg(a.qmark + u) != mark;
-                            if (hs) __stcg(a.qmark + u, mark);
+                            u = __ldcg(a.spill_pool + sb + 2 * idx);
+                            ou = __ldcg(a.spill_pool + sb + 2 * idx + 1);
+                            __stcg(a.qmark + u, mark);
                         }
                         okm = insert_batch(T, hs, ou, u, a);
                     }
@@ -496,7 +525,7 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
     return cudaGetLastError();
 }
 
-int propagate_lanes(int sms) { return sms * 8 * kThreads; }
+int propagate_lanes(int sms) { return sms * 12 * kThreads; }
 long long propagate_log_slack(int lanes) { return (long long)lanes * kLogChunk; }
 long long propagate_spill_slack(int lanes) { return (long long)lanes * kSpillChunk; }
 long long propagate_heap_slack(int lanes) { return (long long)lanes * 64; }

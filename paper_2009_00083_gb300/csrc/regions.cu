@@ -80,7 +80,7 @@ __global__ void members_count_kernel(Geom g, const int* __restrict__ O, const in
 template <int DIR>
 __global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int* __restrict__ vlog,
                                     const int* __restrict__ owner, const int* __restrict__ loc,
-                                    const int* __restrict__ reg_start, int* members, RankBlk* rblk,
+                                    const int* __restrict__ reg_start, int* members, int* member_reg, RankBlk* rblk,
                                     DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nlog = ctr->log_cursor;
@@ -90,30 +90,47 @@ __global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int
         const int t = owner[u];
         if (t > -2) continue;
         const int rid = -2 - t;
-        members[reg_start[rid] + loc[u]] = u;
+        const int p = reg_start[rid] + loc[u];
+        members[p] = u;
+        member_reg[p] = rid;
         const int j = od<DIR>(O[u], g.n);
-        atomicOr(&rblk[j >> 6].mmask, 1ull << (j & 63));
+        atomicOr(&rblk[j >> kRankShift].mmask, 1u << (j & 31));
     }
 }
 
-// Step-2 tier lists by region size r = members + 1 (r <= 16 needs no list).
-__global__ void tiers_kernel(const int* __restrict__ reg_size, int* tier_list, int q, int med_max,
-                             DevCounters* ctr) {
+// Step-2 tier lists by region size r = members + 1.  A region with a single
+// member m needs no work: m is the only candidate for the minus-infinity
+// vertex (it has neighbours outside R), the propagation from s visits it
+// last, and no vertex lacks an outside neighbour, so lhat(m) = 0 after one
+// propagation.
+__global__ void tiers_kernel(const int* __restrict__ reg_size, const int* __restrict__ reg_start, int* lhat,
+                             int* tier_list, int cap, int q, int med_max, DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
+    int trivial = 0;
     for (long long b = (long long)blockIdx.x * blockDim.x; b < nreg; b += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(b + threadIdx.x);
         const int sz = r < nreg ? reg_size[r] + 1 : 0;
+        if (sz == 2) { lhat[reg_start[r]] = 0; ++trivial; }
+        const bool t16 = sz > 2 && sz <= 16;
+        const int p16 = warp_reserve(&ctr->n_t16, t16);
+        if (t16) tier_list[p16] = r;
+        int* rest = tier_list + cap;
         const bool t32 = sz > 16 && sz <= 32;
-        const bool med = sz > 32 && sz <= med_max;
+        const bool med = sz > 32 && sz <= 128;
+        const bool lrg = sz > 128 && sz <= med_max;
         const bool big = sz > med_max;
         const int p32 = warp_reserve(&ctr->n_t32, t32);
         const int pm = warp_reserve(&ctr->n_med, med);
+        const int pl = warp_reserve(&ctr->n_large, lrg);
         const int pb = warp_reserve(&ctr->n_big, big);
-        if (t32) tier_list[p32] = r;
-        if (med) tier_list[q + pm] = r;
-        if (big) tier_list[2 * q + pb] = r;
+        if (t32) rest[p32] = r;
+        if (med) rest[q + pm] = r;
+        if (lrg) rest[2 * q + pl] = r;
+        if (big) rest[3 * q + pb] = r;
     }
+    if (trivial) atomicMax(&ctr->max_floods, 1);
+    warp_atomic_add64(&ctr->total_floods, trivial);
 }
 
 // Per saddle (run by its head region): order the sibling regions by their
@@ -161,7 +178,7 @@ __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __
         }
         reg_att[r] = total;
         const int j = reg_sod[r];
-        atomicOr(&rblk[j >> 6].smask, 1ull << (j & 63));
+        atomicOr(&rblk[j >> kRankShift].smask, 1u << (j & 31));
         ++my_sad;
     }
     warp_atomic_max(&ctr->max_region, my_max);
@@ -180,11 +197,13 @@ cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaS
     members_count_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.parent, w.owner, w.loc, w.class2reg, w.reg_saddle,
                                               w.reg_size, w.reg_top, w.ctr);
     scan_excl_i32(w, w.reg_size, w.reg_start, &w.ctr->n_regions, g.n / 2 + 1, s);
-    members_fill_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.owner, w.loc, w.reg_start, w.members, w.rblk, w.ctr);
+    members_fill_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.owner, w.loc, w.reg_start, w.members, w.member_reg,
+                                             w.rblk, w.ctr);
     siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.listhead, w.next_w,
                                     w.class2reg, w.reg_place, w.reg_att, w.rblk, w.tier_list, w.class_cap / 2,
                                     local_order_tiny_max(), local_order_med_max(), w.ctr);
-    tiers_kernel<<<B, T, 0, s>>>(w.reg_size, w.tier_list, w.class_cap / 4, local_order_med_max(), w.ctr);
+    tiers_kernel<<<B, T, 0, s>>>(w.reg_size, w.reg_start, w.lhat, w.tier_list, w.class_cap, w.class_cap / 4,
+                                 local_order_med_max(), w.ctr);
     w.launches += 6;
     return cudaGetLastError();
 }

@@ -5,10 +5,10 @@
 // So a non-member at rank j moves to
 //     j - M(j) + A(j)
 // with M(j) the members ranked below j and A(j) the members whose saddle is
-// ranked at or below j.  Both are read from a rank-space bitmap of 64-rank
-// blocks holding the member and saddle bits and their prefix counts (about
-// 0.4 byte per vertex, so it stays in L2), plus the prefix sums of the block
-// sizes per saddle.  A member w of region R at saddle s goes to
+// ranked at or below j.  Both are read from a rank-space bitmap of 32-rank
+// blocks holding the member and saddle bits and their prefix counts (16
+// bytes per block, one vector load, 0.5 byte per vertex, so it stays in L2),
+// plus the prefix sums of the block sizes per saddle.  A member w of region R at saddle s goes to
 //     newrank(s) - attached(s) + offset(R) + lhat(w)
 // and takes g(s) bit for bit.  No global sort is needed.
 #include "lts_internal.cuh"
@@ -27,7 +27,7 @@ __global__ void blk_sums_kernel(const RankBlk* __restrict__ b, int nb, unsigned 
     unsigned long long acc = 0;
     for (int i = 0; i < kPer; ++i) {
         const int k = base + threadIdx.x * kPer + i;
-        if (k < nb) acc += (unsigned long long)__popcll(b[k].mmask) | ((unsigned long long)__popcll(b[k].smask) << 32);
+        if (k < nb) acc += (unsigned long long)__popc(b[k].mmask) | ((unsigned long long)__popc(b[k].smask) << 32);
     }
     s[threadIdx.x] = acc;
     __syncthreads();
@@ -64,7 +64,7 @@ __global__ void blk_apply_kernel(RankBlk* b, int nb, const unsigned long long* _
     unsigned long long acc = 0;
     for (int i = 0; i < kPer; ++i) {
         const int k = base + threadIdx.x * kPer + i;
-        if (k < nb) acc += (unsigned long long)__popcll(b[k].mmask) | ((unsigned long long)__popcll(b[k].smask) << 32);
+        if (k < nb) acc += (unsigned long long)__popc(b[k].mmask) | ((unsigned long long)__popc(b[k].smask) << 32);
     }
     s[threadIdx.x] = acc;
     __syncthreads();
@@ -80,7 +80,7 @@ __global__ void blk_apply_kernel(RankBlk* b, int nb, const unsigned long long* _
         if (k < nb) {
             b[k].mpre = (unsigned)run;
             b[k].spre = (unsigned)(run >> 32);
-            run += (unsigned long long)__popcll(b[k].mmask) | ((unsigned long long)__popcll(b[k].smask) << 32);
+            run += (unsigned long long)__popc(b[k].mmask) | ((unsigned long long)__popc(b[k].smask) << 32);
         }
     }
 }
@@ -94,19 +94,19 @@ __global__ void saddle_index_kernel(const RankBlk* __restrict__ rb, const int* _
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
         if (!reg_head[r]) continue;
         const int j = reg_sod[r];
-        const RankBlk b = rb[j >> 6];
-        const int k = (int)b.spre + __popcll(b.smask & ((1ull << (j & 63)) - 1ull));
+        const RankBlk b = rb[j >> kRankShift];
+        const int k = (int)b.spre + __popc(b.smask & ((1u << (j & 31)) - 1u));
         sad_att[k] = reg_att[r];
     }
 }
 
 __device__ __forceinline__ int new_rank(const RankBlk* __restrict__ rb, const int* __restrict__ cumA, int j) {
-    const RankBlk b = rb[j >> 6];
-    const int bit = j & 63;
-    const unsigned long long lt = (1ull << bit) - 1ull;
-    const unsigned long long le = lt | (1ull << bit);
-    const int M = (int)b.mpre + __popcll(b.mmask & lt);
-    const int A = __ldg(cumA + (int)b.spre + __popcll(b.smask & le));
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(rb) + (j >> kRankShift));   // mmask, smask, mpre, spre
+    const int bit = j & 31;
+    const unsigned lt = (1u << bit) - 1u;
+    const unsigned le = lt | (1u << bit);
+    const int M = (int)b.z + __popc(b.x & lt);
+    const int A = __ldg(cumA + (int)b.w + __popc(b.y & le));
     return j - M + A;
 }
 
@@ -130,28 +130,31 @@ __global__ void __launch_bounds__(kT) stream_kernel(int n, int* O, const RankBlk
         O[i] = od<DIR>(new_rank(rb, cumA, od<DIR>(O[i], n)), n);
 }
 
+// one thread per member (CSR position); the first threads also reset the
+// saddles' claims
 template <int DIR>
 __global__ void members_place_kernel(int n, int* O, float* gout, int* owner, const int* __restrict__ members,
-                                     const int* __restrict__ lhat, const int* __restrict__ reg_start,
-                                     const int* __restrict__ reg_size, const int* __restrict__ reg_saddle,
-                                     const int* __restrict__ reg_sod, const int* __restrict__ reg_place,
+                                     const int* __restrict__ member_reg, const int* __restrict__ lhat,
+                                     const int* __restrict__ reg_saddle, const int* __restrict__ reg_sod,
+                                     const int* __restrict__ reg_place, const int* __restrict__ reg_start,
                                      const RankBlk* __restrict__ rb, const int* __restrict__ cumA,
                                      const DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+    const int total = nreg > 0 ? reg_start[nreg] : 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
+        const int r = member_reg[p];
+        const int w = members[p];
         const int s = reg_saddle[r];
-        const int base = new_rank(rb, cumA, reg_sod[r]) + reg_place[r];
-        const float gs = gout[s];
-        const int st0 = reg_start[r], m = reg_size[r];
-        for (int i = 0; i < m; ++i) {
-            const int w = members[st0 + i];
-            O[w] = od<DIR>(base + lhat[st0 + i], n);
-            gout[w] = gs;
-            owner[w] = -1;
-        }
-        owner[s] = -1;
+        O[w] = od<DIR>(new_rank(rb, cumA, reg_sod[r]) + reg_place[r] + lhat[p], n);
+        gout[w] = gout[s];
+        owner[w] = -1;
     }
+}
+
+__global__ void saddles_reset_kernel(int* owner, const int* __restrict__ reg_saddle, const DevCounters* ctr) {
+    const int nreg = ctr->n_regions;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) owner[reg_saddle[r]] = -1;
 }
 
 }  // namespace
@@ -167,10 +170,11 @@ cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms
     saddle_index_kernel<<<sms * 8, 256, 0, s>>>(w.rblk, w.reg_head, w.reg_sod, w.reg_att, w.sad_att, w.ctr);
     scan_excl_i32(w, w.sad_att, w.cumA, &w.ctr->n_saddles, g.n / 2 + 1, s);
     stream_kernel<DIR><<<sms * 8, kT, 0, s>>>(g.n, O, w.rblk, w.cumA, w.ctr);
-    members_place_kernel<DIR><<<sms * 8, 128, 0, s>>>(g.n, O, gout, w.owner, w.members, w.lhat, w.reg_start,
-                                                      w.reg_size, w.reg_saddle, w.reg_sod, w.reg_place, w.rblk,
+    members_place_kernel<DIR><<<sms * 8, 256, 0, s>>>(g.n, O, gout, w.owner, w.members, w.member_reg, w.lhat,
+                                                      w.reg_saddle, w.reg_sod, w.reg_place, w.reg_start, w.rblk,
                                                       w.cumA, w.ctr);
-    w.launches += 6;
+    saddles_reset_kernel<<<sms * 4, 256, 0, s>>>(w.owner, w.reg_saddle, w.ctr);
+    w.launches += 7;
     return cudaGetLastError();
 }
 
