@@ -119,6 +119,47 @@ const char* lts_last_error(const lts_ctx* ctx);
 /* Frees the context and its workspace; NULL is ignored. */
 void lts_destroy(lts_ctx* ctx);
 
+/* ---- Order field with no allocation at call time -------------------------
+ * The paper has no counterpart to this entry point: it is a service for
+ * callers that cannot allocate device memory when they call, e.g. a caller
+ * that has handed the device's free memory to its own pool allocator (so a
+ * cudaMalloc would fail), or one on a latency-bound path where cudaMalloc and
+ * cudaFree (which waits for the whole device) are not acceptable.
+ *
+ * It computes the order field of Sec. 4.1 alone, i.e. O(v) = the rank of
+ * vertex v when the vertices are sorted by (f(v), v), with -0.0 == +0.0;
+ * the result equals d_out_order of lts_simplify with every vertex
+ * authorized.  It runs the same sort kernels as lts_simplify, but its scratch
+ * is a static device array inside the library, sized for at most
+ * LTS_ORDER_STATIC_MAX_VERTICES vertices (16.5 MiB), which CUDA allocates
+ * once per device when the library's module loads there.  The call makes
+ * no cudaMalloc/cudaFree and needs no context.
+ *
+ *   device       CUDA device to run on; made current for the call, and the
+ *                previously current device is restored before returning
+ *   g            grid (see conventions); N = X*Y*Z <= LTS_ORDER_STATIC_MAX_VERTICES
+ *   d_field      device float32[N] on `device`, the input f (not modified)
+ *   d_order      device int32[N] on `device`: O, a permutation of 0..N-1;
+ *                must not overlap d_field
+ *   cuda_stream  a cudaStream_t of `device` (NULL: the legacy default stream)
+ *   err, err_len if err is non-NULL, receives a message on error ("" on success)
+ *
+ * Set-up: the first call on each device looks up the scratch's address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins on the device.
+ * The call enqueues its kernels on cuda_stream and waits for them (one small
+ * read of the status word), so on return d_order is final.
+ * Calls on one device share the scratch: calls that overlap in time (from
+ * several host threads, or on several streams) race and corrupt each other's
+ * results, so serialize them.
+ * Errors: LTS_ERR_ARG (invalid grid, N > LTS_ORDER_STATIC_MAX_VERTICES, NULL
+ * or overlapping pointers, device outside [0, 256)), LTS_ERR_NAN, LTS_ERR_CUDA,
+ * LTS_ERR_TIMEOUT (a bounded wait of the sort expired). */
+#define LTS_ORDER_STATIC_MAX_VERTICES (1LL << 20)
+
+lts_status lts_order_field_static(int device, const lts_grid* g, const float* d_field, int32_t* d_order,
+                                  void* cuda_stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

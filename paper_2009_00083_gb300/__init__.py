@@ -14,14 +14,15 @@ import os
 
 __all__ = [
     "LtsGrid", "LtsStats", "LtsError", "Context", "lts_create", "lts_simplify", "lts_destroy",
-    "lts_workspace_bytes", "lts_last_error", "library_path", "load", "simplify",
-    "MODE_MIN", "MODE_MAX", "MODE_BOTH",
+    "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "library_path", "load", "simplify",
+    "MODE_MIN", "MODE_MAX", "MODE_BOTH", "ORDER_STATIC_MAX_VERTICES",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "liblts.so")
 
 MODE_MIN, MODE_MAX, MODE_BOTH = 1, 2, 3
+ORDER_STATIC_MAX_VERTICES = 1 << 20   # LTS_ORDER_STATIC_MAX_VERTICES
 _MODES = {"min": MODE_MIN, "max": MODE_MAX, "both": MODE_BOTH, 1: 1, 2: 2, 3: 3}
 STATUS = {0: "LTS_OK", 1: "LTS_ERR_ARG", 2: "LTS_ERR_NAN", 3: "LTS_ERR_NO_AUTHORIZED", 4: "LTS_ERR_OOM",
           5: "LTS_ERR_CUDA", 6: "LTS_ERR_TIMEOUT", 7: "LTS_ERR_INTERNAL"}
@@ -89,6 +90,9 @@ def load():
         lib.lts_last_error.restype = ctypes.c_char_p
         lib.lts_destroy.argtypes = [P]
         lib.lts_destroy.restype = None
+        lib.lts_order_field_static.argtypes = [ctypes.c_int, ctypes.POINTER(LtsGrid), P, P, P, ctypes.c_char_p,
+                                               ctypes.c_size_t]
+        lib.lts_order_field_static.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -134,6 +138,14 @@ def lts_last_error(ctx) -> str:
 
 def lts_destroy(ctx) -> None:
     load().lts_destroy(ctx)
+
+
+def lts_order_field_static(device: int, grid: LtsGrid, d_field: int, d_order: int, cuda_stream: int = 0):
+    """Order field with the library's static scratch (no allocation); returns (status, message)."""
+    buf = ctypes.create_string_buffer(256)
+    code = load().lts_order_field_static(int(device), ctypes.byref(grid), ctypes.c_void_p(d_field),
+                                         ctypes.c_void_p(d_order), ctypes.c_void_p(cuda_stream), buf, len(buf))
+    return int(code), buf.value.decode()
 
 
 # ---- convenience wrapper over torch tensors ----

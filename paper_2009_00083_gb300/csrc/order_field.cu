@@ -11,6 +11,9 @@
 // DRAM sector each): it appends the (id, rank) pairs to bins of 2^22 ids,
 // and an inverse pass then writes O bin by bin, so that the random writes of
 // one bin stay inside a 16 MB window of O that L2 merges into full sectors.
+#include <cstdio>
+#include <mutex>
+
 #include "lts_internal.cuh"
 
 namespace lts {
@@ -360,3 +363,146 @@ cudaError_t build_authbits(Work& w, const Geom& g, const int* ids, long long nid
 }
 
 }  // namespace lts
+
+// ---------------------------------------------------------------------------
+// lts_order_field_static: the order field (the kernels above) on a scratch
+// buffer that is a static device array of this file, for callers that cannot
+// allocate device memory when they call (see include/lts.h).  Nothing here is
+// used by lts_simplify.
+// ---------------------------------------------------------------------------
+namespace {
+
+using lts::kTile;
+constexpr long long kStMax = LTS_ORDER_STATIC_MAX_VERTICES;
+constexpr int kStTiles = (int)((kStMax + kTile - 1) / kTile);
+constexpr size_t kStAlign(size_t b) { return (b + 255) & ~(size_t)255; }
+// Scratch layout (byte offsets).  The first kStZero bytes must start at zero
+// on every call: the look-back words (epoch 0 = "not yet published"), the
+// digit histograms (accumulated by atomics), the tile tickets of the four
+// passes and the error word.  Everything after them is fully written before
+// it is read.
+constexpr size_t kStLook = 0;                                           // u64[tiles * 256]
+constexpr size_t kStHist = kStLook + (size_t)kStTiles * 256 * 8;         // u32[4 * 256]
+constexpr size_t kStTicket = kStHist + 1024 * 4;                        // u32[4]
+constexpr size_t kStErr = kStTicket + 16;                               // int32
+constexpr size_t kStZero = kStAlign(kStErr + 4);
+constexpr size_t kStOff = kStZero;                                      // u32[4 * 256] digit starts
+constexpr size_t kStBin = kStAlign(kStOff + 1024 * 4);                  // u32 bin cursors
+constexpr size_t kStKeyA = kStAlign(kStBin + 4 * (((size_t)kStMax >> lts::kBinShift) + 1));
+constexpr size_t kStValA = kStKeyA + 4 * (size_t)kStMax;
+constexpr size_t kStKeyB = kStValA + 4 * (size_t)kStMax;                // also takes the copy of f
+constexpr size_t kStValB = kStKeyB + 4 * (size_t)kStMax;
+constexpr size_t kStBytes = kStValB + 4 * (size_t)kStMax;
+static_assert(kStMax <= (1LL << lts::kBinShift) * 256, "bin cursors");
+
+constexpr int kStMaxDevices = 256;
+std::mutex st_setup_mu;
+void* st_base[kStMaxDevices] = {};
+
+lts_status st_fail(char* err, size_t len, lts_status s, const char* msg) {
+    if (err && len) std::snprintf(err, len, "%s", msg);
+    return s;
+}
+
+}  // namespace
+
+// 16.5 MiB at LTS_ORDER_STATIC_MAX_VERTICES = 2^20.  CUDA allocates it once
+// per device, when this library's module loads there.
+static __device__ __align__(256) unsigned long long lts_order_static_scratch[kStBytes / 8];
+
+extern "C" lts_status lts_order_field_static(int device, const lts_grid* gr, const float* d_field,
+                                             int32_t* d_order, void* cuda_stream, char* err, size_t err_len) {
+    using namespace lts;
+    if (err && err_len) err[0] = '\0';
+    if (!gr || (gr->ndim != 2 && gr->ndim != 3) || gr->dims[0] < 2 || gr->dims[1] < 2 ||
+        (gr->ndim == 3 && gr->dims[2] < 2) || (gr->ndim == 2 && gr->dims[2] != 1) ||
+        gr->dims[0] >= (1LL << 31) || gr->dims[1] >= (1LL << 31) || gr->dims[2] >= (1LL << 31))
+        return st_fail(err, err_len, LTS_ERR_ARG, "invalid grid");
+    const long long n = gr->dims[0] * gr->dims[1] * gr->dims[2];
+    if (n > kStMax) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "grid has %lld vertices; lts_order_field_static takes at most %lld "
+                      "(LTS_ORDER_STATIC_MAX_VERTICES): use lts_simplify", n, kStMax);
+        return st_fail(err, err_len, LTS_ERR_ARG, msg);
+    }
+    if (!d_field || !d_order) return st_fail(err, err_len, LTS_ERR_ARG, "null data pointer");
+    {
+        const char* a = reinterpret_cast<const char*>(d_field);
+        const char* b = reinterpret_cast<const char*>(d_order);
+        if (a < b + 4 * n && b < a + 4 * n) return st_fail(err, err_len, LTS_ERR_ARG, "d_order overlaps d_field");
+    }
+    if (device < 0 || device >= kStMaxDevices) return st_fail(err, err_len, LTS_ERR_ARG, "invalid device");
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return st_fail(err, err_len, LTS_ERR_CUDA, "cudaGetDevice failed");
+    if (cudaSetDevice(device) != cudaSuccess) return st_fail(err, err_len, LTS_ERR_CUDA, "cudaSetDevice failed");
+    struct Restore {
+        int d;
+        ~Restore() { cudaSetDevice(d); }
+    } restore{prev};
+
+    // Set-up, once per device, with that device current: the scratch's
+    // device address.  The first call on a device does it.
+    char* base;
+    {
+        std::lock_guard<std::mutex> lock(st_setup_mu);
+        if (!st_base[device]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, lts_order_static_scratch);
+            if (e != cudaSuccess || !p) {
+                char msg[160];
+                std::snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the static scratch failed: %s",
+                              cudaGetErrorString(e));
+                return st_fail(err, err_len, LTS_ERR_CUDA, msg);
+            }
+            st_base[device] = p;
+        }
+        base = static_cast<char*>(st_base[device]);
+    }
+
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    unsigned long long* look = reinterpret_cast<unsigned long long*>(base + kStLook);
+    unsigned* hist = reinterpret_cast<unsigned*>(base + kStHist);
+    unsigned* ticket = reinterpret_cast<unsigned*>(base + kStTicket);
+    int* st = reinterpret_cast<int*>(base + kStErr);
+    unsigned* goff = reinterpret_cast<unsigned*>(base + kStOff);
+    unsigned* bins = reinterpret_cast<unsigned*>(base + kStBin);
+    unsigned* keyA = reinterpret_cast<unsigned*>(base + kStKeyA);
+    unsigned* valA = reinterpret_cast<unsigned*>(base + kStValA);
+    unsigned* keyB = reinterpret_cast<unsigned*>(base + kStKeyB);
+    unsigned* valB = reinterpret_cast<unsigned*>(base + kStValB);
+    const int ni = (int)n;
+    const int tiles = (int)((n + kTile - 1) / kTile);
+
+    cudaMemsetAsync(base, 0, kStZero, s);
+    {
+        const long long nch = (n + 15) / 16;
+        const int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, 152LL * 8);
+        hist_copy_kernel<<<blocks, kThreads, 0, s>>>(d_field, reinterpret_cast<float*>(keyB), ni, hist, st);
+    }
+    digit_offsets_kernel<<<4, 256, 0, s>>>(hist, goff);
+    const int nbins = (int)(((unsigned)ni + (1u << kBinShift) - 1) >> kBinShift);
+    bin_init_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(bins, nbins);
+    // the look-back words were zeroed above, so the passes take epochs 1..4
+    onesweep_kernel<true, false><<<tiles, kThreads, 0, s>>>(d_field, nullptr, nullptr, keyA, valA, nullptr, ni, 0,
+                                                            goff, look, ticket, 1u, st);
+    onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, keyA, valA, keyB, valB, nullptr, ni, 8,
+                                                             goff + 256, look, ticket + 1, 2u, st);
+    onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, keyB, valB, keyA, valA, nullptr, ni, 16,
+                                                             goff + 512, look, ticket + 2, 3u, st);
+    onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, keyA, valA, keyB, valB, bins, ni, 24,
+                                                            goff + 768, look, ticket + 3, 4u, st);
+    inverse_kernel<<<152 * 8, 256, 0, s>>>(keyB, valB, d_order, ni);
+    cudaError_t e = cudaGetLastError();
+    int h_status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, st, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "CUDA error: %s", cudaGetErrorString(e));
+        return st_fail(err, err_len, LTS_ERR_CUDA, msg);
+    }
+    if (h_status == LTS_ERR_NAN) return st_fail(err, err_len, LTS_ERR_NAN, "the field holds a NaN");
+    if (h_status == LTS_ERR_TIMEOUT) return st_fail(err, err_len, LTS_ERR_TIMEOUT, "a sort look-back wait expired");
+    if (h_status != 0) return st_fail(err, err_len, LTS_ERR_INTERNAL, "unexpected device status");
+    return LTS_OK;
+}

@@ -25,7 +25,8 @@ def lib():
 
 def test_header_declares_the_boundary():
     assert declared_entry_points() == sorted(
-        ["lts_create", "lts_workspace_bytes", "lts_simplify", "lts_last_error", "lts_destroy"])
+        ["lts_create", "lts_workspace_bytes", "lts_simplify", "lts_last_error", "lts_destroy",
+         "lts_order_field_static"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -48,3 +49,20 @@ def test_argument_checks_need_no_device(lib):
     bad.ndim = 4
     assert lts.lts_workspace_bytes(bad) == 0
     assert lts.load().lts_simplify(None, ctypes.byref(g), None, None, 0, 3, None, None, None) == 1
+
+
+def test_static_order_field_rejects_oversize_grids_before_any_device_call(lib):
+    import paper_2009_00083_gb300 as lts
+
+    assert lts.ORDER_STATIC_MAX_VERTICES == 1 << 20
+    code, msg = lts.lts_order_field_static(0, lts.grid_of_shape((1025, 1024)), 16, 1 << 40)
+    assert code == 1 and "at most 1048576" in msg, msg
+    code, msg = lts.lts_order_field_static(0, lts.grid_of_shape((65, 128, 128)), 16, 1 << 40)
+    assert code == 1 and "1064960 vertices" in msg, msg
+    code, msg = lts.lts_order_field_static(0, lts.grid_of_shape((8, 8)), 0, 1 << 40)
+    assert code == 1 and "null" in msg
+    code, msg = lts.lts_order_field_static(0, lts.grid_of_shape((8, 8)), 1 << 40, (1 << 40) + 128)
+    assert code == 1 and "overlaps" in msg
+    bad = lts.LtsGrid()
+    bad.ndim = 3
+    assert lts.lts_order_field_static(0, bad, 16, 1 << 40)[0] == 1
