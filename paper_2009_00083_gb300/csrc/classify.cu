@@ -25,8 +25,7 @@ template <int DIR, int TZT>
 __global__ void __launch_bounds__(kCT) classify_kernel(Geom g, const int* __restrict__ O,
                                                        const unsigned* __restrict__ authbits, int* __restrict__ U,
                                                        int* __restrict__ parent, int* __restrict__ wait_v,
-                                                       int* __restrict__ cnt, int* __restrict__ listhead,
-                                                       int* __restrict__ next_w, int* __restrict__ spill_n,
+                                                       int* __restrict__ spill_n, int* __restrict__ sib_head,
                                                        int cap, DevCounters* ctr) {
     constexpr int SX = TX + 2, SY = TY + 2, SZ = TZT + 2;
     __shared__ int S[SZ][SY][SX];            // order with halo
@@ -131,10 +130,8 @@ __global__ void __launch_bounds__(kCT) classify_kernel(Geom g, const int* __rest
             U[cl] = vfirst + i;
             parent[cl] = cl;
             wait_v[cl] = -1;
-            cnt[cl] = 0;
-            listhead[cl] = -1;
-            next_w[cl] = -1;
-            spill_n[cl] = 0;
+            spill_n[cl] = -1;            // never spilled: a queue rebuilt from the seed
+            sib_head[cl] = -1;
         }
         __syncthreads();
     }
@@ -149,11 +146,11 @@ cudaError_t classify(Work& w, const Geom& g, const int* O, cudaStream_t s) {
                             (g.ndim == 3 ? (g.Z + TZ - 1) / TZ : 1);
     const int blocks = (int)std::min<long long>(tiles, 152LL * 8);
     if (g.ndim == 3)
-        classify_kernel<DIR, TZ><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v, w.cnt, w.listhead,
-                                                        w.next_w, w.spill_n, w.class_cap, w.ctr);
+        classify_kernel<DIR, TZ><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v,
+                                                        w.spill_n, w.sib_head, w.class_cap, w.ctr);
     else
-        classify_kernel<DIR, 1><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v, w.cnt, w.listhead,
-                                                       w.next_w, w.spill_n, w.class_cap, w.ctr);
+        classify_kernel<DIR, 1><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v,
+                                                       w.spill_n, w.sib_head, w.class_cap, w.ctr);
     w.launches += 1;
     return cudaGetLastError();
 }

@@ -42,7 +42,7 @@ Sizes sizes_for(long long n, int sms) {
     z.half = n / 2 + 1;
     z.lanes = propagate_lanes(sms);
     z.tiles = (n + 4095) / 4096;
-    z.log_cap = n + propagate_log_slack((int)z.lanes);
+    z.log_cap = n + z.half + propagate_log_slack((int)z.lanes);
     z.spill_cap = std::min<long long>(4 * n + propagate_spill_slack((int)z.lanes), (1LL << 31) - 1);
     z.heap_cap = 2 * n + propagate_heap_slack((int)z.lanes);
     z.lo_cap = n + z.half;
@@ -58,6 +58,8 @@ size_t bytes_for(const Sizes& z) {
     b += ((size_t)z.n + 31) / 32 * 4;               // authorized bitmap
     b += 2 * 4 * (size_t)z.n + 8 * (size_t)z.n;     // owner, loc, qmark
     b += 8 * 4 * (size_t)z.half;                    // U and class records
+    b += 16 * (size_t)z.half;                       // task records
+    b += 4 * (size_t)z.n;                           // saddle arrival counters
     b += 4 * (size_t)z.spill_cap + 8 * (size_t)z.heap_cap + 4 * (size_t)z.log_cap;
     b += 11 * 4 * (size_t)z.half;                   // region records
     b += 2 * 4 * (size_t)z.n;                       // members, lhat
@@ -113,6 +115,7 @@ lts_status cuda_fail(lts_ctx* c, cudaError_t e, const char* where) {
 cudaError_t clean_workspace(lts_ctx* c) {
     Work& w = c->w;
     cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)w.nmax, c->stream);
+    cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)w.nmax, c->stream);
     cudaMemsetAsync(w.sort_status, 0, (size_t)w.max_tiles * 256 * sizeof(unsigned long long), c->stream);
     w.epoch = 0;
     return cudaGetLastError();
@@ -177,7 +180,8 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     ok = ok && dev_alloc(c, &w.authbits, (z.n + 31) / 32);
     ok = ok && dev_alloc(c, &w.owner, z.n) && dev_alloc(c, &w.loc, z.n) && dev_alloc(c, &w.qmark, z.n);
     ok = ok && dev_alloc(c, &w.U, z.half) && dev_alloc(c, &w.parent, z.half) && dev_alloc(c, &w.wait_v, z.half) &&
-         dev_alloc(c, &w.cnt, z.half) && dev_alloc(c, &w.listhead, z.half) && dev_alloc(c, &w.next_w, z.half) &&
+         dev_alloc(c, &w.cnt, z.n) && dev_alloc(c, &w.tasks, z.half) &&
+         dev_alloc(c, &w.sib_head, z.half) && dev_alloc(c, &w.sib_next, z.half) &&
          dev_alloc(c, &w.spill_base, z.half) && dev_alloc(c, &w.spill_n, z.half);
     ok = ok && dev_alloc(c, &w.spill_pool, z.spill_cap) && dev_alloc(c, &w.heap_pool, z.heap_cap) &&
          dev_alloc(c, &w.vlog, z.log_cap);
@@ -202,6 +206,7 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     for (auto& e : c->ev) cudaEventCreate(&e);
     c->events = true;
     cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, c->stream);
+    cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)z.n, c->stream);
     cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, c->stream);
     w.pass_tag = 0;

@@ -98,7 +98,7 @@ struct DevCounters {
     int n_med;             // regions for the small dense warp tier of step 2
     int n_large;           // regions for the large dense warp tier of step 2
     int n_big;             // regions for the HBM tier of step 2
-    int pad;
+    int n_tasks;           // propagation tasks left after the first step
 };
 
 // Per-pass statistics accumulated into the host stats.
@@ -138,7 +138,10 @@ struct Work {
     unsigned int pass_tag;
     int* loc;                            // per vertex: local index within its region
     int* U;                              // unauthorized extrema
-    int* parent; int* wait_v; int* cnt; int* listhead; int* next_w;
+    int* parent; int* wait_v;            // per class
+    int* sib_head; int* sib_next;        // per class: regions listed under the claimer of their saddle
+    int4* tasks;                         // propagation tasks after the first step
+    int* cnt;                            // per vertex: arrival counter of a saddle
     int* spill_base; int* spill_n;
     int* spill_pool; long long spill_cap;
     unsigned long long* heap_pool; long long heap_cap;

@@ -1,28 +1,45 @@
 // Step 1 with hill chains (Sec. 4.2 step 1, Sec. 4.3, Sec. 4.4): one
-// superlevel set propagation per unauthorized maximum, all in one persistent
-// kernel.
+// superlevel set propagation per unauthorized maximum (a "class").
 //
-// Each propagation (a "class") is run by a team of lanes (a whole warp, so
-// that no two propagations share an instruction stream): lane q handles neighbour q of the
-// popped vertex, so the loads of all neighbours go out in one round trip and
-// every branch is uniform within the team.  The priority queue of the class
-// is a top-K frontier in the team's registers (E slots per lane), popped with
-// a team max-reduction; entries that do not fit go to a per-team binary heap
-// in an HBM pool.  Popping v:
+// The first step of every propagation is data parallel and runs as two
+// thread-per-class kernels: the seed (a maximum: nothing else can reach it)
+// is claimed with a plain store and its highest neighbour u is found; then
+// every class pops u.  All its neighbours are lower than the seed, so u is
+// the first vertex any schedule pops.  If the seed is the only higher
+// neighbour of u, the class claims u and goes on in the engine below.
+// Otherwise u is a saddle (an arrival, see below), and most classes stop
+// there for good.  The queue of a class stopped at its first pop is the
+// seed's neighbourhood minus u, so it is rebuilt when needed instead of
+// spilled.  These arrivals cross a kernel boundary before anything reads
+// them, so they need no memory fence.  Each class that goes on becomes a
+// task record (class, u, Od(u), seed or -1 after a meeting).
+//
+// The persistent engine then runs the classes that go on.  Each is run by a
+// team of lanes (a whole warp, so that no two propagations share an
+// instruction stream): lane q handles neighbour q of the popped vertex, so the loads of all
+// neighbours go out in one round trip and every branch is uniform within the
+// team.  The priority queue of the class is a top-K frontier in the team's
+// registers (E slots per lane), popped with a team max-reduction; entries that
+// do not fit go to a per-team binary heap in an HBM pool.  Popping v:
 //   - v already in the class: skip;
 //   - claim v (atomicCAS on owner[v]); the vertex log records every claim;
 //   - k = higher neighbours of v in the class, h = all higher neighbours;
 //     k == h: v is regular for the class, queue its lower neighbours;
-//   - otherwise v is a saddle for the class (an arrival): the class links
-//     itself into v's wait list (headed by the class that claimed v), copies
-//     its queue to the spill pool, and adds k to the arrival counter of v.
-//     The arrival that brings the counter to h is the last one: it unites
-//     every class waiting at v with itself (union-find), melds their spilled
-//     queues into its own and continues below v.  Any other arrival stops.
+//   - otherwise v is a saddle for the class (an arrival): the class copies
+//     its queue to the spill pool and adds k to the arrival counter of v.
+//     The arrival that brings the counter to h is the last one.  Every
+//     higher neighbour of v then belongs to a class waiting at v, so the
+//     waiting classes are the union-find roots of those neighbours' owners,
+//     found by the lanes in parallel (no wait list).  The last arrival
+//     unites them with itself, melds their queues into its own and
+//     continues below v.  Any other arrival stops.
 // A class thus only passes a saddle once every higher neighbour belongs to a
 // class that has arrived there, so the regions do not depend on the order in
 // which teams run.  Nothing here waits on another team: a stopped class just
-// ends its task, and the kernel ends when every seed has been taken.
+// ends its task, and the kernel ends when every task has been taken.
+// Arrival counters are indexed by the saddle vertex: once a saddle is
+// released nothing touches its counter again in the pass, so the releaser
+// resets it with a plain store.
 // Decisions that read shared mutable state (owner[], parent[]) are taken by
 // one lane and broadcast, so a team never diverges.
 #include <climits>
@@ -52,8 +69,6 @@ struct PropArgs {
     int* parent;
     int* wait_v;
     int* cnt;
-    int* listhead;
-    int* next_w;
     int* spill_base;
     int* spill_n;
     int* spill_pool;
@@ -62,6 +77,7 @@ struct PropArgs {
     long long heap_cap;
     int* vlog;
     long long log_cap;
+    const int4* tasks;           // (class, u, Od(u), seed; -1 after a meeting at u)
     DevCounters* ctr;
 };
 
@@ -76,10 +92,6 @@ __device__ __forceinline__ int find_root(int* parent, int x) {
         __stcg(parent + x, gp);
         x = gp;
     }
-}
-
-__device__ __forceinline__ bool in_class(int* parent, int ow, int c) {
-    return ow >= 0 && (ow == c || find_root(parent, ow) == c);
 }
 
 // Neighbour q of (x,y,z) for a compile-time neighbour count NN.
@@ -239,17 +251,109 @@ __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, cons
     return ok;
 }
 
+// The queue of a class that stopped at its first pop u: the neighbours of its
+// seed m but u (marked as queued by the class `mark`).
 template <int DIR, int NN>
-__global__ void __launch_bounds__(kThreads, 12) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
+__device__ __forceinline__ bool rebuild_first_queue(TeamState<NN>& T, const Geom& g, const int* __restrict__ O, int m,
+                                                    int u, unsigned long long mark, const PropArgs& a, int tl) {
+    int x, y, z;
+    coords_of(g, m, x, y, z);
+    const int nb = tl < NN ? nbr_q<NN>(g, x, y, z, tl) : -1;
+    const bool cand = nb >= 0 && nb != u;
+    int key = 0;
+    if (cand) {
+        key = od<DIR>(__ldg(O + nb), g.n);
+        __stcg(a.qmark + nb, mark);
+    }
+    return insert_batch(T, cand, key, nb, a);
+}
+
+// First step, part 1 (thread per class c): claim the seed, log it, and find
+// its highest neighbour u (kept in wait_v[c]).  Log slots [0, nU) hold the
+// seeds and [nU, 2 nU) the first pops; the engine's log starts at 2 nU.
+template <int DIR, int NN>
+__global__ void __launch_bounds__(256) seed_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
+    DevCounters* ctr = a.ctr;
+    if (failed(&ctr->status)) return;
+    const int nU = ctr->n_unauth;
+    if (nU > 0 && ctr->n_auth_ext == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&ctr->status, LTS_ERR_NO_AUTHORIZED);
+        return;
+    }
+    if (2LL * nU > a.log_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&ctr->status, LTS_ERR_OOM);
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->log_cursor = 2 * nU;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nU; c += gridDim.x * blockDim.x) {
+        const int m = __ldg(a.U + c);
+        a.owner[m] = c;
+        a.vlog[c] = m;
+        int x, y, z;
+        coords_of(g, m, x, y, z);
+        int best = -1, u = -1;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const int nb = nbr_q<NN>(g, x, y, z, q);
+            if (nb >= 0) {
+                const int k = od<DIR>(__ldg(O + nb), g.n);
+                if (k > best) { best = k; u = nb; }
+            }
+        }
+        a.wait_v[c] = u;
+    }
+}
+
+// First step, part 2 (thread per class c): pop u = wait_v[c].  If the seed
+// is u's only higher neighbour, c claims u and becomes an engine task.
+// Otherwise c arrives at u with k = 1 (its one vertex, the seed; spill_n[c]
+// stays -1: its queue is rebuilt from the seed); the arrival that completes
+// u's count makes a task that melds every class waiting at u.  The others
+// stop here.
+template <int DIR, int NN>
+__global__ void __launch_bounds__(256) first_pop_kernel(Geom g, const int* __restrict__ O, PropArgs a, int4* tasks) {
+    DevCounters* ctr = a.ctr;
+    if (failed(&ctr->status)) return;
+    const int nU = ctr->n_unauth;
+    const int lane = threadIdx.x & 31;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < nU; b += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(b + threadIdx.x);
+        int4 task = make_int4(-1, 0, 0, 0);
+        if (c < nU) {
+            const int u = a.wait_v[c];
+            const int prev = atomicCAS(a.owner + u, -1, c);
+            a.vlog[nU + c] = prev == -1 ? u : -1;
+            int x, y, z;
+            coords_of(g, u, x, y, z);
+            const int ku = od<DIR>(__ldg(O + u), g.n);
+            int h = 0;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                const int nb = nbr_q<NN>(g, x, y, z, q);
+                if (nb >= 0 && od<DIR>(__ldg(O + nb), g.n) > ku) ++h;
+            }
+            if (h == 1) {
+                if (prev == -1) task = make_int4(c, u, ku, __ldg(a.U + c));
+                else set_status(&ctr->status, LTS_ERR_INTERNAL);   // only the seed's class can reach u
+            } else if (atomicAdd(a.cnt + u, 1) + 1 == h) {
+                task = make_int4(c, u, ku, -1);
+            }
+        }
+        const unsigned want = __ballot_sync(0xffffffffu, task.x >= 0);
+        int base = 0;
+        if (lane == 0 && want) base = atomicAdd(&ctr->n_tasks, __popc(want));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (task.x >= 0) tasks[base + __popc(want & ((1u << lane) - 1u))] = task;
+    }
+}
+
+template <int DIR, int NN>
+__global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
     constexpr int TS = TeamCfg<NN>::TS, E = TeamCfg<NN>::E;
     DevCounters* ctr = a.ctr;
     int* st = &ctr->status;
     if (failed(st)) return;
-    const int nU = *(volatile int*)&ctr->n_unauth;
-    if (nU > 0 && *(volatile int*)&ctr->n_auth_ext == 0) {
-        if (threadIdx.x == 0) set_status(st, LTS_ERR_NO_AUTHORIZED);
-        return;
-    }
+    const int nT = *(volatile int*)&ctr->n_tasks;
     TeamState<NN> T;
     T.lane = threadIdx.x & 31;
     T.tb = T.lane & ~(TS - 1);
@@ -263,96 +367,108 @@ __global__ void __launch_bounds__(kThreads, 12) propagate_kernel(Geom g, const i
     for (int e = 0; e < E; ++e) { T.sk[e] = -1; T.sv[e] = 0; }
 
     // team-leader state
-    int seed_lo = 0, seed_hi = 0;
+    int task_lo = 0, task_hi = 0;
     long long log_pos = 0, log_end = 0;
     long long sp_pos = 0, sp_end = 0;
     int c = -1;
     bool merged = false;     // c has absorbed other classes: membership needs find_root
 
     for (;;) {
-        if (c < 0) {                                   // take the next seed
-            int nc = -1;
+        int v, kv;
+        bool resumed = false;    // v is the first pop of a task, already owned by the class
+        if (c < 0) {                                   // take the next task
+            int4 t = make_int4(-1, 0, 0, 0);
             if (leader) {
-                if (seed_lo == seed_hi) {
-                    // guided batches: large while many seeds remain, single ones at the end
-                    const int rem = nU - *(volatile int*)&ctr->seed_cursor;
+                if (task_lo == task_hi) {
+                    // guided batches: large while many tasks remain, single ones at the end
+                    const int rem = nT - *(volatile int*)&ctr->seed_cursor;
                     const int nwarps = gridDim.x * (blockDim.x / 32);
                     const int bsz = max(1, min(kSeedBatch, rem / (4 * nwarps)));
                     const int b = atomicAdd(&ctr->seed_cursor, bsz);
-                    seed_lo = b;
-                    seed_hi = min(b + bsz, nU);
+                    task_lo = b;
+                    task_hi = min(b + bsz, nT);
                 }
-                if (seed_lo < seed_hi && !failed(st)) nc = seed_lo++;
+                if (task_lo < task_hi && !failed(st)) t = __ldcg(a.tasks + task_lo++);
             }
-            nc = __shfl_sync(T.tmask, nc, T.tb);
-            if (nc < 0) break;
-            c = nc;
-            merged = false;
+            c = __shfl_sync(T.tmask, t.x, T.tb);
+            if (c < 0) break;
+            const int u = __shfl_sync(T.tmask, t.y, T.tb);
+            kv = __shfl_sync(T.tmask, t.z, T.tb);
+            const int seed = __shfl_sync(T.tmask, t.w, T.tb);
 #pragma unroll
             for (int e = 0; e < E; ++e) T.sk[e] = -1;
             T.ov.n = 0; T.ovn = 0; T.ov_top = -1;
-            // The seed is a maximum: no other class can reach it (classes only queue
-            // lower neighbours) and all its neighbours are lower, so it is claimed
-            // with a plain store and every neighbour is queued at once.
-            const int m = __ldg(a.U + c);
-            int okl = 1;
-            if (leader) {
-                __stcg(a.owner + m, c);
-                if (log_pos == log_end) {
-                    log_pos = atomicAdd(&ctr->log_cursor, kLogChunk);
-                    log_end = log_pos + kLogChunk;
-                    if (log_end > a.log_cap) { log_pos = log_end = 0; set_status(st, LTS_ERR_OOM); okl = 0; }
-                }
-                if (okl) a.vlog[log_pos++] = m;
-            }
-            if (!__shfl_sync(T.tmask, okl, T.tb)) break;
-            int mx, my, mz;
-            coords_of(g, m, mx, my, mz);
-            const int mnb = tl < NN ? nbr_q<NN>(g, mx, my, mz, tl) : -1;
             const unsigned long long mk = a.tag | (unsigned)c;
-            int mo = 0;
-            if (mnb >= 0) {
-                mo = od<DIR>(__ldg(O + mnb), g.n);
-                __stcg(a.qmark + mnb, mk);
+            bool ok;
+            if (seed >= 0) {                           // u has one higher neighbour, the seed of c
+                merged = false;
+                ok = rebuild_first_queue<DIR, NN>(T, g, O, seed, u, mk, a, tl);
+            } else {
+                // a meeting at u: its higher neighbours are the seeds of the classes that met
+                merged = true;
+                int ux, uy, uz;
+                coords_of(g, u, ux, uy, uz);
+                const int unb = tl < NN ? nbr_q<NN>(g, ux, uy, uz, tl) : -1;
+                bool hi = false;
+                int own = -1;
+                if (unb >= 0) {
+                    hi = od<DIR>(__ldg(O + unb), g.n) > kv;
+                    own = __ldcg(a.owner + unb);
+                }
+                unsigned hm = __ballot_sync(T.tmask, hi);
+                ok = true;
+                while (hm && ok) {
+                    const int L = __ffs(hm) - 1;
+                    hm &= hm - 1;
+                    const int w = __shfl_sync(T.tmask, unb, L);
+                    const int r = __shfl_sync(T.tmask, own, L);
+                    if (leader && r != c) __stcg(a.parent + r, c);
+                    ok = rebuild_first_queue<DIR, NN>(T, g, O, w, u, mk, a, tl);
+                }
+                if (leader) __stcg(a.cnt + u, 0);
             }
-            if (!insert_batch(T, mnb >= 0, mo, mnb, a)) break;
-        }
-        const unsigned long long mark = a.tag | (unsigned)c;
-        // ---- pop the highest queued vertex ----
-        int bk = -1, bs = 0;
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-            if (T.sk[e] > bk) { bk = T.sk[e]; bs = e; }
-        const int K = __reduce_max_sync(T.tmask, bk);
-        if (K < 0 && T.ov_top < 0) {                  // cannot happen with an authorized maximum
-            if (leader) set_status(st, LTS_ERR_INTERNAL);
-            break;
-        }
-        int v, kv;
-        if (T.ov_top > K) {
-            unsigned long long e = 0;
-            if (leader) e = ov_pop(T.ov);
-            e = __shfl_sync(T.tmask, e, T.tb);
-            ov_sync(T);
-            v = (int)(e & 0xffffffffu);
-            kv = (int)(e >> 32);
+            if (!ok) break;
+            if (leader) __stcg(a.wait_v + c, -1);
+            __syncwarp(T.tmask);
+            v = u;
+            resumed = true;
         } else {
-            const int L = __ffs(__ballot_sync(T.tmask, bk == K)) - 1;
-            int myv = 0;
+            // ---- pop the highest queued vertex ----
+            int bk = -1, bs = 0;
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (e == bs) myv = T.sv[e];
-            if (T.lane == L) {
+                if (T.sk[e] > bk) { bk = T.sk[e]; bs = e; }
+            const int K = __reduce_max_sync(T.tmask, bk);
+            if (K < 0 && T.ov_top < 0) {                  // cannot happen with an authorized maximum
+                if (leader) set_status(st, LTS_ERR_INTERNAL);
+                break;
+            }
+            if (T.ov_top > K) {
+                unsigned long long e = 0;
+                if (leader) e = ov_pop(T.ov);
+                e = __shfl_sync(T.tmask, e, T.tb);
+                ov_sync(T);
+                v = (int)(e & 0xffffffffu);
+                kv = (int)(e >> 32);
+            } else {
+                const int L = __ffs(__ballot_sync(T.tmask, bk == K)) - 1;
+                int myv = 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e)
-                    if (e == bs) T.sk[e] = -1;
+                    if (e == bs) myv = T.sv[e];
+                if (T.lane == L) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (e == bs) T.sk[e] = -1;
+                }
+                v = __shfl_sync(T.tmask, myv, L);
+                kv = K;
             }
-            v = __shfl_sync(T.tmask, myv, L);
-            kv = K;
         }
+        const unsigned long long mark = a.tag | (unsigned)c;
         // the leader claims v first, so that the atomic overlaps the neighbour loads
         int prev = 0;
-        if (leader) prev = atomicCAS(a.owner + v, -1, c);
+        if (leader && !resumed) prev = atomicCAS(a.owner + v, -1, c);
         // ---- one round of loads: order, owner, mark of every neighbour ----
         int x, y, z;
         coords_of(g, v, x, y, z);
@@ -365,11 +481,12 @@ __global__ void __launch_bounds__(kThreads, 12) propagate_kernel(Geom g, const i
             qm = __ldcg(a.qmark + nb);
         }
         // the leader claims v (or learns its owner) and broadcasts the outcome
-        int o = -1, decision = 0;     // decision: 0 skip, 1 claimed, 2 owned by another class
+        int decision = 0;             // 0 skip, 1 claimed (or resumed), 2 owned by another class
         if (leader) {
-            if (prev == -1) {
+            if (resumed) {
                 decision = 1;
-                o = c;
+            } else if (prev == -1) {
+                decision = 1;
                 if (log_pos == log_end) {
                     log_pos = atomicAdd(&ctr->log_cursor, kLogChunk);
                     log_end = log_pos + kLogChunk;
@@ -381,26 +498,22 @@ __global__ void __launch_bounds__(kThreads, 12) propagate_kernel(Geom g, const i
                 }
                 if (decision == 1) a.vlog[log_pos++] = v;
             } else {
-                o = prev;
                 decision = (prev == c || (merged && find_root(a.parent, prev) == c)) ? 0 : 2;
             }
         }
         decision = __shfl_sync(T.tmask, decision, T.tb);
         if (decision < 0) break;
         if (decision == 0) continue;
-        o = __shfl_sync(T.tmask, o, T.tb);
-        const bool claimed = decision == 1;
         const bool higher = nb >= 0 && on > kv;
         bool inC = nb >= 0 && ow >= 0 && (ow == c || (merged && find_root(a.parent, ow) == c));
         const int h = __popc(__ballot_sync(T.tmask, higher));
         const int k = __popc(__ballot_sync(T.tmask, higher && inC));
         if (k != h) {
-            // ---- arrival at the saddle v ----
-            const int head = claimed ? c : o;
-            if (leader && !claimed) {
-                const int old = atomicExch(a.listhead + head, c);
-                __stcg(a.next_w + c, old);
+            if (resumed) {                            // every higher neighbour of a task's u is in the class
+                if (leader) set_status(st, LTS_ERR_INTERNAL);
+                break;
             }
+            // ---- arrival at the saddle v ----
             // the queue must be readable by whoever releases this class
             int nreg = 0;
 #pragma unroll
@@ -442,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 12) propagate_kernel(Geom g, const i
                     __stcg(a.spill_pool + pos + 2 * i + 1, (int)(oh[i] >> 32));
                 }
             }
-            __syncwarp(T.tmask);                       // orders the team's spill writes before the leader's fence
+            __syncwarp(T.tmask);                       // orders the team's spill writes before the leader's release
             int tot = 0;
             if (leader) {
                 __stcg(a.spill_base + c, (int)base);
@@ -450,53 +563,58 @@ __global__ void __launch_bounds__(kThreads, 12) propagate_kernel(Geom g, const i
                 __stcg(a.wait_v + c, v);
                 // release: this class's spill and records; acquire: those of the
                 // classes that arrived before
-                cuda::atomic_ref<int, cuda::thread_scope_device> counter(a.cnt[head]);
+                cuda::atomic_ref<int, cuda::thread_scope_device> counter(a.cnt[v]);
                 tot = counter.fetch_add(k, cuda::memory_order_acq_rel) + k;
             }
             tot = __shfl_sync(T.tmask, tot, T.tb);
             if (tot < h) { c = -1; continue; }        // a higher neighbour is still unvisited: stop
             // ---- last arrival: merge every class stopped at v ----
+            // Every higher neighbour of v now belongs to a class waiting at v:
+            // those classes are the roots of the neighbours' owners.
             __syncwarp(T.tmask);
+            const int ow2 = nb >= 0 ? __ldcg(a.owner + nb) : -1;
+            const int rt = ow2 >= 0 ? find_root(a.parent, ow2) : -1;
+            const unsigned hmask = __ballot_sync(T.tmask, higher);
+            const unsigned grp = __match_any_sync(T.tmask, rt);
+            const bool rep_lane = higher && rt != c && rt >= 0 && (__ffs(grp & hmask) - 1) == T.lane;
+            int sb = 0, sn = 0;
+            if (rep_lane) {                            // one lane per class to merge
+                sb = __ldcg(a.spill_base + rt);
+                sn = __ldcg(a.spill_n + rt);
+                __stcg(a.parent + rt, c);
+            }
+            unsigned todo = __ballot_sync(T.tmask, rep_lane);
             merged = true;
-            int cur = head;
-            bool first = true;
             bool okm = true;
-            while (cur >= 0 && okm) {
-                if (cur != c) {
-                    int sb = 0, sn = 0;
-                    if (leader) {
-                        __stcg(a.parent + cur, c);
-                        sb = __ldcg(a.spill_base + cur);
-                        sn = __ldcg(a.spill_n + cur);
-                    }
-                    sb = __shfl_sync(T.tmask, sb, T.tb);
-                    sn = __shfl_sync(T.tmask, sn, T.tb);
-                    for (int i = 0; i < sn && okm; i += TS) {
-                        const int idx = i + tl;
-                        bool hs = idx < sn;
-                        int u = 0, ou = 0;
-                        if (hs) {
-                            u = __ldcg(a.spill_pool + sb + 2 * idx);
-                            ou = __ldcg(a.spill_pool + sb + 2 * idx + 1);
-                            __stcg(a.qmark + u, mark);
-                        }
-                        okm = insert_batch(T, hs, ou, u, a);
-                    }
+            while (todo && okm) {
+                const int L = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int rsb = __shfl_sync(T.tmask, sb, L);
+                const int rsn = __shfl_sync(T.tmask, sn, L);
+                if (rsn < 0) {                         // stopped at its first pop: v, below its seed
+                    okm = rebuild_first_queue<DIR, NN>(T, g, O, __shfl_sync(T.tmask, nb, L), v, mark, a, tl);
                 }
-                int nx = -1;
-                if (leader) nx = first ? __ldcg(a.listhead + head) : __ldcg(a.next_w + cur);
-                cur = __shfl_sync(T.tmask, nx, T.tb);
-                first = false;
+                for (int i = 0; i < rsn && okm; i += TS) {
+                    const int idx = i + tl;
+                    bool hs = idx < rsn;
+                    int u = 0, ou = 0;
+                    if (hs) {
+                        u = __ldcg(a.spill_pool + rsb + 2 * idx);
+                        ou = __ldcg(a.spill_pool + rsb + 2 * idx + 1);
+                        __stcg(a.qmark + u, mark);
+                    }
+                    okm = insert_batch(T, hs, ou, u, a);
+                }
             }
             if (!okm) break;
+            // v is released: nothing reads its counter again in this pass
             if (leader) {
                 __stcg(a.wait_v + c, -1);
-                if (head == c) { __stcg(a.cnt + c, 0); __stcg(a.listhead + c, -1); }
-                __threadfence();
+                __stcg(a.cnt + v, 0);
             }
             __syncwarp(T.tmask);
-            // classes merged into c: recheck which neighbours are in c
-            inC = nb >= 0 && in_class(a.parent, ow, c);
+            // a neighbour is in c if its root is c or the root of a higher neighbour
+            inC = nb >= 0 && rt >= 0 && (rt == c || (grp & hmask) != 0);
         }
         // ---- v belongs to c: queue its lower neighbours ----
         const bool cand = nb >= 0 && on < kv && !inC && qm != mark;
@@ -515,17 +633,25 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
     PropArgs a;
     a.U = w.U; a.owner = w.owner; a.qmark = w.qmark; a.tag = (unsigned long long)(++w.pass_tag) << 32;
     a.parent = w.parent; a.wait_v = w.wait_v; a.cnt = w.cnt;
-    a.listhead = w.listhead; a.next_w = w.next_w; a.spill_base = w.spill_base; a.spill_n = w.spill_n;
+    a.spill_base = w.spill_base; a.spill_n = w.spill_n;
     a.spill_pool = w.spill_pool; a.spill_cap = w.spill_cap; a.heap_pool = w.heap_pool; a.heap_cap = w.heap_cap;
-    a.vlog = w.vlog; a.log_cap = w.log_cap; a.ctr = w.ctr;
+    a.vlog = w.vlog; a.log_cap = w.log_cap; a.tasks = w.tasks; a.ctr = w.ctr;
+    const int pb = sms * 8;
     const int blocks = w.lanes / kThreads;
-    if (g.nn == 14) propagate_kernel<DIR, 14><<<blocks, kThreads, 0, s>>>(g, O, a);
-    else propagate_kernel<DIR, 6><<<blocks, kThreads, 0, s>>>(g, O, a);
-    w.launches += 1;
+    if (g.nn == 14) {
+        seed_kernel<DIR, 14><<<pb, 256, 0, s>>>(g, O, a);
+        first_pop_kernel<DIR, 14><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
+        propagate_kernel<DIR, 14><<<blocks, kThreads, 0, s>>>(g, O, a);
+    } else {
+        seed_kernel<DIR, 6><<<pb, 256, 0, s>>>(g, O, a);
+        first_pop_kernel<DIR, 6><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
+        propagate_kernel<DIR, 6><<<blocks, kThreads, 0, s>>>(g, O, a);
+    }
+    w.launches += 3;
     return cudaGetLastError();
 }
 
-int propagate_lanes(int sms) { return sms * 12 * kThreads; }
+int propagate_lanes(int sms) { return sms * 8 * kThreads; }
 long long propagate_log_slack(int lanes) { return (long long)lanes * kLogChunk; }
 long long propagate_spill_slack(int lanes) { return (long long)lanes * kSpillChunk; }
 long long propagate_heap_slack(int lanes) { return (long long)lanes * 64; }

@@ -32,9 +32,12 @@ __global__ void flatten_kernel(int* parent, const DevCounters* ctr) {
     }
 }
 
+// Every root class is a region waiting at its saddle.  The siblings at a
+// saddle are listed under the class that claimed it (sib_head, sib_next).
 template <int DIR>
 __global__ void roots_kernel(Geom g, const int* __restrict__ O, const int* __restrict__ parent,
-                             const int* __restrict__ wait_v, const int* __restrict__ owner, int* class2reg,
+                             const int* __restrict__ wait_v, const int* __restrict__ owner, int* sib_head,
+                             int* sib_next, int* class2reg,
                              int* reg_class, int* reg_saddle, int* reg_size, int* reg_top, int* reg_sod, int* reg_head,
                              DevCounters* ctr) {
     if (failed(&ctr->status)) return;
@@ -53,7 +56,10 @@ __global__ void roots_kernel(Geom g, const int* __restrict__ O, const int* __res
         reg_size[rid] = 0;
         reg_top[rid] = -1;
         reg_sod[rid] = od<DIR>(O[sv], g.n);
-        reg_head[rid] = owner[sv] == c;
+        const int hc = owner[sv];                     // the class that claimed the saddle waits there too
+        reg_head[rid] = hc == c;
+        if (hc < 0) set_status(&ctr->status, LTS_ERR_INTERNAL);
+        else if (hc != c) sib_next[c] = atomicExch(sib_head + hc, c);
     }
 }
 
@@ -137,10 +143,9 @@ __global__ void tiers_kernel(const int* __restrict__ reg_size, const int* __rest
 // highest member and give each the offset of its block below the saddle.
 __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __restrict__ reg_head,
                                 const int* __restrict__ reg_sod, const int* __restrict__ reg_size,
-                                const int* __restrict__ reg_top, const int* __restrict__ listhead,
-                                const int* __restrict__ next_w, const int* __restrict__ class2reg, int* reg_place,
-                                int* reg_att, RankBlk* rblk, int* tier_list, int half, int tiny_max,
-                                int med_max, DevCounters* ctr) {
+                                const int* __restrict__ reg_top, const int* __restrict__ sib_head,
+                                const int* __restrict__ sib_next, const int* __restrict__ class2reg, int* reg_place,
+                                int* reg_att, RankBlk* rblk, DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
     int my_max = 0, my_sad = 0;
@@ -148,35 +153,29 @@ __global__ void siblings_kernel(const int* __restrict__ reg_class, const int* __
         const int sz = reg_size[r];
         my_max = max(my_max, sz);
         if (!reg_head[r]) continue;
-        // siblings: the head class and the chain of classes that joined it
-        int total = 0;
-        int cur = reg_class[r];
-        bool first = true;
-        while (cur >= 0) {
-            const int rr = class2reg[cur];
-            total += reg_size[rr];
-            cur = first ? listhead[reg_class[r]] : next_w[cur];
-            first = false;
-        }
-        cur = reg_class[r];
-        first = true;
-        while (cur >= 0) {
-            const int rr = class2reg[cur];
-            const int t = reg_top[rr];
-            int below = 0;                               // sizes of siblings with a lower top
-            int c2 = reg_class[r];
-            bool f2 = true;
-            while (c2 >= 0) {
-                const int r2 = class2reg[c2];
-                if (reg_top[r2] < t) below += reg_size[r2];
-                c2 = f2 ? listhead[reg_class[r]] : next_w[c2];
-                f2 = false;
+        const int hc = reg_class[r];
+        const int first = sib_head[hc];
+        if (first < 0) {                               // the common case: one region at the saddle
+            reg_place[r] = -sz;
+            reg_att[r] = sz;
+        } else {
+            // siblings: the head class and the classes listed under it
+            int total = sz;
+            for (int cur = first; cur >= 0; cur = sib_next[cur]) total += reg_size[class2reg[cur]];
+            int cur = hc;
+            while (cur >= 0) {
+                const int rr = class2reg[cur];
+                const int t = reg_top[rr];
+                int below = reg_top[r] < t ? sz : 0;   // sizes of siblings with a lower top
+                for (int c2 = first; c2 >= 0; c2 = sib_next[c2]) {
+                    const int r2 = class2reg[c2];
+                    if (reg_top[r2] < t) below += reg_size[r2];
+                }
+                reg_place[rr] = below - total;
+                cur = cur == hc ? first : sib_next[cur];
             }
-            reg_place[rr] = below - total;
-            cur = first ? listhead[reg_class[r]] : next_w[cur];
-            first = false;
+            reg_att[r] = total;
         }
-        reg_att[r] = total;
         const int j = reg_sod[r];
         atomicOr(&rblk[j >> kRankShift].smask, 1u << (j & 31));
         ++my_sad;
@@ -192,16 +191,15 @@ cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaS
     const int T = 256;
     const int B = sms * 8;
     flatten_kernel<<<B, T, 0, s>>>(w.parent, w.ctr);
-    roots_kernel<DIR><<<B, T, 0, s>>>(g, O, w.parent, w.wait_v, w.owner, w.class2reg, w.reg_class, w.reg_saddle,
+    roots_kernel<DIR><<<B, T, 0, s>>>(g, O, w.parent, w.wait_v, w.owner, w.sib_head, w.sib_next, w.class2reg, w.reg_class, w.reg_saddle,
                                       w.reg_size, w.reg_top, w.reg_sod, w.reg_head, w.ctr);
     members_count_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.parent, w.owner, w.loc, w.class2reg, w.reg_saddle,
                                               w.reg_size, w.reg_top, w.ctr);
     scan_excl_i32(w, w.reg_size, w.reg_start, &w.ctr->n_regions, g.n / 2 + 1, s);
     members_fill_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.owner, w.loc, w.reg_start, w.members, w.member_reg,
                                              w.rblk, w.ctr);
-    siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.listhead, w.next_w,
-                                    w.class2reg, w.reg_place, w.reg_att, w.rblk, w.tier_list, w.class_cap / 2,
-                                    local_order_tiny_max(), local_order_med_max(), w.ctr);
+    siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.sib_head, w.sib_next,
+                                    w.class2reg, w.reg_place, w.reg_att, w.rblk, w.ctr);
     tiers_kernel<<<B, T, 0, s>>>(w.reg_size, w.reg_start, w.lhat, w.tier_list, w.class_cap, w.class_cap / 4,
                                  local_order_med_max(), w.ctr);
     w.launches += 6;

@@ -152,9 +152,14 @@ __global__ void members_place_kernel(int n, int* O, float* gout, int* owner, con
     }
 }
 
-__global__ void saddles_reset_kernel(int* owner, const int* __restrict__ reg_saddle, const DevCounters* ctr) {
+// the final saddles: release their claims and clear their arrival counters
+__global__ void saddles_reset_kernel(int* owner, int* cnt, const int* __restrict__ reg_saddle, const DevCounters* ctr) {
     const int nreg = ctr->n_regions;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) owner[reg_saddle[r]] = -1;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+        const int sv = reg_saddle[r];
+        owner[sv] = -1;
+        cnt[sv] = 0;
+    }
 }
 
 }  // namespace
@@ -173,7 +178,7 @@ cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms
     members_place_kernel<DIR><<<sms * 8, 256, 0, s>>>(g.n, O, gout, w.owner, w.members, w.member_reg, w.lhat,
                                                       w.reg_saddle, w.reg_sod, w.reg_place, w.reg_start, w.rblk,
                                                       w.cumA, w.ctr);
-    saddles_reset_kernel<<<sms * 4, 256, 0, s>>>(w.owner, w.reg_saddle, w.ctr);
+    saddles_reset_kernel<<<sms * 4, 256, 0, s>>>(w.owner, w.cnt, w.reg_saddle, w.ctr);
     w.launches += 7;
     return cudaGetLastError();
 }
