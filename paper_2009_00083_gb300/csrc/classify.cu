@@ -13,128 +13,127 @@ namespace {
 // The Freudenthal neighbourhood of v is the union of two unit cubes: the one
 // with v as its lowest corner and the one with v as its highest corner
 // (offsets {0,1}^d and -{0,1}^d).  The order is injective, so v is a maximum
-// exactly when it is the maximum of both cubes.  A block loads a tile of the
-// pass-oriented order with a one-vertex halo into shared memory (outside the
-// grid: -1, below every rank), computes the maxima of all 2x2x2 cubes
-// separably, and compares.  The tile's unauthorized extrema are appended
-// with one atomic.
-constexpr int TX = 32, TY = 8, TZ = 8;       // outputs per tile (3D); 2D uses TZ = 1
-constexpr int kCT = 256;
+// exactly when it is the maximum of both cubes.  Each cube is two 2x2
+// squares of consecutive z planes: with A_z(x,y) the maximum of the square
+// {x,x+1} x {y,y+1} of plane z and B_z(x,y) that of {x-1,x} x {y-1,y},
+//     v is a maximum  <=>  v == max(A_z, A_z+1)  and  v == max(B_z, B_z-1).
+// A warp owns 30 consecutive x of one row y (its lanes span x-1 .. x+30, so
+// the two end lanes only provide neighbours) and marches kZC planes along z.
+// Per plane a lane loads its vertex in rows y-1, y, y+1 (the neighbouring
+// warps of the block read the same lines, so most of these hit L1), takes
+// x-1 and x+1 from its neighbour lanes and keeps the squares of its column in
+// registers.  The minima pass compares with min instead of max on O itself
+// (outside the grid: -1 for maxima, N for minima), so no value is
+// transformed.  A 2D grid is the case Z = 1.  Unauthorized extrema are
+// gathered per warp in shared memory and appended to U with one atomic per
+// flush.
+constexpr int kWarps = 8;                    // rows per block
+constexpr int kCT = 32 * kWarps;
+constexpr int kOut = 30;                     // outputs per warp row
+constexpr int kZC = 64;                      // planes per warp
+constexpr int kWL = 256;                     // gathered extrema per warp before a flush
 
-template <int DIR, int TZT>
+template <int DIR>
+__device__ __forceinline__ int top2(int a, int b) { return DIR > 0 ? max(a, b) : min(a, b); }
+
+template <int DIR>
 __global__ void __launch_bounds__(kCT) classify_kernel(Geom g, const int* __restrict__ O,
                                                        const unsigned* __restrict__ authbits, int* __restrict__ U,
                                                        int* __restrict__ parent, int* __restrict__ wait_v,
                                                        int* __restrict__ spill_n, int* __restrict__ sib_head,
                                                        int cap, DevCounters* ctr) {
-    constexpr int SX = TX + 2, SY = TY + 2, SZ = TZT + 2;
-    __shared__ int S[SZ][SY][SX];            // order with halo
-    __shared__ int s_warp[kCT / 32];
-    __shared__ int s_base;
+    __shared__ int s_list[kWarps][kWL];
     if (failed(&ctr->status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ntx = (g.X + TX - 1) / TX, nty = (g.Y + TY - 1) / TY, ntz = (g.Z + TZT - 1) / TZT;
-    const long long ntiles = (long long)ntx * nty * ntz;
+    const int outside = DIR > 0 ? -1 : g.n;
+    const int ntx = (g.X + kOut - 1) / kOut, nty = (g.Y + kWarps - 1) / kWarps, nzc = (g.Z + kZC - 1) / kZC;
+    const int ntxy = ntx * nty;
+    const int nblk = ntxy * nzc;
+    int* L = s_list[warp];
+    int cnt = 0;                             // gathered in L (warp-uniform)
     int my_auth = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((long long)ntx * nty));
-        const int x0 = tx * TX - 1, y0 = ty * TY - 1, z0 = tz * TZT - 1;
-        // rows of SX values (one per (y, z) of the halo tile), one row per warp
-        // step; every lane issues its loads before storing any of them
-        constexpr int ROWS = SY * SZ;
-        constexpr int RPW = (ROWS + kCT / 32 - 1) / (kCT / 32);   // rows per warp
-        int vals[RPW][2];
-#pragma unroll
-        for (int k = 0; k < RPW; ++k) {
-            const int rr = warp + k * (kCT / 32);
-            const int ly = rr % SY, lz = rr / SY;
-            const int y = y0 + ly, z = z0 + lz;
-            const bool rowok = rr < ROWS && (unsigned)y < (unsigned)g.Y && (unsigned)z < (unsigned)g.Z;
-            const int* rowp = O + (long long)g.XY * z + (long long)g.X * y;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int lx = lane + 32 * h;
-                const int x = x0 + lx;
-                vals[k][h] = (rowok && lx < SX && (unsigned)x < (unsigned)g.X) ? od<DIR>(__ldg(rowp + x), g.n) : -1;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < RPW; ++k) {
-            const int rr = warp + k * (kCT / 32);
-            if (rr >= ROWS) break;
-            const int ly = rr % SY, lz = rr / SY;
-            S[lz][ly][lane] = vals[k][0];
-            if (lane + 32 < SX) S[lz][ly][lane + 32] = vals[k][1];
-        }
-        __syncthreads();
-        // each thread: PER consecutive outputs along x of one (y, z) row; the two
-        // cubes of an output use 7 rows of S: (dy,dz) in {0,1}^2 and -{0,1}^2
-        unsigned mu = 0;
-        constexpr int PER = TX * TY * TZT / kCT;
-        constexpr int GROUPS = TX / PER;   // threads along x per row
-        const int gx = threadIdx.x % GROUPS, row = threadIdx.x / GROUPS;
-        const int oy = row % TY, oz = row / TY;
-        const int z = z0 + 1 + oz, y = y0 + 1 + oy;
-        const int vfirst = (x0 + 1 + gx * PER) + g.X * y + g.XY * z;
-        if (oz < TZT && z < g.Z && y < g.Y) {
-            const int bx = gx * PER;           // S column of x - 1 for the first output
-            constexpr int DY[7] = {0, 1, 0, 1, -1, 0, -1};
-            constexpr int DZ[7] = {0, 0, 1, 1, 0, -1, -1};
-            int pm[7][PER + 1];                // pairwise x maxima of each row
-#pragma unroll
-            for (int r = 0; r < 7; ++r) {
-                int prevv = S[oz + 1 + DZ[r]][oy + 1 + DY[r]][bx];
-#pragma unroll
-                for (int i = 0; i <= PER; ++i) {
-                    const int cur = S[oz + 1 + DZ[r]][oy + 1 + DY[r]][bx + 1 + i];
-                    pm[r][i] = max(prevv, cur);
-                    prevv = cur;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                const int x = x0 + 1 + bx + i;
-                if (x >= g.X) break;
-                const int ov = S[oz + 1][oy + 1][bx + 1 + i];
-                const int cpos = max(max(pm[0][i + 1], pm[1][i + 1]), max(pm[2][i + 1], pm[3][i + 1]));
-                const int cneg = max(max(pm[0][i], pm[4][i]), max(pm[5][i], pm[6][i]));
-                if (ov == cpos && ov == cneg) {
-                    const int v = vfirst + i;
-                    if ((__ldg(authbits + (v >> 5)) >> (v & 31)) & 1u) ++my_auth;
-                    else mu |= 1u << i;
-                }
-            }
-        }
-        // block-wide exclusive scan of the per-thread counts, one atomic per tile
-        const int c = __popc(mu);
-        int x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int yv = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += yv;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int w = 0; w < kCT / 32; ++w) { const int tt = s_warp[w]; s_warp[w] = run; run += tt; }
-            s_base = run ? atomicAdd(&ctr->n_unauth, run) : 0;
-        }
-        __syncthreads();
-        int pos = s_base + s_warp[warp] + x - c;
-        while (mu) {
-            const int i = __ffs(mu) - 1;
-            mu &= mu - 1;
-            const int cl = pos++;
+
+    auto flush = [&]() {
+        if (cnt == 0) return;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->n_unauth, cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < cnt; i += 32) {
+            const int cl = base + i;
             if (cl >= cap) { set_status(&ctr->status, LTS_ERR_INTERNAL); continue; }
-            U[cl] = vfirst + i;
+            U[cl] = L[i];
             parent[cl] = cl;
             wait_v[cl] = -1;
-            spill_n[cl] = -1;            // never spilled: a queue rebuilt from the seed
+            spill_n[cl] = -1;                // never spilled: a queue rebuilt from the seed
             sib_head[cl] = -1;
         }
-        __syncthreads();
+        __syncwarp();
+        cnt = 0;
+    };
+
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int zc = b / ntxy, t = b - zc * ntxy;
+        const int ty = t / ntx, tx = t - ty * ntx;
+        const int y = ty * kWarps + warp;
+        if (y >= g.Y) continue;                          // warp-uniform: no output row
+        const int x = tx * kOut - 1 + lane;
+        const bool xin = (unsigned)x < (unsigned)g.X;
+        const bool out_lane = lane >= 1 && lane <= kOut && x < g.X;
+        const int zs = zc * kZC, ze = min(zs + kZC, g.Z);
+        const bool r0 = y >= 1 && xin, r1 = xin, r2 = y + 1 < g.Y && xin;
+        // rows y-1, y, y+1 of plane zs-1 at x (pointer arithmetic only where valid)
+        const int* p = O + ((long long)g.XY * (zs - 1) + (long long)g.X * y + (xin ? x : 0));
+        const long long XY = g.XY;
+        const int X = g.X;
+        auto load = [&](int pz, const int* q, int& a0, int& a1, int& a2) {
+            const bool pin = (unsigned)pz < (unsigned)g.Z;
+            a0 = (pin && r0) ? __ldg(q - X) : outside;
+            a1 = (pin && r1) ? __ldg(q) : outside;
+            a2 = (pin && r2) ? __ldg(q + X) : outside;
+        };
+        // squares of the lane's column in one plane
+        auto squares = [&](int a0, int a1, int a2, int& A, int& B) {
+            const int n1 = __shfl_down_sync(0xffffffffu, a1, 1), n2 = __shfl_down_sync(0xffffffffu, a2, 1);
+            const int p0 = __shfl_up_sync(0xffffffffu, a0, 1), p1 = __shfl_up_sync(0xffffffffu, a1, 1);
+            A = top2<DIR>(top2<DIR>(a1, n1), top2<DIR>(a2, n2));
+            B = top2<DIR>(top2<DIR>(a1, p1), top2<DIR>(a0, p0));
+        };
+        int c0, c1, c2, d0, d1, d2;
+        load(zs - 1, p, c0, c1, c2);
+        load(zs, p + XY, d0, d1, d2);
+        int Am, Bm, A0, B0;
+        squares(c0, c1, c2, Am, Bm);                    // plane zs-1: only B is used
+        squares(d0, d1, d2, A0, B0);                    // plane zs
+        int v0 = d1;
+        p += 2 * XY;                                    // plane zs+1
+        int e0, e1, e2;
+        load(zs + 1, p, e0, e1, e2);
+        for (int z = zs; z < ze; ++z) {
+            const int w0 = e0, w1 = e1, w2 = e2;        // plane z+1
+            p += XY;
+            if (z + 2 <= ze) load(z + 2, p, e0, e1, e2); // one plane ahead
+            int A1, B1;
+            squares(w0, w1, w2, A1, B1);
+            const bool is_ext = out_lane && v0 == top2<DIR>(A0, A1) && v0 == top2<DIR>(B0, Bm);
+            bool unauth = false;
+            int v = 0;
+            if (is_ext) {
+                v = x + X * y + g.XY * z;
+                if ((__ldg(authbits + (v >> 5)) >> (v & 31)) & 1u) ++my_auth;
+                else unauth = true;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, unauth);
+            if (m) {
+                if (unauth) L[cnt + __popc(m & ((1u << lane) - 1u))] = v;
+                cnt += __popc(m);
+                __syncwarp();
+                if (cnt > kWL - 32) flush();
+            }
+            Bm = B0;
+            A0 = A1; B0 = B1; v0 = w1;
+        }
     }
+    flush();
     warp_atomic_add(&ctr->n_auth_ext, my_auth);
 }
 
@@ -142,15 +141,10 @@ __global__ void __launch_bounds__(kCT) classify_kernel(Geom g, const int* __rest
 
 template <int DIR>
 cudaError_t classify(Work& w, const Geom& g, const int* O, cudaStream_t s) {
-    const long long tiles = (long long)((g.X + TX - 1) / TX) * ((g.Y + TY - 1) / TY) *
-                            (g.ndim == 3 ? (g.Z + TZ - 1) / TZ : 1);
-    const int blocks = (int)std::min<long long>(tiles, 152LL * 8);
-    if (g.ndim == 3)
-        classify_kernel<DIR, TZ><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v,
-                                                        w.spill_n, w.sib_head, w.class_cap, w.ctr);
-    else
-        classify_kernel<DIR, 1><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v,
-                                                       w.spill_n, w.sib_head, w.class_cap, w.ctr);
+    const long long nblk = (long long)((g.X + kOut - 1) / kOut) * ((g.Y + kWarps - 1) / kWarps) * ((g.Z + kZC - 1) / kZC);
+    const int blocks = (int)std::min<long long>(nblk, 152LL * 8 * 4);
+    classify_kernel<DIR><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v, w.spill_n, w.sib_head,
+                                                w.class_cap, w.ctr);
     w.launches += 1;
     return cudaGetLastError();
 }
