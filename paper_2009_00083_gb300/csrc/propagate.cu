@@ -1,8 +1,8 @@
 // Step 1 with hill chains (Sec. 4.2 step 1, Sec. 4.3, Sec. 4.4): one
 // superlevel set propagation per unauthorized maximum (a "class").
 //
-// The first step of every propagation is data parallel and runs as two
-// thread-per-class kernels: the seed (a maximum: nothing else can reach it)
+// The first step of every propagation is data parallel and runs as one
+// thread-per-class kernel: the seed (a maximum: nothing else can reach it)
 // is claimed with a plain store and its highest neighbour u is found; then
 // every class pops u.  All its neighbours are lower than the seed, so u is
 // the first vertex any schedule pops.  If the seed is the only higher
@@ -268,11 +268,18 @@ __device__ __forceinline__ bool rebuild_first_queue(TeamState<NN>& T, const Geom
     return insert_batch(T, cand, key, nb, a);
 }
 
-// First step, part 1 (thread per class c): claim the seed, log it, and find
-// its highest neighbour u (kept in wait_v[c]).  Log slots [0, nU) hold the
-// seeds and [nU, 2 nU) the first pops; the engine's log starts at 2 nU.
+// First step (thread per class c): claim the seed m and log it (log slots
+// [0, nU) hold the seeds, [nU, 2 nU) the first pops; the engine's log starts
+// at 2 nU), find m's highest neighbour u (kept in wait_v[c]) and pop it.  If
+// m is u's only higher neighbour, c claims u and becomes an engine task.
+// Otherwise c arrives at u with k = 1 (its one vertex, the seed; spill_n[c]
+// stays -1: its queue is rebuilt from the seed); the arrival that completes
+// u's count makes a task that melds every class waiting at u.  The others
+// stop here.  u is not a seed, so its claim never meets a seed's plain store,
+// and u's neighbourhood overlaps m's, so most of its loads hit L1.
 template <int DIR, int NN>
-__global__ void __launch_bounds__(256) seed_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
+__global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __restrict__ O, PropArgs a, int4* tasks) {
+    __shared__ int s_n, s_base;
     DevCounters* ctr = a.ctr;
     if (failed(&ctr->status)) return;
     const int nU = ctr->n_unauth;
@@ -285,47 +292,29 @@ __global__ void __launch_bounds__(256) seed_kernel(Geom g, const int* __restrict
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->log_cursor = 2 * nU;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nU; c += gridDim.x * blockDim.x) {
-        const int m = __ldg(a.U + c);
-        a.owner[m] = c;
-        a.vlog[c] = m;
-        int x, y, z;
-        coords_of(g, m, x, y, z);
-        int best = -1, u = -1;
-#pragma unroll
-        for (int q = 0; q < NN; ++q) {
-            const int nb = nbr_q<NN>(g, x, y, z, q);
-            if (nb >= 0) {
-                const int k = od<DIR>(__ldg(O + nb), g.n);
-                if (k > best) { best = k; u = nb; }
-            }
-        }
-        a.wait_v[c] = u;
-    }
-}
-
-// First step, part 2 (thread per class c): pop u = wait_v[c].  If the seed
-// is u's only higher neighbour, c claims u and becomes an engine task.
-// Otherwise c arrives at u with k = 1 (its one vertex, the seed; spill_n[c]
-// stays -1: its queue is rebuilt from the seed); the arrival that completes
-// u's count makes a task that melds every class waiting at u.  The others
-// stop here.
-template <int DIR, int NN>
-__global__ void __launch_bounds__(256) first_pop_kernel(Geom g, const int* __restrict__ O, PropArgs a, int4* tasks) {
-    DevCounters* ctr = a.ctr;
-    if (failed(&ctr->status)) return;
-    const int nU = ctr->n_unauth;
     const int lane = threadIdx.x & 31;
     for (long long b = (long long)blockIdx.x * blockDim.x; b < nU; b += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(b + threadIdx.x);
         int4 task = make_int4(-1, 0, 0, 0);
         if (c < nU) {
-            const int u = a.wait_v[c];
+            const int m = __ldg(a.U + c);
+            a.owner[m] = c;
+            a.vlog[c] = m;
+            int x, y, z;
+            coords_of(g, m, x, y, z);
+            int ku = -1, u = -1;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                const int nb = nbr_q<NN>(g, x, y, z, q);
+                if (nb >= 0) {
+                    const int k = od<DIR>(__ldg(O + nb), g.n);
+                    if (k > ku) { ku = k; u = nb; }
+                }
+            }
+            a.wait_v[c] = u;
             const int prev = atomicCAS(a.owner + u, -1, c);
             a.vlog[nU + c] = prev == -1 ? u : -1;
-            int x, y, z;
             coords_of(g, u, x, y, z);
-            const int ku = od<DIR>(__ldg(O + u), g.n);
             int h = 0;
 #pragma unroll
             for (int q = 0; q < NN; ++q) {
@@ -333,17 +322,24 @@ __global__ void __launch_bounds__(256) first_pop_kernel(Geom g, const int* __res
                 if (nb >= 0 && od<DIR>(__ldg(O + nb), g.n) > ku) ++h;
             }
             if (h == 1) {
-                if (prev == -1) task = make_int4(c, u, ku, __ldg(a.U + c));
+                if (prev == -1) task = make_int4(c, u, ku, m);
                 else set_status(&ctr->status, LTS_ERR_INTERNAL);   // only the seed's class can reach u
             } else if (atomicAdd(a.cnt + u, 1) + 1 == h) {
                 task = make_int4(c, u, ku, -1);
             }
         }
+        // task slots: one global atomic per block
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
         const unsigned want = __ballot_sync(0xffffffffu, task.x >= 0);
-        int base = 0;
-        if (lane == 0 && want) base = atomicAdd(&ctr->n_tasks, __popc(want));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (task.x >= 0) tasks[base + __popc(want & ((1u << lane) - 1u))] = task;
+        int wb = 0;
+        if (lane == 0 && want) wb = atomicAdd(&s_n, __popc(want));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) s_base = s_n ? atomicAdd(&ctr->n_tasks, s_n) : 0;
+        __syncthreads();
+        if (task.x >= 0) tasks[s_base + wb + __popc(want & ((1u << lane) - 1u))] = task;
+        __syncthreads();
     }
 }
 
@@ -639,15 +635,13 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
     const int pb = sms * 8;
     const int blocks = w.lanes / kThreads;
     if (g.nn == 14) {
-        seed_kernel<DIR, 14><<<pb, 256, 0, s>>>(g, O, a);
-        first_pop_kernel<DIR, 14><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
+        first_step_kernel<DIR, 14><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
         propagate_kernel<DIR, 14><<<blocks, kThreads, 0, s>>>(g, O, a);
     } else {
-        seed_kernel<DIR, 6><<<pb, 256, 0, s>>>(g, O, a);
-        first_pop_kernel<DIR, 6><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
+        first_step_kernel<DIR, 6><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
         propagate_kernel<DIR, 6><<<blocks, kThreads, 0, s>>>(g, O, a);
     }
-    w.launches += 3;
+    w.launches += 2;
     return cudaGetLastError();
 }
 
