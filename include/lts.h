@@ -113,6 +113,38 @@ lts_status lts_simplify(lts_ctx* ctx, const lts_grid* g, const float* d_field,
                         const int32_t* d_authorized, int64_t n_authorized, lts_mode mode,
                         float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats);
 
+/* Simplifies nf independent fields (Sec. 4 on each; the paper runs one field
+ * at a time, and batching is this library's addition).  Array arguments
+ * hold one entry per field, with the meaning they have in lts_simplify;
+ * every field must fit the context's max_vertices.  The fields are spread
+ * over the context's workspace and up to 3 more (allocated on first use,
+ * each sized for the largest field of the batch, kept for later batches),
+ * each on its own stream, largest fields first; the extra streams start
+ * after the work already on the context's stream, and the call returns when
+ * every field is done.  opt_stats, if non-NULL, is an array of nf entries
+ * (stage_us is not filled).  Returns LTS_OK when every field succeeded, else
+ * the status of the first failing field, whose index the last-error
+ * message names; the other fields are still simplified.  Argument errors
+ * (LTS_ERR_ARG, naming the field) are reported before any work starts. */
+lts_status lts_simplify_batch(lts_ctx* ctx, int32_t nf, const lts_grid* grids, const float* const* d_fields,
+                              const int32_t* const* d_authorized, const int64_t* n_authorized, lts_mode mode,
+                              float* const* d_out_fields, int32_t* const* d_out_orders, lts_stats* opt_stats);
+
+/* Serving.  lts_submit enqueues one simplification (arguments as in
+ * lts_simplify) on the context's stream and returns at once with a ticket
+ * (> 0); requests run in submission order.  lts_poll sets *done to 1 once the
+ * request is finished and then returns its status (LTS_OK or the error it
+ * met); while it runs, *done is 0 and the return is LTS_OK.  The result of a
+ * ticket stays readable until 1024 newer requests have been submitted
+ * (later polls give LTS_ERR_ARG); lts_submit waits for the request 1024
+ * places before it if that one is still running.  A failed request leaves
+ * the workspace clean for the requests behind it.  The first lts_submit on
+ * a context allocates its pinned request ring. */
+lts_status lts_submit(lts_ctx* ctx, const lts_grid* g, const float* d_field, const int32_t* d_authorized,
+                      int64_t n_authorized, lts_mode mode, float* d_out_field, int32_t* d_out_order,
+                      uint64_t* ticket);
+lts_status lts_poll(lts_ctx* ctx, uint64_t ticket, int* done);
+
 /* Message describing the last error on this context ("" if none). */
 const char* lts_last_error(const lts_ctx* ctx);
 

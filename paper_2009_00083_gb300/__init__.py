@@ -14,7 +14,8 @@ import os
 
 __all__ = [
     "LtsGrid", "LtsStats", "LtsError", "Context", "lts_create", "lts_simplify", "lts_destroy",
-    "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "library_path", "load", "simplify",
+    "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "lts_simplify_batch", "lts_submit",
+    "lts_poll", "library_path", "load", "simplify",
     "MODE_MIN", "MODE_MAX", "MODE_BOTH", "ORDER_STATIC_MAX_VERTICES",
 ]
 
@@ -93,6 +94,16 @@ def load():
         lib.lts_order_field_static.argtypes = [ctypes.c_int, ctypes.POINTER(LtsGrid), P, P, P, ctypes.c_char_p,
                                                ctypes.c_size_t]
         lib.lts_order_field_static.restype = ctypes.c_int
+        PP = ctypes.POINTER(P)
+        lib.lts_simplify_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(LtsGrid), PP, PP,
+                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int, PP, PP,
+                                           ctypes.POINTER(LtsStats)]
+        lib.lts_simplify_batch.restype = ctypes.c_int
+        lib.lts_submit.argtypes = [P, ctypes.POINTER(LtsGrid), P, P, ctypes.c_int64, ctypes.c_int, P, P,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+        lib.lts_submit.restype = ctypes.c_int
+        lib.lts_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+        lib.lts_poll.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -138,6 +149,36 @@ def lts_last_error(ctx) -> str:
 
 def lts_destroy(ctx) -> None:
     load().lts_destroy(ctx)
+
+
+def lts_simplify_batch(ctx, grids, d_fields, d_authorized, n_authorized, mode, d_out_fields, d_out_orders,
+                       stats=None) -> int:
+    """grids: list of LtsGrid; the others: lists of device addresses / counts (one per field);
+    stats: a ctypes array of LtsStats of the same length, or None."""
+    nf = len(grids)
+    P = ctypes.c_void_p
+    ga = (LtsGrid * max(nf, 1))(*grids)
+    arr = lambda xs: (P * max(nf, 1))(*[P(x) for x in xs])
+    na = (ctypes.c_int64 * max(nf, 1))(*[int(x) for x in n_authorized])
+    return load().lts_simplify_batch(ctx, nf, ga, arr(d_fields), arr(d_authorized), na, _MODES[mode],
+                                     arr(d_out_fields), arr(d_out_orders), stats)
+
+
+def lts_submit(ctx, grid: LtsGrid, d_field: int, d_authorized: int, n_authorized: int, mode, d_out_field: int,
+               d_out_order: int):
+    """Returns (status, ticket)."""
+    t = ctypes.c_uint64(0)
+    code = load().lts_submit(ctx, ctypes.byref(grid), ctypes.c_void_p(d_field), ctypes.c_void_p(d_authorized),
+                             int(n_authorized), _MODES[mode], ctypes.c_void_p(d_out_field),
+                             ctypes.c_void_p(d_out_order), ctypes.byref(t))
+    return int(code), int(t.value)
+
+
+def lts_poll(ctx, ticket: int):
+    """Returns (status, done)."""
+    d = ctypes.c_int(0)
+    code = load().lts_poll(ctx, ctypes.c_uint64(ticket), ctypes.byref(d))
+    return int(code), bool(d.value)
 
 
 def lts_order_field_static(device: int, grid: LtsGrid, d_field: int, d_order: int, cuda_stream: int = 0):
@@ -191,6 +232,62 @@ class Context:
         if code != 0:
             raise LtsError(code, lts_last_error(self._ctx))
         return g, o, (st.as_dict() if st is not None else None)
+
+
+    def simplify_batch(self, fields, authorized, mode="both", with_stats=True):
+        """fields: list of CUDA float32 tensors; authorized: list of CUDA int32
+        tensors.  Returns (list of (g, order), list of stats dicts or None)."""
+        import torch
+
+        if len(fields) != len(authorized):
+            raise ValueError("one authorized list per field")
+        outs, grids = [], []
+        auth = [a.contiguous() for a in authorized]
+        for f in fields:
+            if f.dtype != torch.float32 or not f.is_cuda or not f.is_contiguous():
+                raise ValueError("fields must be contiguous CUDA float32 tensors")
+            grids.append(grid_of_shape(tuple(f.shape)))
+            outs.append((torch.empty_like(f), torch.empty(f.shape, dtype=torch.int32, device=f.device)))
+        st = (LtsStats * max(len(fields), 1))() if with_stats else None
+        code = lts_simplify_batch(self._ctx, grids, [f.data_ptr() for f in fields],
+                                  [a.data_ptr() if a.numel() else 0 for a in auth], [a.numel() for a in auth], mode,
+                                  [o[0].data_ptr() for o in outs], [o[1].data_ptr() for o in outs], st)
+        if code != 0:
+            raise LtsError(code, lts_last_error(self._ctx))
+        return outs, ([st[i].as_dict() for i in range(len(fields))] if st is not None else None)
+
+    def submit(self, field, authorized, mode="both"):
+        """Queues a simplification; returns a ticket.  The tensors are kept
+        alive until the ticket is polled done."""
+        import torch
+
+        if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
+            raise ValueError("field must be a contiguous CUDA float32 tensor")
+        authorized = authorized.contiguous()
+        g = torch.empty_like(field)
+        o = torch.empty(field.shape, dtype=torch.int32, device=field.device)
+        code, t = lts_submit(self._ctx, grid_of_shape(tuple(field.shape)), field.data_ptr(),
+                             authorized.data_ptr() if authorized.numel() else 0, authorized.numel(), mode,
+                             g.data_ptr(), o.data_ptr())
+        if code != 0:
+            raise LtsError(code, lts_last_error(self._ctx))
+        if not hasattr(self, "_pending"):
+            self._pending = {}
+        self._pending[t] = (field, authorized, g, o)
+        return t
+
+    def poll(self, ticket):
+        """None while the request runs; (g, order) once it is done; raises
+        LtsError if it failed."""
+        code, done = lts_poll(self._ctx, ticket)
+        if not done:
+            if code != 0:
+                raise LtsError(code, lts_last_error(self._ctx))
+            return None
+        _, _, g, o = getattr(self, "_pending", {}).pop(ticket, (None, None, None, None))
+        if code != 0:
+            raise LtsError(code, lts_last_error(self._ctx))
+        return g, o
 
 
 def simplify(field, authorized, mode="both"):

@@ -295,7 +295,7 @@ __device__ __forceinline__ void team_extremum(const TeamLO<TS>& T, int L, unsign
 }
 
 template <int DIR, int NN, int TS>
-__global__ void __launch_bounds__(128, 8) lo_team_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
+__global__ void __launch_bounds__(128, 12) lo_team_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
     if (failed(&a.ctr->status)) return;
     TeamLO<TS> T;
     T.lane = threadIdx.x & 31;
@@ -606,9 +606,9 @@ void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t
     cudaFuncSetAttribute(lo_dense_kernel<DIR, NN, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
     cudaFuncSetAttribute(lo_dense_kernel<DIR, NN, kMedR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large);
     const int* tl = w.tier_list + w.class_cap;
-    lo_team_kernel<DIR, NN, 16><<<sms * 8, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t16);
-    lo_team_kernel<DIR, NN, 32><<<sms * 8, 128, 0, s>>>(g, a, tl, &w.ctr->n_t32);
-    lo_dense_kernel<DIR, NN, 128, 4><<<sms * 8, 128, small, s>>>(g, a, tl + q, &w.ctr->n_med);
+    lo_team_kernel<DIR, NN, 16><<<sms * 12, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t16);
+    lo_team_kernel<DIR, NN, 32><<<sms * 12, 128, 0, s>>>(g, a, tl, &w.ctr->n_t32);
+    lo_dense_kernel<DIR, NN, 128, 4><<<sms * 10, 128, small, s>>>(g, a, tl + q, &w.ctr->n_med);
     lo_dense_kernel<DIR, NN, kMedR, 1><<<sms * 5, 32, large, s>>>(g, a, tl + 2 * q, &w.ctr->n_large);
     lo_big_kernel<DIR, NN><<<sms, 128, 0, s>>>(g, a, tl + 3 * q, &w.ctr->n_big);
 }

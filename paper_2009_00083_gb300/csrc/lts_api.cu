@@ -1,9 +1,14 @@
-// C ABI of the library (include/lts.h): context and workspace management,
-// argument checks, and the sequence of stages of one simplification.
+// C ABI of the library (include/lts.h): contexts and their workspaces,
+// argument checks, and the sequence of stages of one simplification, run
+// synchronously (lts_simplify), over a batch of fields spread on several
+// workspaces at once (lts_simplify_batch), or as queued requests
+// (lts_submit / lts_poll).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
+#include <vector>
 
 #include "lts_internal.cuh"
 
@@ -17,17 +22,53 @@ int scan_tiles_for(long long max_count);
 
 using namespace lts;
 
-struct lts_ctx {
-    int device = 0;
-    int sms = 0;
-    cudaStream_t stream = nullptr;
+namespace lts {
+// Final state of one request, written on the device after its last kernel.
+struct ReqResult {
+    int status;
+    int pad;
+    PassStats ps[2];
+    unsigned long long ticket;
+};
+}  // namespace lts
+
+namespace {
+
+constexpr int kMaxLanes = 4;       // the context's own workspace and up to 3 more for batches
+constexpr int kRing = 1024;        // serving requests in flight per context
+
+// A workspace with the stream its work is enqueued on.
+struct Lane {
     Work w{};
-    bool dirty = false;          // workspace may hold state of an aborted call
-    std::string err;
+    long long nmax = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
     cudaEvent_t ev[16];
     bool events = false;
     void* allocs[64];
     int nallocs = 0;
+    bool dirty = false;            // a CUDA error left the workspace in an unknown state
+};
+
+}  // namespace
+
+struct lts_ctx {
+    int device = 0;
+    int sms = 0;
+    Lane lane[kMaxLanes];
+    int nlanes = 1;
+    std::string err;
+    // batches
+    ReqResult* batch_dev = nullptr;
+    ReqResult* batch_host = nullptr;
+    int batch_cap = 0;
+    cudaEvent_t fork = nullptr, join[kMaxLanes] = {};
+    // serving
+    ReqResult* ring_host = nullptr;   // pinned, mapped
+    ReqResult* ring_dev = nullptr;
+    cudaEvent_t ring_ev[kRing];
+    bool ring_ready = false;
+    unsigned long long next_ticket = 1;
 };
 
 namespace {
@@ -62,7 +103,7 @@ size_t bytes_for(const Sizes& z) {
     b += 4 * (size_t)z.n;                           // saddle arrival counters
     b += 4 * (size_t)z.spill_cap + 8 * (size_t)z.heap_cap + 4 * (size_t)z.log_cap;
     b += 11 * 4 * (size_t)z.half;                   // region records
-    b += 2 * 4 * (size_t)z.n;                       // members, lhat
+    b += 3 * 4 * (size_t)z.n;                       // members, member regions, lhat
     b += 17 * (size_t)z.lo_cap;                     // local-order scratch
     b += sizeof(RankBlk) * (size_t)z.nblk + 2 * 4 * (size_t)z.half;
     b += 8 * (size_t)z.scan_tiles + sizeof(DevCounters) + 2 * sizeof(PassStats);
@@ -70,22 +111,90 @@ size_t bytes_for(const Sizes& z) {
 }
 
 template <typename T>
-bool dev_alloc(lts_ctx* c, T** p, size_t count) {
+bool dev_alloc(Lane& L, T** p, size_t count) {
     void* q = nullptr;
     if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return false;
-    c->allocs[c->nallocs++] = q;
+    L.allocs[L.nallocs++] = q;
     *p = static_cast<T*>(q);
     return true;
 }
 
-void free_all(lts_ctx* c) {
-    for (int i = 0; i < c->nallocs; ++i) cudaFree(c->allocs[i]);
-    c->nallocs = 0;
-    if (c->w.h_ctr) cudaFreeHost(c->w.h_ctr);
-    c->w.h_ctr = nullptr;
-    if (c->events)
-        for (auto& e : c->ev) cudaEventDestroy(e);
-    c->events = false;
+void lane_free(Lane& L) {
+    for (int i = 0; i < L.nallocs; ++i) cudaFree(L.allocs[i]);
+    L.nallocs = 0;
+    if (L.w.h_ctr) cudaFreeHost(L.w.h_ctr);
+    L.w.h_ctr = nullptr;
+    if (L.events)
+        for (auto& e : L.ev) cudaEventDestroy(e);
+    L.events = false;
+    if (L.own_stream && L.stream) cudaStreamDestroy(L.stream);
+    L.stream = nullptr;
+    L.own_stream = false;
+    L.w = Work{};
+    L.nmax = 0;
+}
+
+// Allocates and initializes a workspace for grids of up to nmax vertices.
+lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, bool own_stream) {
+    L.stream = stream;
+    L.own_stream = own_stream;
+    L.nmax = nmax;
+    const Sizes z = sizes_for(nmax, sms);
+    Work& w = L.w;
+    w.nmax = (int)nmax;
+    w.max_tiles = (int)z.tiles;
+    w.lanes = (int)z.lanes;
+    w.class_cap = (int)z.half;
+    w.log_cap = z.log_cap; w.spill_cap = z.spill_cap; w.heap_cap = z.heap_cap; w.lo_cap = z.lo_cap;
+    w.nblk = (int)z.nblk;
+    w.scan_tmp_cap = (int)z.scan_tiles;
+    bool ok = true;
+    ok = ok && dev_alloc(L, &w.keyA, z.n) && dev_alloc(L, &w.valA, z.n) && dev_alloc(L, &w.keyB, z.n) &&
+         dev_alloc(L, &w.valB, z.n);
+    ok = ok && dev_alloc(L, &w.sort_status, (size_t)z.tiles * 256) && dev_alloc(L, &w.sort_hist, 1024) &&
+         dev_alloc(L, &w.sort_offsets, 1024) && dev_alloc(L, &w.tile_counter, 4) &&
+         dev_alloc(L, &w.bin_cursor, 1024);
+    ok = ok && dev_alloc(L, &w.authbits, (z.n + 31) / 32);
+    ok = ok && dev_alloc(L, &w.owner, z.n) && dev_alloc(L, &w.loc, z.n) && dev_alloc(L, &w.qmark, z.n);
+    ok = ok && dev_alloc(L, &w.U, z.half) && dev_alloc(L, &w.parent, z.half) && dev_alloc(L, &w.wait_v, z.half) &&
+         dev_alloc(L, &w.cnt, z.n) && dev_alloc(L, &w.tasks, z.half) &&
+         dev_alloc(L, &w.sib_head, z.half) && dev_alloc(L, &w.sib_next, z.half) &&
+         dev_alloc(L, &w.spill_base, z.half) && dev_alloc(L, &w.spill_n, z.half);
+    ok = ok && dev_alloc(L, &w.spill_pool, z.spill_cap) && dev_alloc(L, &w.heap_pool, z.heap_cap) &&
+         dev_alloc(L, &w.vlog, z.log_cap);
+    ok = ok && dev_alloc(L, &w.class2reg, z.half) && dev_alloc(L, &w.reg_class, z.half) &&
+         dev_alloc(L, &w.reg_saddle, z.half) && dev_alloc(L, &w.reg_size, z.half) &&
+         dev_alloc(L, &w.reg_start, z.half + 1) && dev_alloc(L, &w.reg_top, z.half) &&
+         dev_alloc(L, &w.reg_sod, z.half) && dev_alloc(L, &w.reg_place, z.half) && dev_alloc(L, &w.reg_head, z.half) &&
+         dev_alloc(L, &w.reg_att, z.half) && dev_alloc(L, &w.reg_floods, z.half);
+    ok = ok && dev_alloc(L, &w.members, z.n) && dev_alloc(L, &w.lhat, z.n) && dev_alloc(L, &w.tier_list, 2 * z.half) &&
+         dev_alloc(L, &w.member_reg, z.n);
+    ok = ok && dev_alloc(L, &w.lo_v, z.lo_cap) && dev_alloc(L, &w.lo_L, z.lo_cap) && dev_alloc(L, &w.lo_L2, z.lo_cap) &&
+         dev_alloc(L, &w.lo_heap, z.lo_cap) && dev_alloc(L, &w.lo_flag, z.lo_cap);
+    ok = ok && dev_alloc(L, &w.rblk, z.nblk) && dev_alloc(L, &w.sad_att, z.half) && dev_alloc(L, &w.cumA, z.half + 1);
+    ok = ok && dev_alloc(L, &w.scan_tmp, z.scan_tiles) && dev_alloc(L, &w.ctr, 1) && dev_alloc(L, &w.pstats, 2);
+    if (ok && cudaMallocHost((void**)&w.h_ctr, sizeof(DevCounters) + 2 * sizeof(PassStats)) != cudaSuccess) ok = false;
+    if (!ok) {
+        cudaGetLastError();
+        lane_free(L);
+        return LTS_ERR_OOM;
+    }
+    for (auto& e : L.ev) cudaEventCreate(&e);
+    L.events = true;
+    cudaStream_t s = L.stream;
+    cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, s);
+    cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)z.n, s);
+    cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, s);
+    w.pass_tag = 0;
+    cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), s);
+    w.epoch = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        lane_free(L);
+        return LTS_ERR_CUDA;
+    }
+    return LTS_OK;
 }
 
 bool grid_ok(const lts_grid* g, long long* n_out) {
@@ -100,25 +209,69 @@ bool grid_ok(const lts_grid* g, long long* n_out) {
     return true;
 }
 
-lts_status fail(lts_ctx* c, lts_status s, const char* msg) {
+Geom geom_of(const lts_grid* gr, long long n) {
+    Geom g;
+    g.ndim = gr->ndim;
+    g.nn = gr->ndim == 2 ? 6 : 14;
+    g.X = (int)gr->dims[0]; g.Y = (int)gr->dims[1]; g.Z = (int)gr->dims[2];
+    g.n = (int)n;
+    g.XY = g.X * g.Y;
+    g.dX = make_fastdiv((unsigned)g.X);
+    g.dXY = make_fastdiv((unsigned)g.XY);
+    return g;
+}
+
+lts_status fail(lts_ctx* c, lts_status s, const std::string& msg) {
     c->err = msg;
     return s;
 }
 
-lts_status cuda_fail(lts_ctx* c, cudaError_t e, const char* where) {
+lts_status cuda_fail(lts_ctx* c, Lane& L, cudaError_t e, const char* where) {
     c->err = std::string(where) + ": " + cudaGetErrorString(e);
-    c->dirty = true;
+    L.dirty = true;
     return LTS_ERR_CUDA;
 }
 
-// reset the per-vertex state after an aborted call
-cudaError_t clean_workspace(lts_ctx* c) {
-    Work& w = c->w;
-    cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)w.nmax, c->stream);
-    cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)w.nmax, c->stream);
-    cudaMemsetAsync(w.sort_status, 0, (size_t)w.max_tiles * 256 * sizeof(unsigned long long), c->stream);
+const char* status_text(int status) {
+    return status == LTS_ERR_NAN ? "the field holds a NaN"
+         : status == LTS_ERR_NO_AUTHORIZED ? "a pass has unauthorized extrema but no authorized one"
+         : status == LTS_ERR_ARG ? "an authorized id is out of range"
+         : status == LTS_ERR_OOM ? "a workspace pool was exhausted"
+         : status == LTS_ERR_TIMEOUT ? "a bounded device wait expired"
+         : "internal consistency check failed";
+}
+
+// reset the per-vertex state after a CUDA error
+cudaError_t clean_workspace(Lane& L) {
+    Work& w = L.w;
+    cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)w.nmax, L.stream);
+    cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)w.nmax, L.stream);
+    cudaMemsetAsync(w.sort_status, 0, (size_t)w.max_tiles * 256 * sizeof(unsigned long long), L.stream);
     w.epoch = 0;
     return cudaGetLastError();
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const char* x = static_cast<const char*>(a);
+    const char* y = static_cast<const char*>(b);
+    return x < y + nb && y < x + na;
+}
+
+// Checks one field's arguments; n receives its vertex count.
+lts_status check_field(lts_ctx* c, const lts_grid* gr, long long nmax, const float* d_field,
+                       const int32_t* d_authorized, int64_t n_authorized, lts_mode mode, const float* d_out_field,
+                       const int32_t* d_out_order, long long* n, const std::string& what) {
+    if (!grid_ok(gr, n)) return fail(c, LTS_ERR_ARG, what + "invalid grid");
+    if (*n > nmax) return fail(c, LTS_ERR_ARG, what + "grid larger than the context's max_vertices");
+    if (mode < LTS_MODE_MIN || mode > LTS_MODE_BOTH) return fail(c, LTS_ERR_ARG, what + "invalid mode");
+    if (!d_field || !d_out_field || !d_out_order) return fail(c, LTS_ERR_ARG, what + "null data pointer");
+    if (n_authorized < 0 || (n_authorized > 0 && !d_authorized))
+        return fail(c, LTS_ERR_ARG, what + "invalid authorized list");
+    const size_t nb = (size_t)*n * 4;
+    if (overlap(d_field, nb, d_out_field, nb) || overlap(d_field, nb, d_out_order, nb) ||
+        overlap(d_out_field, nb, d_out_order, nb))
+        return fail(c, LTS_ERR_ARG, what + "outputs overlap the input or each other");
+    return LTS_OK;
 }
 
 }  // namespace
@@ -141,8 +294,126 @@ __global__ void save_pass_kernel(const DevCounters* ctr, const int* reg_start, P
     ps->total_floods = ctr->total_floods;
     ps->heap_spills = ctr->heap_spills;
 }
+
+// the request's final status and pass statistics
+__global__ void capture_kernel(const DevCounters* ctr, const PassStats* ps, ReqResult* out, unsigned long long ticket) {
+    out->status = ctr->status;
+    out->ps[0] = ps[0];
+    out->ps[1] = ps[1];
+    out->ticket = ticket;
+}
+
+// After a failed request (and only then) the claims and arrival counters it
+// left behind are cleared, so that the next request on this workspace,
+// already enqueued behind it, starts from a clean state.
+__global__ void fail_clean_kernel(const DevCounters* ctr, int* owner, int* cnt, int nmax) {
+    if (*(volatile const int*)&ctr->status == 0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nmax; i += (long long)gridDim.x * blockDim.x) {
+        owner[i] = -1;
+        cnt[i] = 0;
+    }
+}
 }  // namespace
 }  // namespace lts
+
+namespace {
+
+// Enqueues one simplification on the lane's stream: stage events ev[0..11],
+// the result capture (when res is set) and the clean-up after a failure.
+cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const int32_t* d_authorized,
+                             int64_t n_authorized, lts_mode mode, float* gout, int* O, int sms, ReqResult* res,
+                             unsigned long long ticket) {
+    cudaStream_t s = L.stream;
+    Work& w = L.w;
+    w.nblk_cur = (g.n + 31) / 32;
+    cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), s);
+    cudaMemsetAsync(w.pstats, 0, 2 * sizeof(PassStats), s);
+    w.launches = 0;
+    cudaEventRecord(L.ev[0], s);
+    build_authbits(w, g, d_authorized, n_authorized, s);
+    order_field(w, g, d_field, gout, O, s);
+    cudaEventRecord(L.ev[1], s);
+    int evi = 2;
+    for (int side = 0; side < 2; ++side) {
+        const bool run = side == 0 ? (mode & LTS_MODE_MIN) != 0 : (mode & LTS_MODE_MAX) != 0;
+        if (!run) {
+            for (int k = 0; k < 5; ++k) cudaEventRecord(L.ev[evi++], s);
+            continue;
+        }
+        pass_reset(w, s);
+        if (side == 0) {
+            classify<-1>(w, g, O, s);               cudaEventRecord(L.ev[evi++], s);
+            propagate<-1>(w, g, O, sms, s);         cudaEventRecord(L.ev[evi++], s);
+            extract_regions<-1>(w, g, O, sms, s);   cudaEventRecord(L.ev[evi++], s);
+            local_orders<-1>(w, g, O, sms, s);      cudaEventRecord(L.ev[evi++], s);
+            reorder_flatten<-1>(w, g, O, gout, sms, s); cudaEventRecord(L.ev[evi++], s);
+        } else {
+            classify<1>(w, g, O, s);                cudaEventRecord(L.ev[evi++], s);
+            propagate<1>(w, g, O, sms, s);          cudaEventRecord(L.ev[evi++], s);
+            extract_regions<1>(w, g, O, sms, s);    cudaEventRecord(L.ev[evi++], s);
+            local_orders<1>(w, g, O, sms, s);       cudaEventRecord(L.ev[evi++], s);
+            reorder_flatten<1>(w, g, O, gout, sms, s); cudaEventRecord(L.ev[evi++], s);
+        }
+        save_pass_kernel<<<1, 1, 0, s>>>(w.ctr, w.reg_start, w.pstats + side);
+        w.launches += 1;
+    }
+    if (res) {
+        capture_kernel<<<1, 1, 0, s>>>(w.ctr, w.pstats, res, ticket);
+        w.launches += 1;
+    }
+    fail_clean_kernel<<<sms * 4, 256, 0, s>>>(w.ctr, w.owner, w.cnt, w.nmax);
+    w.launches += 1;
+    return cudaGetLastError();
+}
+
+void fill_stats(lts_stats& o, long long n, const PassStats* ps, long long launches) {
+    memset(&o, 0, sizeof o);
+    o.n_vertices = n;
+    for (int k = 0; k < 2; ++k) {
+        o.removed[k] = ps[k].removed;
+        o.regions[k] = ps[k].regions;
+        o.region_vertices[k] = ps[k].region_vertices;
+        o.max_region[k] = ps[k].max_region;
+        o.max_local_floods[k] = (int32_t)ps[k].max_floods;
+        o.total_local_floods[k] = ps[k].total_floods;
+        o.heap_spills[k] = ps[k].heap_spills;
+    }
+    o.kernel_launches = launches;
+}
+
+void fill_stage_times(lts_stats& o, Lane& L) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, L.ev[0], L.ev[1]) == cudaSuccess) o.stage_us[0] = ms * 1000.f;
+    for (int st = 0; st < 5; ++st) {
+        float acc = 0;
+        for (int side = 0; side < 2; ++side) {
+            const int a = 1 + side * 5 + st;
+            if (cudaEventElapsedTime(&ms, L.ev[a], L.ev[a + 1]) == cudaSuccess) acc += ms;
+        }
+        o.stage_us[1 + st] = acc * 1000.f;
+    }
+    if (cudaEventElapsedTime(&ms, L.ev[0], L.ev[11]) == cudaSuccess) o.stage_us[6] = ms * 1000.f;
+}
+
+lts_status ensure_ring(lts_ctx* c) {
+    if (c->ring_ready) return LTS_OK;
+    if (cudaHostAlloc((void**)&c->ring_host, kRing * sizeof(ReqResult), cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LTS_ERR_OOM, "cannot allocate the request ring");
+    }
+    memset(c->ring_host, 0, kRing * sizeof(ReqResult));
+    if (cudaHostGetDevicePointer((void**)&c->ring_dev, c->ring_host, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(c->ring_host);
+        c->ring_host = nullptr;
+        return fail(c, LTS_ERR_CUDA, "cannot map the request ring");
+    }
+    for (auto& e : c->ring_ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    c->ring_ready = true;
+    return LTS_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -160,63 +431,11 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     if (cudaSetDevice(device) != cudaSuccess) return LTS_ERR_CUDA;
     lts_ctx* c = new lts_ctx();
     c->device = device;
-    c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
-    const Sizes z = sizes_for(max_vertices, c->sms);
-    Work& w = c->w;
-    w.nmax = (int)max_vertices;
-    w.max_tiles = (int)z.tiles;
-    w.lanes = (int)z.lanes;
-    w.class_cap = (int)z.half;
-    w.log_cap = z.log_cap; w.spill_cap = z.spill_cap; w.heap_cap = z.heap_cap; w.lo_cap = z.lo_cap;
-    w.nblk = (int)z.nblk;
-    w.scan_tmp_cap = (int)z.scan_tiles;
-    bool ok = true;
-    ok = ok && dev_alloc(c, &w.keyA, z.n) && dev_alloc(c, &w.valA, z.n) && dev_alloc(c, &w.keyB, z.n) &&
-         dev_alloc(c, &w.valB, z.n);
-    ok = ok && dev_alloc(c, &w.sort_status, (size_t)z.tiles * 256) && dev_alloc(c, &w.sort_hist, 1024) &&
-         dev_alloc(c, &w.sort_offsets, 1024) && dev_alloc(c, &w.tile_counter, 4) &&
-         dev_alloc(c, &w.bin_cursor, 1024);
-    ok = ok && dev_alloc(c, &w.authbits, (z.n + 31) / 32);
-    ok = ok && dev_alloc(c, &w.owner, z.n) && dev_alloc(c, &w.loc, z.n) && dev_alloc(c, &w.qmark, z.n);
-    ok = ok && dev_alloc(c, &w.U, z.half) && dev_alloc(c, &w.parent, z.half) && dev_alloc(c, &w.wait_v, z.half) &&
-         dev_alloc(c, &w.cnt, z.n) && dev_alloc(c, &w.tasks, z.half) &&
-         dev_alloc(c, &w.sib_head, z.half) && dev_alloc(c, &w.sib_next, z.half) &&
-         dev_alloc(c, &w.spill_base, z.half) && dev_alloc(c, &w.spill_n, z.half);
-    ok = ok && dev_alloc(c, &w.spill_pool, z.spill_cap) && dev_alloc(c, &w.heap_pool, z.heap_cap) &&
-         dev_alloc(c, &w.vlog, z.log_cap);
-    ok = ok && dev_alloc(c, &w.class2reg, z.half) && dev_alloc(c, &w.reg_class, z.half) &&
-         dev_alloc(c, &w.reg_saddle, z.half) && dev_alloc(c, &w.reg_size, z.half) &&
-         dev_alloc(c, &w.reg_start, z.half + 1) && dev_alloc(c, &w.reg_top, z.half) &&
-         dev_alloc(c, &w.reg_sod, z.half) && dev_alloc(c, &w.reg_place, z.half) && dev_alloc(c, &w.reg_head, z.half) &&
-         dev_alloc(c, &w.reg_att, z.half) && dev_alloc(c, &w.reg_floods, z.half);
-    ok = ok && dev_alloc(c, &w.members, z.n) && dev_alloc(c, &w.lhat, z.n) && dev_alloc(c, &w.tier_list, 2 * z.half) &&
-         dev_alloc(c, &w.member_reg, z.n);
-    ok = ok && dev_alloc(c, &w.lo_v, z.lo_cap) && dev_alloc(c, &w.lo_L, z.lo_cap) && dev_alloc(c, &w.lo_L2, z.lo_cap) &&
-         dev_alloc(c, &w.lo_heap, z.lo_cap) && dev_alloc(c, &w.lo_flag, z.lo_cap);
-    ok = ok && dev_alloc(c, &w.rblk, z.nblk) && dev_alloc(c, &w.sad_att, z.half) && dev_alloc(c, &w.cumA, z.half + 1);
-    ok = ok && dev_alloc(c, &w.scan_tmp, z.scan_tiles) && dev_alloc(c, &w.ctr, 1) && dev_alloc(c, &w.pstats, 2);
-    if (ok && cudaMallocHost((void**)&w.h_ctr, sizeof(DevCounters) + 2 * sizeof(PassStats)) != cudaSuccess) ok = false;
-    if (!ok) {
-        cudaGetLastError();
-        free_all(c);
+    const lts_status st = lane_alloc(c->lane[0], max_vertices, c->sms, static_cast<cudaStream_t>(cuda_stream), false);
+    if (st != LTS_OK) {
         delete c;
-        return LTS_ERR_OOM;
-    }
-    for (auto& e : c->ev) cudaEventCreate(&e);
-    c->events = true;
-    cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, c->stream);
-    cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)z.n, c->stream);
-    cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), c->stream);
-    cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, c->stream);
-    w.pass_tag = 0;
-    cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), c->stream);
-    w.epoch = 0;
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) {
-        free_all(c);
-        delete c;
-        return LTS_ERR_CUDA;
+        return st;
     }
     *out = c;
     return LTS_OK;
@@ -225,131 +444,208 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
 void lts_destroy(lts_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
-    cudaStreamSynchronize(c->stream);
-    free_all(c);
+    cudaStreamSynchronize(c->lane[0].stream);
+    for (int i = 1; i < kMaxLanes; ++i)
+        if (c->lane[i].stream) cudaStreamSynchronize(c->lane[i].stream);
+    for (int i = 0; i < kMaxLanes; ++i) lane_free(c->lane[i]);
+    if (c->batch_dev) cudaFree(c->batch_dev);
+    if (c->batch_host) cudaFreeHost(c->batch_host);
+    if (c->fork) cudaEventDestroy(c->fork);
+    for (auto& e : c->join)
+        if (e) cudaEventDestroy(e);
+    if (c->ring_ready) {
+        for (auto& e : c->ring_ev) cudaEventDestroy(e);
+        cudaFreeHost(c->ring_host);
+    }
     delete c;
 }
 
 const char* lts_last_error(const lts_ctx* c) { return c ? c->err.c_str() : "null context"; }
-
-static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
-    const char* x = static_cast<const char*>(a);
-    const char* y = static_cast<const char*>(b);
-    return x < y + nb && y < x + na;
-}
 
 lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, const int32_t* d_authorized,
                         int64_t n_authorized, lts_mode mode, float* d_out_field, int32_t* d_out_order,
                         lts_stats* opt_stats) {
     if (!c) return LTS_ERR_ARG;
     c->err.clear();
+    Lane& L = c->lane[0];
     long long n;
-    if (!grid_ok(gr, &n)) return fail(c, LTS_ERR_ARG, "invalid grid");
-    if (n > c->w.nmax) return fail(c, LTS_ERR_ARG, "grid larger than the context's max_vertices");
-    if (mode < LTS_MODE_MIN || mode > LTS_MODE_BOTH) return fail(c, LTS_ERR_ARG, "invalid mode");
-    if (!d_field || !d_out_field || !d_out_order) return fail(c, LTS_ERR_ARG, "null data pointer");
-    if (n_authorized < 0 || (n_authorized > 0 && !d_authorized)) return fail(c, LTS_ERR_ARG, "invalid authorized list");
-    const size_t nb = (size_t)n * 4;
-    if (overlap(d_field, nb, d_out_field, nb) || overlap(d_field, nb, d_out_order, nb) ||
-        overlap(d_out_field, nb, d_out_order, nb))
-        return fail(c, LTS_ERR_ARG, "outputs overlap the input or each other");
+    lts_status st = check_field(c, gr, L.nmax, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order,
+                                &n, "");
+    if (st != LTS_OK) return st;
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
-    cudaStream_t s = c->stream;
-    Work& w = c->w;
     cudaError_t e;
-    if (c->dirty) {
-        if ((e = clean_workspace(c)) != cudaSuccess) return cuda_fail(c, e, "clean");
-        c->dirty = false;
+    if (L.dirty) {
+        if ((e = clean_workspace(L)) != cudaSuccess) return cuda_fail(c, L, e, "clean");
+        L.dirty = false;
     }
-    Geom g;
-    g.ndim = gr->ndim;
-    g.nn = gr->ndim == 2 ? 6 : 14;
-    g.X = (int)gr->dims[0]; g.Y = (int)gr->dims[1]; g.Z = (int)gr->dims[2];
-    g.n = (int)n;
-    g.XY = g.X * g.Y;
-    g.dX = make_fastdiv((unsigned)g.X);
-    g.dXY = make_fastdiv((unsigned)g.XY);
-    w.nblk_cur = (int)((n + 31) / 32);
-    const int sms = c->sms;
-    int* O = d_out_order;
-    float* gout = d_out_field;
-
-    cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), s);
-    cudaMemsetAsync(w.pstats, 0, 2 * sizeof(PassStats), s);
-    w.launches = 0;
-    cudaEventRecord(c->ev[0], s);
-    build_authbits(w, g, d_authorized, n_authorized, s);
-    order_field(w, g, d_field, gout, O, s);
-    cudaEventRecord(c->ev[1], s);
-    int evi = 2;
-    for (int side = 0; side < 2; ++side) {
-        const bool run = side == 0 ? (mode & LTS_MODE_MIN) != 0 : (mode & LTS_MODE_MAX) != 0;
-        if (!run) {
-            for (int k = 0; k < 5; ++k) cudaEventRecord(c->ev[evi++], s);
-            continue;
-        }
-        pass_reset(w, s);
-        if (side == 0) {
-            classify<-1>(w, g, O, s);               cudaEventRecord(c->ev[evi++], s);
-            propagate<-1>(w, g, O, sms, s);         cudaEventRecord(c->ev[evi++], s);
-            extract_regions<-1>(w, g, O, sms, s);   cudaEventRecord(c->ev[evi++], s);
-            local_orders<-1>(w, g, O, sms, s);      cudaEventRecord(c->ev[evi++], s);
-            reorder_flatten<-1>(w, g, O, gout, sms, s); cudaEventRecord(c->ev[evi++], s);
-        } else {
-            classify<1>(w, g, O, s);                cudaEventRecord(c->ev[evi++], s);
-            propagate<1>(w, g, O, sms, s);          cudaEventRecord(c->ev[evi++], s);
-            extract_regions<1>(w, g, O, sms, s);    cudaEventRecord(c->ev[evi++], s);
-            local_orders<1>(w, g, O, sms, s);       cudaEventRecord(c->ev[evi++], s);
-            reorder_flatten<1>(w, g, O, gout, sms, s); cudaEventRecord(c->ev[evi++], s);
-        }
-        save_pass_kernel<<<1, 1, 0, s>>>(w.ctr, w.reg_start, w.pstats + side);
-        w.launches += 1;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "launch");
-    cudaMemcpyAsync(w.h_ctr, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    const Geom g = geom_of(gr, n);
+    if ((e = enqueue_simplify(L, g, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order, c->sms,
+                              nullptr, 0)) != cudaSuccess)
+        return cuda_fail(c, L, e, "launch");
+    Work& w = L.w;
+    cudaMemcpyAsync(w.h_ctr, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
     PassStats* hps = reinterpret_cast<PassStats*>(w.h_ctr + 1);
-    cudaMemcpyAsync(hps, w.pstats, 2 * sizeof(PassStats), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    cudaMemcpyAsync(hps, w.pstats, 2 * sizeof(PassStats), cudaMemcpyDeviceToHost, L.stream);
+    if ((e = cudaStreamSynchronize(L.stream)) != cudaSuccess) return cuda_fail(c, L, e, "synchronize");
     const int status = w.h_ctr->status;
     if (opt_stats) {
-        lts_stats& o = *opt_stats;
-        memset(&o, 0, sizeof o);
-        o.n_vertices = n;
-        for (int k = 0; k < 2; ++k) {
-            o.removed[k] = hps[k].removed;
-            o.regions[k] = hps[k].regions;
-            o.region_vertices[k] = hps[k].region_vertices;
-            o.max_region[k] = hps[k].max_region;
-            o.max_local_floods[k] = (int32_t)hps[k].max_floods;
-            o.total_local_floods[k] = hps[k].total_floods;
-            o.heap_spills[k] = hps[k].heap_spills;
-        }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
-        o.stage_us[0] = ms * 1000.f;
-        for (int st = 0; st < 5; ++st) {
-            float acc = 0;
-            for (int side = 0; side < 2; ++side) {
-                const int a = 1 + side * 5 + st;
-                if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[a + 1]) == cudaSuccess) acc += ms;
-            }
-            o.stage_us[1 + st] = acc * 1000.f;
-        }
-        cudaEventElapsedTime(&ms, c->ev[0], c->ev[11]);
-        o.stage_us[6] = ms * 1000.f;
-        o.kernel_launches = w.launches;
+        fill_stats(*opt_stats, n, hps, w.launches);
+        fill_stage_times(*opt_stats, L);
     }
-    if (status != 0) {
-        c->dirty = true;
-        const char* what = status == LTS_ERR_NAN ? "the field holds a NaN"
-                         : status == LTS_ERR_NO_AUTHORIZED ? "a pass has unauthorized extrema but no authorized one"
-                         : status == LTS_ERR_ARG ? "an authorized id is out of range"
-                         : status == LTS_ERR_OOM ? "a workspace pool was exhausted"
-                         : status == LTS_ERR_TIMEOUT ? "a bounded device wait expired"
-                         : "internal consistency check failed";
-        c->err = what;
-        return (lts_status)status;
+    if (status != 0) return fail(c, (lts_status)status, status_text(status));
+    return LTS_OK;
+}
+
+lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, const float* const* d_fields,
+                              const int32_t* const* d_authorized, const int64_t* n_authorized, lts_mode mode,
+                              float* const* d_out_fields, int32_t* const* d_out_orders, lts_stats* opt_stats) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    if (nf < 0) return fail(c, LTS_ERR_ARG, "negative field count");
+    if (nf == 0) return LTS_OK;
+    if (!grids || !d_fields || !d_authorized || !n_authorized || !d_out_fields || !d_out_orders)
+        return fail(c, LTS_ERR_ARG, "null array argument");
+    std::vector<long long> n(nf);
+    long long nbig = 0;
+    for (int i = 0; i < nf; ++i) {
+        const lts_status st = check_field(c, &grids[i], c->lane[0].nmax, d_fields[i], d_authorized[i],
+                                          n_authorized[i], mode, d_out_fields[i], d_out_orders[i], &n[i],
+                                          "field " + std::to_string(i) + ": ");
+        if (st != LTS_OK) return st;
+        nbig = std::max(nbig, n[i]);
     }
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
+    cudaError_t e;
+    // workspaces: the context's own, and up to kMaxLanes - 1 more sized for the largest field
+    const int want = std::min(kMaxLanes, nf);
+    for (int i = 1; i < want; ++i) {
+        Lane& L = c->lane[i];
+        if (L.nmax >= nbig) continue;
+        if (L.stream) cudaStreamSynchronize(L.stream);
+        lane_free(L);
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LTS_ERR_CUDA, "cannot create a stream");
+        }
+        const lts_status st = lane_alloc(L, nbig, c->sms, s, true);
+        if (st != LTS_OK) {
+            cudaStreamDestroy(s);
+            L.stream = nullptr;
+            return fail(c, st, "cannot allocate a batch workspace");
+        }
+    }
+    c->nlanes = std::max(c->nlanes, want);
+    if (!c->fork) {
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+        for (auto& j : c->join) cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    }
+    if (c->batch_cap < nf) {
+        if (c->batch_dev) cudaFree(c->batch_dev);
+        if (c->batch_host) cudaFreeHost(c->batch_host);
+        c->batch_dev = nullptr;
+        c->batch_host = nullptr;
+        c->batch_cap = 0;
+        if (cudaMalloc((void**)&c->batch_dev, nf * sizeof(ReqResult)) != cudaSuccess ||
+            cudaMallocHost((void**)&c->batch_host, nf * sizeof(ReqResult)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LTS_ERR_OOM, "cannot allocate batch results");
+        }
+        c->batch_cap = nf;
+    }
+    for (int i = 0; i < want; ++i)
+        if (c->lane[i].dirty) {
+            if ((e = clean_workspace(c->lane[i])) != cudaSuccess) return cuda_fail(c, c->lane[i], e, "clean");
+            c->lane[i].dirty = false;
+        }
+    // every lane starts after what the context's stream holds
+    cudaStream_t s0 = c->lane[0].stream;
+    cudaEventRecord(c->fork, s0);
+    for (int i = 1; i < want; ++i) cudaStreamWaitEvent(c->lane[i].stream, c->fork, 0);
+    // largest fields first, each to the least loaded lane
+    std::vector<int> order(nf);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    std::vector<long long> load(want, 0);
+    std::vector<long long> launches(nf, 0);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[l] += n[i];
+        Lane& L = c->lane[l];
+        const Geom g = geom_of(&grids[i], n[i]);
+        if ((e = enqueue_simplify(L, g, d_fields[i], d_authorized[i], n_authorized[i], mode, d_out_fields[i],
+                                  d_out_orders[i], c->sms, c->batch_dev + i, 0)) != cudaSuccess)
+            return cuda_fail(c, L, e, "launch");
+        launches[i] = L.w.launches;
+    }
+    for (int i = 1; i < want; ++i) {
+        cudaEventRecord(c->join[i], c->lane[i].stream);
+        cudaStreamWaitEvent(s0, c->join[i], 0);
+    }
+    cudaMemcpyAsync(c->batch_host, c->batch_dev, nf * sizeof(ReqResult), cudaMemcpyDeviceToHost, s0);
+    if ((e = cudaStreamSynchronize(s0)) != cudaSuccess) return cuda_fail(c, c->lane[0], e, "synchronize");
+    int first_bad = -1;
+    for (int i = 0; i < nf; ++i) {
+        if (opt_stats) fill_stats(opt_stats[i], n[i], c->batch_host[i].ps, launches[i]);
+        if (first_bad < 0 && c->batch_host[i].status != 0) first_bad = i;
+    }
+    if (first_bad >= 0) {
+        const int status = c->batch_host[first_bad].status;
+        return fail(c, (lts_status)status, "field " + std::to_string(first_bad) + ": " + status_text(status));
+    }
+    return LTS_OK;
+}
+
+lts_status lts_submit(lts_ctx* c, const lts_grid* gr, const float* d_field, const int32_t* d_authorized,
+                      int64_t n_authorized, lts_mode mode, float* d_out_field, int32_t* d_out_order,
+                      uint64_t* ticket) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    if (!ticket) return fail(c, LTS_ERR_ARG, "null ticket");
+    Lane& L = c->lane[0];
+    long long n;
+    lts_status st = check_field(c, gr, L.nmax, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order,
+                                &n, "");
+    if (st != LTS_OK) return st;
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
+    if ((st = ensure_ring(c)) != LTS_OK) return st;
+    cudaError_t e;
+    if (L.dirty) {
+        if ((e = clean_workspace(L)) != cudaSuccess) return cuda_fail(c, L, e, "clean");
+        L.dirty = false;
+    }
+    const unsigned long long t = c->next_ticket;
+    const int slot = (int)(t % kRing);
+    // the slot's previous request must be finished before the slot is reused
+    if (t > kRing && (e = cudaEventSynchronize(c->ring_ev[slot])) != cudaSuccess) return cuda_fail(c, L, e, "wait");
+    c->ring_host[slot].ticket = 0;
+    const Geom g = geom_of(gr, n);
+    if ((e = enqueue_simplify(L, g, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order, c->sms,
+                              c->ring_dev + slot, t)) != cudaSuccess)
+        return cuda_fail(c, L, e, "launch");
+    if ((e = cudaEventRecord(c->ring_ev[slot], L.stream)) != cudaSuccess) return cuda_fail(c, L, e, "record");
+    c->next_ticket = t + 1;
+    *ticket = t;
+    return LTS_OK;
+}
+
+lts_status lts_poll(lts_ctx* c, uint64_t ticket, int* done) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    if (!done) return fail(c, LTS_ERR_ARG, "null done flag");
+    *done = 0;
+    if (ticket == 0 || ticket >= c->next_ticket || !c->ring_ready) return fail(c, LTS_ERR_ARG, "unknown ticket");
+    if (ticket + kRing < c->next_ticket) return fail(c, LTS_ERR_ARG, "ticket expired (its slot was reused)");
+    const int slot = (int)(ticket % kRing);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
+    const cudaError_t q = cudaEventQuery(c->ring_ev[slot]);
+    if (q == cudaErrorNotReady) return LTS_OK;
+    if (q != cudaSuccess) return cuda_fail(c, c->lane[0], q, "query");
+    const volatile ReqResult* r = c->ring_host + slot;
+    if (r->ticket != ticket) return fail(c, LTS_ERR_INTERNAL, "request result missing");
+    *done = 1;
+    const int status = r->status;
+    if (status != 0) return fail(c, (lts_status)status, status_text(status));
     return LTS_OK;
 }
 

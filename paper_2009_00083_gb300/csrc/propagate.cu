@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
 }
 
 template <int DIR, int NN>
-__global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
+__global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
     constexpr int TS = TeamCfg<NN>::TS, E = TeamCfg<NN>::E;
     DevCounters* ctr = a.ctr;
     int* st = &ctr->status;
@@ -645,7 +645,7 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
     return cudaGetLastError();
 }
 
-int propagate_lanes(int sms) { return sms * 8 * kThreads; }
+int propagate_lanes(int sms) { return sms * 10 * kThreads; }
 long long propagate_log_slack(int lanes) { return (long long)lanes * kLogChunk; }
 long long propagate_spill_slack(int lanes) { return (long long)lanes * kSpillChunk; }
 long long propagate_heap_slack(int lanes) { return (long long)lanes * 64; }
