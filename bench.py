@@ -55,11 +55,13 @@ def parse():
     p.add_argument("--workload", default="boxnoise3d_512")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
 
 def load_workload(name):
-    from tests.golden import make_golden as mg
+    from tests.golden import store as mg
 
     rec = mg.load_record(name)
     ids = mg.load_authorized(name)
@@ -182,6 +184,121 @@ def run_reference(args):
     }))
 
 
+def _load_set(name, make_field, specs):
+    """Fields of a stored multi-field workload (hash-checked) and their authorized lists."""
+    from tests.golden import store as mg
+
+    rec = mg.load_record(name)
+    auth = mg.load_set_authorized(name)
+    fields = []
+    for spec, fr in zip(specs, rec["fields"]):
+        f = make_field(spec)
+        if W.sha256_of(f) != fr["field_sha256"]:
+            raise RuntimeError(f"{name}: generated field does not match the stored hash")
+        fields.append(f)
+    return rec, fields, auth
+
+
+def batch_leg(lts, torch, dev, reps=3):
+    """The 256-field batch (2D squares of side 64..1024 and 3D cubes of side
+    32..160, 125.6 Mvertices): one plain lts_simplify per field against one
+    lts_simplify_batch call; inputs resident on the device; wall clock around
+    synchronized calls, median of `reps` after one warm-up."""
+    rec, fs, auth = _load_set("mixed_batch_256", W.batch_field, W.batch_specs(256))
+    fields = [torch.from_numpy(f).to(dev) for f in fs]
+    ids = [torch.from_numpy(a).to(dev) for a in auth]
+    total = sum(f.numel() for f in fields)
+    ctx = lts.Context(max(f.numel() for f in fields), device=dev.index)
+    outs = [(torch.empty_like(f), torch.empty(f.shape, dtype=torch.int32, device=dev)) for f in fields]
+    grids = [lts.grid_of_shape(tuple(f.shape)) for f in fields]
+
+    def plain():
+        for f, a, (g, o) in zip(fields, ids, outs):
+            ctx.simplify(f, a, "both", out_field=g, out_order=o, with_stats=False)
+
+    def batched():
+        code = lts.lts_simplify_batch(ctx._ctx, grids, [f.data_ptr() for f in fields], [a.data_ptr() for a in ids],
+                                      [a.numel() for a in ids], "both", [g.data_ptr() for g, _ in outs],
+                                      [o.data_ptr() for _, o in outs])
+        if code != 0:
+            raise lts.LtsError(code, lts.lts_last_error(ctx._ctx))
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize(dev)
+            ts.append(time.perf_counter() - t)
+        return statistics.median(ts)
+
+    tp = timed(plain)
+    tb = timed(batched)
+    parity = all(W.sha256_of(o.cpu().numpy()) == fr["order_sha256"] and W.sha256_of(g.cpu().numpy()) == fr["g_sha256"]
+                 for (g, o), fr in zip(outs, rec["fields"]))
+    ctx.close()
+    return {"workload": "mixed_batch_256: 128 2D squares (side 64..1024) + 128 3D cubes (side 32..160)",
+            "fields": len(fields), "vertices": total, "plain_mvps": round(total / tp / 1e6, 1),
+            "batched_mvps": round(total / tb / 1e6, 1), "plain_ms": round(tp * 1e3, 2),
+            "batched_ms": round(tb * 1e3, 2), "parity_vs_oracle": bool(parity),
+            "timing": f"wall clock around synchronized calls, median of {reps}, inputs on the device"}
+
+
+def serve_leg(lts, torch, dev, nreq=2000, warm=100, rate=200.0):
+    """Served requests: Poisson arrivals at `rate`/s, each a 3D cube (side
+    32..256) from a pool of the first 16 requests of the served workload,
+    submitted with lts_submit at its arrival time and polled with lts_poll;
+    latency = completion seen by the poller - scheduled arrival; the first
+    `warm` requests are excluded.  Inputs resident on the device."""
+    specs = W.serve_specs(16)
+    rec, fs, auth = _load_set("serve_pool_16", W.serve_field, specs)
+    fields = [torch.from_numpy(f).to(dev) for f in fs]
+    ids = [torch.from_numpy(a).to(dev) for a in auth]
+    outs = [(torch.empty_like(f), torch.empty(f.shape, dtype=torch.int32, device=dev)) for f in fields]
+    grids = [lts.grid_of_shape(tuple(f.shape)) for f in fields]
+    ctx = lts.Context(max(f.numel() for f in fields), device=dev.index)
+    for f, a, (g, o) in zip(fields, ids, outs):
+        ctx.simplify(f, a, "both", out_field=g, out_order=o, with_stats=False)
+    torch.cuda.synchronize(dev)
+    arr = W.serve_arrivals(nreq, rate)
+    lat = np.zeros(nreq)
+    pending = {}
+    errors = 0
+    i = 0
+    t0 = time.perf_counter()
+    while i < nreq or pending:
+        now = time.perf_counter() - t0
+        while i < nreq and arr[i] <= now:
+            k = i % len(fields)
+            g, o = outs[k]
+            code, t = lts.lts_submit(ctx._ctx, grids[k], fields[k].data_ptr(), ids[k].data_ptr(), ids[k].numel(),
+                                     "both", g.data_ptr(), o.data_ptr())
+            if code != 0:
+                raise lts.LtsError(code, lts.lts_last_error(ctx._ctx))
+            pending[t] = i
+            i += 1
+        for t in list(pending):
+            code, done = lts.lts_poll(ctx._ctx, t)
+            if done:
+                j = pending.pop(t)
+                lat[j] = time.perf_counter() - t0 - arr[j]
+                errors += code != 0
+        if not pending and i < nreq:
+            wait = arr[i] - (time.perf_counter() - t0) - 2e-4
+            if wait > 0:
+                time.sleep(wait)
+    ctx.close()
+    sizes = [f.numel() for f in fields]
+    served = lat[warm:] * 1e3
+    return {"workload": "serve_3d: Poisson arrivals, 3D cubes of side 32..256 (pool of 16 cycled)",
+            "requests": nreq, "warmup_excluded": warm, "rate_hz": rate,
+            "mean_vertices": int(np.mean([sizes[j % len(sizes)] for j in range(nreq)])),
+            "p50_ms": round(float(np.percentile(served, 50)), 3), "p99_ms": round(float(np.percentile(served, 99)), 3),
+            "mean_ms": round(float(np.mean(served)), 3), "errors": int(errors)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -284,6 +401,8 @@ def main():
     achieved = BYTES_PER_VERTEX[dom] * n / (dom_us * 1e-6) / 1e9
     path_achieved = PATH_BYTES_PER_VERTEX * n / (ms * 1e-3) / 1e9
     cpu = None if args.no_cpu_baseline else cpu_baseline()
+    batch = None if args.no_batch or world > 1 else batch_leg(lts, torch, dev)
+    serve = None if args.no_serve or world > 1 else serve_leg(lts, torch, dev)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mvertices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
@@ -302,6 +421,8 @@ def main():
                                      "max_local_floods", "heap_spills")},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batch": batch,
+        "serve": serve,
         "clocks": clk.summary(),
         "gpu_launches": int(st.get("launches", 0)) * args.steps,
     }

@@ -26,7 +26,7 @@ namespace lts {
 // Final state of one request, written on the device after its last kernel.
 struct ReqResult {
     int status;
-    int pad;
+    int oom_pool;
     PassStats ps[2];
     unsigned long long ticket;
 };
@@ -84,8 +84,8 @@ Sizes sizes_for(long long n, int sms) {
     z.lanes = propagate_lanes(sms);
     z.tiles = (n + 4095) / 4096;
     z.log_cap = n + z.half + propagate_log_slack((int)z.lanes);
-    z.spill_cap = std::min<long long>(4 * n + propagate_spill_slack((int)z.lanes), (1LL << 31) - 1);
-    z.heap_cap = 2 * n + propagate_heap_slack((int)z.lanes);
+    z.spill_cap = std::min<long long>(8 * n + propagate_spill_slack((int)z.lanes), (1LL << 31) - 1);
+    z.heap_cap = 4 * n + propagate_heap_slack((int)z.lanes);
     z.lo_cap = n + z.half;
     z.nblk = (n + 31) / 32;
     z.scan_tiles = std::max<long long>(scan_tiles_for(z.half + 1), (z.nblk + 4095) / 4096 + 1);
@@ -99,7 +99,7 @@ size_t bytes_for(const Sizes& z) {
     b += ((size_t)z.n + 31) / 32 * 4;               // authorized bitmap
     b += 2 * 4 * (size_t)z.n + 8 * (size_t)z.n;     // owner, loc, qmark
     b += 8 * 4 * (size_t)z.half;                    // U and class records
-    b += 16 * (size_t)z.half;                       // task records
+    b += 32 * (size_t)z.half;                       // task records, heap records
     b += 4 * (size_t)z.n;                           // saddle arrival counters
     b += 4 * (size_t)z.spill_cap + 8 * (size_t)z.heap_cap + 4 * (size_t)z.log_cap;
     b += 11 * 4 * (size_t)z.half;                   // region records
@@ -159,7 +159,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     ok = ok && dev_alloc(L, &w.U, z.half) && dev_alloc(L, &w.parent, z.half) && dev_alloc(L, &w.wait_v, z.half) &&
          dev_alloc(L, &w.cnt, z.n) && dev_alloc(L, &w.tasks, z.half) &&
          dev_alloc(L, &w.sib_head, z.half) && dev_alloc(L, &w.sib_next, z.half) &&
-         dev_alloc(L, &w.spill_base, z.half) && dev_alloc(L, &w.spill_n, z.half);
+         dev_alloc(L, &w.spill_base, z.half) && dev_alloc(L, &w.spill_n, z.half) && dev_alloc(L, &w.heaprec, z.half);
     ok = ok && dev_alloc(L, &w.spill_pool, z.spill_cap) && dev_alloc(L, &w.heap_pool, z.heap_cap) &&
          dev_alloc(L, &w.vlog, z.log_cap);
     ok = ok && dev_alloc(L, &w.class2reg, z.half) && dev_alloc(L, &w.reg_class, z.half) &&
@@ -232,11 +232,15 @@ lts_status cuda_fail(lts_ctx* c, Lane& L, cudaError_t e, const char* where) {
     return LTS_ERR_CUDA;
 }
 
-const char* status_text(int status) {
+std::string status_text(int status, int oom_pool = 0) {
+    if (status == LTS_ERR_OOM) {
+        const char* pool = oom_pool == 1 ? " (flood overflow heaps)" : oom_pool == 2 ? " (queue spill pool)"
+                         : oom_pool == 3 ? " (visited-vertex log)" : "";
+        return std::string("a workspace pool was exhausted") + pool;
+    }
     return status == LTS_ERR_NAN ? "the field holds a NaN"
          : status == LTS_ERR_NO_AUTHORIZED ? "a pass has unauthorized extrema but no authorized one"
          : status == LTS_ERR_ARG ? "an authorized id is out of range"
-         : status == LTS_ERR_OOM ? "a workspace pool was exhausted"
          : status == LTS_ERR_TIMEOUT ? "a bounded device wait expired"
          : "internal consistency check failed";
 }
@@ -278,8 +282,8 @@ lts_status check_field(lts_ctx* c, const lts_grid* gr, long long nmax, const flo
 
 namespace lts {
 cudaError_t pass_reset(Work& w, cudaStream_t s) {
-    // every counter but the status word
-    cudaMemsetAsync(reinterpret_cast<char*>(w.ctr) + sizeof(int), 0, sizeof(DevCounters) - sizeof(int), s);
+    // every counter but the status word and the pool it names
+    cudaMemsetAsync(reinterpret_cast<char*>(w.ctr) + 2 * sizeof(int), 0, sizeof(DevCounters) - 2 * sizeof(int), s);
     cudaMemsetAsync(w.rblk, 0, sizeof(RankBlk) * (size_t)w.nblk_cur, s);
     return cudaGetLastError();
 }
@@ -298,6 +302,7 @@ __global__ void save_pass_kernel(const DevCounters* ctr, const int* reg_start, P
 // the request's final status and pass statistics
 __global__ void capture_kernel(const DevCounters* ctr, const PassStats* ps, ReqResult* out, unsigned long long ticket) {
     out->status = ctr->status;
+    out->oom_pool = ctr->oom_pool;
     out->ps[0] = ps[0];
     out->ps[1] = ps[1];
     out->ticket = ticket;
@@ -492,7 +497,7 @@ lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, co
         fill_stats(*opt_stats, n, hps, w.launches);
         fill_stage_times(*opt_stats, L);
     }
-    if (status != 0) return fail(c, (lts_status)status, status_text(status));
+    if (status != 0) return fail(c, (lts_status)status, status_text(status, w.h_ctr->oom_pool));
     return LTS_OK;
 }
 
@@ -591,7 +596,8 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
     }
     if (first_bad >= 0) {
         const int status = c->batch_host[first_bad].status;
-        return fail(c, (lts_status)status, "field " + std::to_string(first_bad) + ": " + status_text(status));
+        return fail(c, (lts_status)status, "field " + std::to_string(first_bad) + ": " +
+                                               status_text(status, c->batch_host[first_bad].oom_pool));
     }
     return LTS_OK;
 }
@@ -645,7 +651,7 @@ lts_status lts_poll(lts_ctx* c, uint64_t ticket, int* done) {
     if (r->ticket != ticket) return fail(c, LTS_ERR_INTERNAL, "request result missing");
     *done = 1;
     const int status = r->status;
-    if (status != 0) return fail(c, (lts_status)status, status_text(status));
+    if (status != 0) return fail(c, (lts_status)status, status_text(status, r->oom_pool));
     return LTS_OK;
 }
 

@@ -80,13 +80,14 @@ constexpr long long kSpinLimit = 1LL << 26;
 // Scalars produced and consumed on the device, read back once per call.
 struct DevCounters {
     int status;
+    int oom_pool;          // the pool that ran out: 1 overflow heap, 2 spill, 3 vertex log
     int n_unauth;          // |U| of the current pass
     int n_auth_ext;        // authorized extrema present in the current pass
     int n_regions;
     int n_saddles;         // distinct saddles (head regions)
     int log_cursor;        // visited-vertex log length (chunk reserved)
     int seed_cursor;
-    int spill_cursor;
+    long long spill_cursor; // spill pool (ints)
     long long heap_cursor; // lane heap pool (entries)
     int max_region;
     int max_floods;
@@ -100,6 +101,11 @@ struct DevCounters {
     int n_big;             // regions for the HBM tier of step 2
     int n_tasks;           // propagation tasks left after the first step
 };
+
+__device__ __forceinline__ void set_oom(DevCounters* ctr, int pool) {
+    atomicCAS(&ctr->oom_pool, 0, pool);
+    set_status(&ctr->status, LTS_ERR_OOM);
+}
 
 // Per-pass statistics accumulated into the host stats.
 struct PassStats {
@@ -142,7 +148,7 @@ struct Work {
     int* sib_head; int* sib_next;        // per class: regions listed under the claimer of their saddle
     int4* tasks;                         // propagation tasks after the first step
     int* cnt;                            // per vertex: arrival counter of a saddle
-    int* spill_base; int* spill_n;
+    int* spill_base; int* spill_n; int4* heaprec;
     int* spill_pool; long long spill_cap;
     unsigned long long* heap_pool; long long heap_cap;
     int* vlog; long long log_cap;

@@ -71,6 +71,7 @@ struct PropArgs {
     int* cnt;
     int* spill_base;
     int* spill_n;
+    int4* heaprec;               // a stopped class's overflow heap: (offset low, offset high, entries, capacity)
     int* spill_pool;
     long long spill_cap;
     unsigned long long* heap_pool;
@@ -117,9 +118,9 @@ struct Overflow {
 
 __device__ bool ov_push(Overflow& H, unsigned long long e, const PropArgs& a) {
     if (H.n == H.cap) {
-        const int ncap = max(4 * H.cap, 256);
+        const int ncap = max(2 * H.cap, 256);
         const long long off = atomicAdd((unsigned long long*)&a.ctr->heap_cursor, (unsigned long long)ncap);
-        if (off + ncap > a.heap_cap) { set_status(&a.ctr->status, LTS_ERR_OOM); return false; }
+        if (off + ncap > a.heap_cap) { set_oom(a.ctr, 1); return false; }
         unsigned long long* nh = a.heap_pool + off;
         for (int i = 0; i < H.n; ++i) nh[i] = H.h[i];
         if (H.cap == 0) atomicAdd(&a.ctr->heap_spills, 1);
@@ -252,18 +253,19 @@ __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, cons
 }
 
 // The queue of a class that stopped at its first pop u: the neighbours of its
-// seed m but u (marked as queued by the class `mark`).
+// seed m but u, inserted unless the class `mark` already queued them.
 template <int DIR, int NN>
 __device__ __forceinline__ bool rebuild_first_queue(TeamState<NN>& T, const Geom& g, const int* __restrict__ O, int m,
                                                     int u, unsigned long long mark, const PropArgs& a, int tl) {
     int x, y, z;
     coords_of(g, m, x, y, z);
     const int nb = tl < NN ? nbr_q<NN>(g, x, y, z, tl) : -1;
-    const bool cand = nb >= 0 && nb != u;
+    bool cand = nb >= 0 && nb != u;
     int key = 0;
     if (cand) {
         key = od<DIR>(__ldg(O + nb), g.n);
-        __stcg(a.qmark + nb, mark);
+        if (__ldcg(a.qmark + nb) == mark) cand = false;
+        else __stcg(a.qmark + nb, mark);
     }
     return insert_batch(T, cand, key, nb, a);
 }
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
         return;
     }
     if (2LL * nU > a.log_cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&ctr->status, LTS_ERR_OOM);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_oom(ctr, 3);
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->log_cursor = 2 * nU;
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
             const int seed = __shfl_sync(T.tmask, t.w, T.tb);
 #pragma unroll
             for (int e = 0; e < E; ++e) T.sk[e] = -1;
-            T.ov.n = 0; T.ovn = 0; T.ov_top = -1;
+            T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0; T.ovn = 0; T.ov_top = -1;
             const unsigned long long mk = a.tag | (unsigned)c;
             bool ok;
             if (seed >= 0) {                           // u has one higher neighbour, the seed of c
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                     log_end = log_pos + kLogChunk;
                     if (log_end > a.log_cap) {
                         log_pos = log_end = 0;
-                        set_status(st, LTS_ERR_OOM);
+                        set_oom(ctr, 3);
                         decision = -1;
                     }
                 }
@@ -510,19 +512,21 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                 break;
             }
             // ---- arrival at the saddle v ----
-            // the queue must be readable by whoever releases this class
+            // The queue must be readable by whoever releases this class: the
+            // register part is copied to the spill pool, and the overflow heap
+            // stays where it is, its block recorded with the class.
             int nreg = 0;
 #pragma unroll
             for (int e = 0; e < E; ++e) nreg += T.sk[e] >= 0;
-            const int total = __reduce_add_sync(T.tmask, nreg) + T.ovn;
+            const int total = __reduce_add_sync(T.tmask, nreg);
             long long base = 0;
             int okr = 1;
             if (leader) {
                 if (sp_end - sp_pos < 2 * total) {
                     const int want = max(2 * total, kSpillChunk);
-                    sp_pos = atomicAdd(&ctr->spill_cursor, want);
+                    sp_pos = (long long)atomicAdd((unsigned long long*)&ctr->spill_cursor, (unsigned long long)want);
                     sp_end = sp_pos + want;
-                    if (sp_end > a.spill_cap) { set_status(st, LTS_ERR_OOM); okr = 0; sp_pos = sp_end = 0; }
+                    if (sp_end > a.spill_cap) { set_oom(ctr, 2); okr = 0; sp_pos = sp_end = 0; }
                 }
                 base = sp_pos;
                 sp_pos += 2 * total;
@@ -543,27 +547,26 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                 }
                 pos += 2 * __popc(m);
             }
-            if (T.ovn > 0) {
-                const unsigned long long* oh = reinterpret_cast<const unsigned long long*>(
-                    __shfl_sync(T.tmask, reinterpret_cast<unsigned long long>(T.ov.h), T.tb));
-                for (int i = tl; i < T.ovn; i += TS) {
-                    __stcg(a.spill_pool + pos + 2 * i, (int)(oh[i] & 0xffffffffu));
-                    __stcg(a.spill_pool + pos + 2 * i + 1, (int)(oh[i] >> 32));
-                }
-            }
             __syncwarp(T.tmask);                       // orders the team's spill writes before the leader's release
             int tot = 0;
             if (leader) {
                 __stcg(a.spill_base + c, (int)base);
                 __stcg(a.spill_n + c, total);
                 __stcg(a.wait_v + c, v);
+                const long long ho = T.ov.h ? (long long)(T.ov.h - a.heap_pool) : 0;
+                __stcg(a.heaprec + c, make_int4((int)(ho & 0xffffffffLL), (int)(ho >> 32), T.ov.n, T.ov.cap));
                 // release: this class's spill and records; acquire: those of the
                 // classes that arrived before
                 cuda::atomic_ref<int, cuda::thread_scope_device> counter(a.cnt[v]);
                 tot = counter.fetch_add(k, cuda::memory_order_acq_rel) + k;
             }
             tot = __shfl_sync(T.tmask, tot, T.tb);
-            if (tot < h) { c = -1; continue; }        // a higher neighbour is still unvisited: stop
+            if (tot < h) {                             // a higher neighbour is still unvisited: stop
+                c = -1;
+                T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0;   // the heap block now belongs to the class
+                T.ovn = 0; T.ov_top = -1;
+                continue;
+            }
             // ---- last arrival: merge every class stopped at v ----
             // Every higher neighbour of v now belongs to a class waiting at v:
             // those classes are the roots of the neighbours' owners.
@@ -574,9 +577,11 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
             const unsigned grp = __match_any_sync(T.tmask, rt);
             const bool rep_lane = higher && rt != c && rt >= 0 && (__ffs(grp & hmask) - 1) == T.lane;
             int sb = 0, sn = 0;
+            int4 hr = make_int4(0, 0, 0, 0);
             if (rep_lane) {                            // one lane per class to merge
                 sb = __ldcg(a.spill_base + rt);
                 sn = __ldcg(a.spill_n + rt);
+                if (sn >= 0) hr = __ldcg(a.heaprec + rt);
                 __stcg(a.parent + rt, c);
             }
             unsigned todo = __ballot_sync(T.tmask, rep_lane);
@@ -595,11 +600,31 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                     bool hs = idx < rsn;
                     int u = 0, ou = 0;
                     if (hs) {
+                        // entries the class already queued are dropped: melded
+                        // queues of neighbouring classes share much of their frontier
                         u = __ldcg(a.spill_pool + rsb + 2 * idx);
                         ou = __ldcg(a.spill_pool + rsb + 2 * idx + 1);
-                        __stcg(a.qmark + u, mark);
+                        if (__ldcg(a.qmark + u) == mark) hs = false;
+                        else __stcg(a.qmark + u, mark);
                     }
                     okm = insert_batch(T, hs, ou, u, a);
+                }
+                // its overflow heap: keep the larger heap, push the smaller one's
+                // entries into it (each entry moves O(log) times over the pass)
+                const int rhn = __shfl_sync(T.tmask, hr.z, L);
+                if (rhn > 0 && okm) {
+                    const int rlo = __shfl_sync(T.tmask, hr.x, L), rhi = __shfl_sync(T.tmask, hr.y, L);
+                    const int rcap = __shfl_sync(T.tmask, hr.w, L);
+                    int hok = 1;
+                    if (leader) {
+                        const long long off = ((long long)rhi << 32) | (unsigned)rlo;
+                        Overflow R{a.heap_pool + off, rhn, rcap};
+                        if (R.n > T.ov.n) { const Overflow t2 = T.ov; T.ov = R; R = t2; }
+                        for (int i = 0; i < R.n && hok; ++i) hok = ov_push(T.ov, __ldcg(R.h + i), a) ? 1 : 0;
+                    }
+                    hok = __shfl_sync(T.tmask, hok, T.tb);
+                    ov_sync(T);
+                    okm = hok != 0;
                 }
             }
             if (!okm) break;
@@ -629,7 +654,7 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
     PropArgs a;
     a.U = w.U; a.owner = w.owner; a.qmark = w.qmark; a.tag = (unsigned long long)(++w.pass_tag) << 32;
     a.parent = w.parent; a.wait_v = w.wait_v; a.cnt = w.cnt;
-    a.spill_base = w.spill_base; a.spill_n = w.spill_n;
+    a.spill_base = w.spill_base; a.spill_n = w.spill_n; a.heaprec = w.heaprec;
     a.spill_pool = w.spill_pool; a.spill_cap = w.spill_cap; a.heap_pool = w.heap_pool; a.heap_cap = w.heap_cap;
     a.vlog = w.vlog; a.log_cap = w.log_cap; a.tasks = w.tasks; a.ctr = w.ctr;
     const int pb = sms * 8;
@@ -646,9 +671,10 @@ cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_
 }
 
 int propagate_lanes(int sms) { return sms * 10 * kThreads; }
-long long propagate_log_slack(int lanes) { return (long long)lanes * kLogChunk; }
-long long propagate_spill_slack(int lanes) { return (long long)lanes * kSpillChunk; }
-long long propagate_heap_slack(int lanes) { return (long long)lanes * 64; }
+// pool slack: every warp may hold one partly used reservation of each pool
+long long propagate_log_slack(int lanes) { return (long long)(lanes / 32) * kLogChunk; }
+long long propagate_spill_slack(int lanes) { return (long long)(lanes / 32) * kSpillChunk; }
+long long propagate_heap_slack(int lanes) { return (long long)(lanes / 32) * 2048; }
 
 template cudaError_t propagate<1>(Work&, const Geom&, const int*, int, cudaStream_t);
 template cudaError_t propagate<-1>(Work&, const Geom&, const int*, int, cudaStream_t);

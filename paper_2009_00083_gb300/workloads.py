@@ -27,6 +27,12 @@ CONFIGS = {
     0: dict(name="gauss2d_256", shape=(256, 256), K=16, noise=0.05, thr=0.05, kind="gauss"),
     1: dict(name="gauss3d_128", shape=(128, 128, 128), K=64, noise=0.02, thr=0.01, kind="gauss"),
     2: dict(name="boxnoise3d_512", shape=(512, 512, 512), radius=2, levels=1024, thr=0.10, kind="box"),
+    # many fields at once: even k a 2D square of side exp(U[ln 64, ln 1024]), odd k a 3D cube of side
+    # exp(U[ln 32, ln 160]); the generator of config 0; threshold U[1%, 10%] per field
+    3: dict(name="mixed_batch_256", count=256, K=16, noise=0.05, kind="batch"),
+    # served requests: 3D cubes of side exp(U[ln 32, ln 256]); the generator of config 1; threshold
+    # U[0.5%, 10%] per request; Poisson arrivals at 200/s
+    4: dict(name="serve_3d", K=64, noise=0.02, rate_hz=200.0, kind="serve"),
 }
 
 
@@ -139,3 +145,47 @@ def dims_of(shape):
 
 def log_uniform_int(rng, lo, hi):
     return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def batch_specs(count=256):
+    """Shapes, thresholds and seeds of the fields of the batch workload
+    (config 3), drawn in field order from their own generator."""
+    rng = np.random.Generator(np.random.PCG64(seed_of(3, 999)))
+    specs = []
+    for k in range(count):
+        if k % 2 == 0:
+            side = int(round(float(np.exp(rng.uniform(np.log(64.0), np.log(1024.0))))))
+            shape = (side, side)
+        else:
+            side = int(round(float(np.exp(rng.uniform(np.log(32.0), np.log(160.0))))))
+            shape = (side, side, side)
+        specs.append(dict(shape=shape, thr=float(rng.uniform(0.01, 0.10)), seed=seed_of(3, k)))
+    return specs
+
+
+def batch_field(spec):
+    c = CONFIGS[3]
+    return gaussian_field(spec["shape"], c["K"], c["noise"], spec["seed"])
+
+
+def serve_specs(count):
+    """Shapes, thresholds and seeds of served requests (config 4)."""
+    rng = np.random.Generator(np.random.PCG64(seed_of(4, 999)))
+    specs = []
+    for k in range(count):
+        side = int(round(float(np.exp(rng.uniform(np.log(32.0), np.log(256.0))))))
+        specs.append(dict(shape=(side, side, side), thr=float(rng.uniform(0.005, 0.10)), seed=seed_of(4, k)))
+    return specs
+
+
+def serve_field(spec):
+    c = CONFIGS[4]
+    return gaussian_field(spec["shape"], c["K"], c["noise"], spec["seed"])
+
+
+def serve_arrivals(count, rate_hz=200.0):
+    """Arrival times (seconds from the first) of a Poisson process."""
+    rng = np.random.Generator(np.random.PCG64(seed_of(4, 998)))
+    gaps = rng.exponential(1.0 / rate_hz, count)
+    gaps[0] = 0.0
+    return np.cumsum(gaps)

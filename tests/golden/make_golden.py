@@ -7,6 +7,8 @@ extrema always kept), and the SHA-256 of the oracle's simplified field g and
 order field (mode both: minima pass, then maxima pass) with its statistics.
 
     python tests/golden/make_golden.py boxnoise3d_512
+    python tests/golden/make_golden.py mixed_batch_256    # config 3, 256 fields
+    python tests/golden/make_golden.py serve_pool_16      # config 4, the first 16 requests
 
 The GPU tests regenerate the field, check its hash, run the library with the
 stored authorized list and compare the hashes of its outputs; bench.py uses
@@ -60,16 +62,51 @@ def main(name):
     print(json.dumps(rec, indent=1))
 
 
-def load_authorized(name):
-    """Authorized ids stored by main() (delta-encoded, sorted)."""
-    d = np.load(os.path.join(HERE, f"{name}_authorized.npz"))
-    return np.cumsum(d["ids"].astype(np.int64)).astype(np.int32)
+SETS = {"mixed_batch_256": ("batch", 256), "serve_pool_16": ("serve", 16)}
 
 
-def load_record(name):
-    with open(os.path.join(HERE, f"{name}.json")) as fh:
-        return json.load(fh)
+def _specs(name):
+    kind, count = SETS[name]
+    return W.batch_specs(count) if kind == "batch" else W.serve_specs(count)
+
+
+def _one_field(args):
+    name, k = args
+    kind, _ = SETS[name]
+    spec = _specs(name)[k]
+    f = W.batch_field(spec) if kind == "batch" else W.serve_field(spec)
+    O = oracle.order_field(f)
+    ids = oracle.authorized_by_persistence(f, spec["thr"], O)
+    g, Og = oracle.lts(f, ids, mode="both")
+    return k, W.sha256_of(f), np.sort(ids).astype(np.int64), W.sha256_of(g), W.sha256_of(Og)
+
+
+def main_set(name, procs=8):
+    """A set of fields (one record each): field hash, authorized ids, output hashes."""
+    import multiprocessing as mp
+
+    specs = _specs(name)
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = sorted(pool.map(_one_field, [(name, k) for k in range(len(specs))], chunksize=1))
+    ids = [r[2] for r in res]
+    off = np.cumsum([0] + [len(i) for i in ids])
+    flat = np.concatenate([np.diff(np.concatenate([[0], i])) for i in ids]).astype(np.int32)
+    np.savez_compressed(os.path.join(HERE, f"{name}_authorized.npz"), ids=flat, offsets=off.astype(np.int64))
+    rec = {"workload": name, "fields": [
+        {"shape": list(spec["shape"]), "thr": spec["thr"], "seed": spec["seed"], "field_sha256": r[1],
+         "n_authorized": int(len(r[2])), "g_sha256": r[3], "order_sha256": r[4]}
+        for spec, r in zip(specs, res)], "oracle_seconds": round(time.time() - t0, 1)}
+    with open(os.path.join(HERE, f"{name}.json"), "w") as fh:
+        json.dump(rec, fh, indent=0)
+    print(name, len(specs), "fields,", int(off[-1]), "authorized ids,", rec["oracle_seconds"], "s")
+
+
+from tests.golden.store import load_authorized, load_record, load_set_authorized  # noqa: E402,F401
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    if sys.argv[1] in SETS:
+        main_set(sys.argv[1])
+    else:
+        main(sys.argv[1])

@@ -140,3 +140,62 @@ def test_submitted_requests_match_oracle_in_order_and_after_a_failure(lts):
         assert code == 1 and not done
     finally:
         ctx.close()
+
+
+def test_full_batch_workload_against_stored_oracle_hashes(lts):
+    """The 256-field batch workload (2D 64..1024 squares, 3D 32..160 cubes,
+    125,571,267 vertices) in one lts_simplify_batch call: every field's g and
+    order field hash equal the oracle's stored ones."""
+    from tests.golden import store as mg
+
+    rec = mg.load_record("mixed_batch_256")
+    auth = mg.load_set_authorized("mixed_batch_256")
+    specs = W.batch_specs(256)
+    dev = torch.device("cuda", 0)
+    fields, ids = [], []
+    for spec, fr, a in zip(specs, rec["fields"], auth):
+        f = W.batch_field(spec)
+        assert W.sha256_of(f) == fr["field_sha256"]
+        fields.append(torch.from_numpy(f).to(dev))
+        ids.append(torch.from_numpy(a).to(dev))
+    ctx = lts.Context(max(f.numel() for f in fields), device=0)
+    try:
+        outs, _ = ctx.simplify_batch(fields, ids, "both", with_stats=False)
+        torch.cuda.synchronize()
+        for k, ((g, o), fr) in enumerate(zip(outs, rec["fields"])):
+            assert W.sha256_of(o.cpu().numpy()) == fr["order_sha256"], f"field {k} {fr['shape']}: order"
+            assert W.sha256_of(g.cpu().numpy()) == fr["g_sha256"], f"field {k} {fr['shape']}: field"
+    finally:
+        ctx.close()
+
+
+def test_served_pool_against_stored_oracle_hashes(lts):
+    """The first 16 served requests (3D cubes of side 32..256) through
+    lts_submit / lts_poll, all queued at once."""
+    from tests.golden import store as mg
+
+    rec = mg.load_record("serve_pool_16")
+    auth = mg.load_set_authorized("serve_pool_16")
+    dev = torch.device("cuda", 0)
+    reqs = []
+    for spec, fr, a in zip(W.serve_specs(16), rec["fields"], auth):
+        f = W.serve_field(spec)
+        assert W.sha256_of(f) == fr["field_sha256"]
+        reqs.append((torch.from_numpy(f).to(dev), torch.from_numpy(a).to(dev)))
+    ctx = lts.Context(max(f.numel() for f, _ in reqs), device=0)
+    try:
+        torch.cuda.synchronize()
+        tickets = [ctx.submit(f, a, "both") for f, a in reqs]
+        done = {}
+        while len(done) < len(tickets):
+            for k, t in enumerate(tickets):
+                if k not in done:
+                    r = ctx.poll(t)
+                    if r is not None:
+                        done[k] = r
+        for k, fr in enumerate(rec["fields"]):
+            g, o = done[k]
+            assert W.sha256_of(o.cpu().numpy()) == fr["order_sha256"], f"request {k}: order"
+            assert W.sha256_of(g.cpu().numpy()) == fr["g_sha256"], f"request {k}: field"
+    finally:
+        ctx.close()

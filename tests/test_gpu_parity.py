@@ -135,7 +135,7 @@ def test_random_authorized_sets_and_repeat(ctx_small):
 
 
 def _golden(name):
-    from tests.golden import make_golden as mg
+    from tests.golden import store as mg
 
     if not os.path.exists(os.path.join(GOLDEN, f"{name}.json")):
         pytest.skip(f"no stored values for {name}")
