@@ -18,9 +18,11 @@
 //     lane in registers (adjacency as a bit mask over the team's lanes); a
 //     propagation step is one team max/min reduction over the frontier and
 //     one broadcast of the popped vertex's adjacency;
-//   r <= 1024: one region per warp, arrays in shared memory; each step scans
-//     the frontier densely (r/32 vertices per lane) and reduces over the warp;
-//   larger: one region per lane, binary heaps in HBM scratch.
+//   r <= 128, r <= 1024 and r <= 4096: one region per warp, arrays in shared
+//     memory; each step scans the frontier densely (r/32 vertices per lane)
+//     and reduces over the warp;
+//   larger: one region per warp, a 32-ary heap in shared memory (one region
+//     per lane with binary heaps in HBM scratch when the heap overflows).
 #include <climits>
 
 #include "lts_internal.cuh"
@@ -31,6 +33,7 @@ namespace {
 
 constexpr unsigned char kBnd = 1, kVis = 2, kTried = 4;
 constexpr int kMedR = 1024;
+constexpr int kHugeR = 4096;
 constexpr int kNoNbr = 0xffff;
 
 // ---------------------------------------------------------------------------
@@ -217,20 +220,6 @@ struct LOArgs {
     const int* reg_size; const int* reg_saddle; int* lhat;
     int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
     const int* tier_list; DevCounters* ctr;
-};
-
-struct FloodStat {
-    int mx = 0;
-    long long tot = 0;
-    __device__ void add(DevCounters* ctr, int nfl) {
-        if (nfl < 0) { set_status(&ctr->status, LTS_ERR_INTERNAL); return; }
-        mx = max(mx, nfl);
-        tot += nfl;
-    }
-    __device__ void flush(DevCounters* ctr) {   // all 32 lanes
-        warp_atomic_max(&ctr->max_floods, mx);
-        warp_atomic_add64(&ctr->total_floods, tot);
-    }
 };
 
 // ---- tiers 1-2: one region per team of TS lanes (r <= TS), registers ----
@@ -560,42 +549,258 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
     }
 }
 
-// ---- tier 3: one lane per region above kMedR vertices, HBM scratch ----
+// ---- tier 6: one warp per region above kHugeR vertices ----
+// The same algorithm as local_order_run, run by a warp: the frontier is a
+// 32-ary max-heap of (biased key << 32 | local index) in shared memory, so a
+// pop sifts down one level per warp-wide load and max-reduction; the keys are
+// unique, so the pops come in the same order as with any other heap.  V, L,
+// L2 and the flags live in the region's HBM scratch; neighbours are
+// recomputed from the grid and the region tags.  A region whose frontier
+// outgrows the heap is redone by lane 0 on the single-thread path.
+constexpr int kWarpHeapCap = 28672;
+
+struct WarpRegion {
+    int* V; int* L; int* L2; unsigned char* F;
+    Geom g; const int* owner; const int* loc; int tag; int s; int m; int r;
+};
+
+__device__ __forceinline__ int wr_nbr(const WarpRegion& R, int vtx, int q) {
+    int x, y, z;
+    coords_of(R.g, vtx, x, y, z);
+    const int nb = nbr_of(R.g, x, y, z, q);
+    if (nb < 0) return -1;
+    if (nb == R.s) return R.m;
+    if (__ldg(R.owner + nb) != R.tag) return -1;
+    return __ldg(R.loc + nb);
+}
+
+// biased key: unsigned order of the (max-first) or reversed (min-first) key
+template <bool MAXF>
+__device__ __forceinline__ unsigned long long wr_entry(int key, int i) {
+    unsigned k = (unsigned)key ^ 0x80000000u;
+    if (!MAXF) k = ~k;
+    return ((unsigned long long)k << 32) | (unsigned)i;
+}
+
+// lane 0 pushes e; hn is the warp-uniform heap size
+__device__ __forceinline__ void wh_push(unsigned long long* H, int& hn, unsigned long long e, int lane) {
+    if (lane == 0) {
+        int p = hn;
+        while (p > 0) {
+            const int par = (p - 1) >> 5;
+            const unsigned long long hp = H[par];
+            if (hp >= e) break;
+            H[p] = hp;
+            p = par;
+        }
+        H[p] = e;
+    }
+    ++hn;
+    __syncwarp();
+}
+
+__device__ __forceinline__ unsigned long long wh_pop(unsigned long long* H, int& hn, int lane) {
+    const unsigned long long top = H[0];
+    --hn;
+    if (hn == 0) { __syncwarp(); return top; }
+    const unsigned long long last = H[hn];
+    int p = 0;
+    for (;;) {
+        const int c0 = p * 32 + 1;
+        if (c0 >= hn) break;
+        const int c = c0 + lane;
+        const unsigned long long hv = c < hn ? H[c] : 0ull;
+        const unsigned hi = c < hn ? (unsigned)(hv >> 32) : 0u;
+        const unsigned K = __reduce_max_sync(0xffffffffu, hi);
+        const int lm = __ffs(__ballot_sync(0xffffffffu, c < hn && hi == K)) - 1;
+        const unsigned long long mv = __shfl_sync(0xffffffffu, hv, lm);
+        if (mv <= last) break;
+        __syncwarp();
+        if (lane == 0) H[p] = mv;
+        p = c0 + lm;
+    }
+    __syncwarp();
+    if (lane == 0) H[p] = last;
+    __syncwarp();
+    return top;
+}
+
+// superlevel (MAXF) or sublevel propagation; returns the last vertex (max),
+// -2 if R was not covered, -3 if the heap overflowed
+template <bool MAXF, int NN>
+__device__ int wr_flood(const WarpRegion& R, unsigned long long* H, int lane) {
+    for (int i = lane; i < R.r; i += 32) R.F[i] &= (unsigned char)~kVis;
+    __syncwarp();
+    int hn = 0;
+    if (MAXF) {
+        if (lane == 0) R.F[R.m] |= kVis;
+        wh_push(H, hn, wr_entry<true>(R.L[R.m], R.m), lane);
+    } else {
+        for (int b = 0; b < R.m; b += 32) {
+            const int i = b + lane;
+            const bool sd = i < R.m && (R.F[i] & kBnd);
+            if (sd) R.F[i] |= kVis;
+            const int key = sd ? R.L[i] : 0;
+            unsigned mk = __ballot_sync(0xffffffffu, sd);
+            while (mk) {
+                const int l = __ffs(mk) - 1;
+                mk &= mk - 1;
+                const int ki = __shfl_sync(0xffffffffu, key, l);
+                if (hn >= kWarpHeapCap) return -3;
+                wh_push(H, hn, wr_entry<false>(ki, b + l), lane);
+            }
+        }
+    }
+    int cnt = 0, last = -1;
+    while (hn > 0) {
+        const unsigned long long top = wh_pop(H, hn, lane);
+        const int i = (int)(top & 0xffffffffu);
+        if (lane == 0) R.L2[i] = MAXF ? R.r - 1 - cnt : cnt;
+        ++cnt;
+        last = i;
+        const int vtx = R.V[i];
+        int j = -1, key = 0;
+        if (lane < NN) {
+            j = wr_nbr(R, vtx, lane);
+            if (j >= 0 && !(R.F[j] & kVis)) {
+                R.F[j] |= kVis;
+                key = R.L[j];
+            } else {
+                j = -1;
+            }
+        }
+        unsigned mk = __ballot_sync(0xffffffffu, j >= 0);
+        while (mk) {
+            const int l = __ffs(mk) - 1;
+            mk &= mk - 1;
+            const int jj = __shfl_sync(0xffffffffu, j, l);
+            const int kk = __shfl_sync(0xffffffffu, key, l);
+            if (hn >= kWarpHeapCap) return -3;
+            wh_push(H, hn, wr_entry<MAXF>(kk, jj), lane);
+        }
+    }
+    if (!MAXF) return cnt == R.r ? 0 : -2;
+    return cnt == R.r ? last : -2;
+}
+
+// some vertex (not s, for minima: without an outside neighbour) is a strict
+// local minimum (MINF) or maximum of L
+template <bool MINF, int NN>
+__device__ bool wr_has_extremum(const WarpRegion& R, int lane) {
+    bool found = false;
+    const int lim = MINF ? R.r : R.m;
+    for (int i = lane; i < lim && !found; i += 32) {
+        if (MINF && (R.F[i] & kBnd)) continue;
+        const int li = R.L[i], vtx = R.V[i];
+        bool ext = true;
+        for (int q = 0; q < NN && ext; ++q) {
+            const int j = wr_nbr(R, vtx, q);
+            if (j >= 0 && (MINF ? R.L[j] < li : R.L[j] > li)) ext = false;
+        }
+        found = ext;
+    }
+    return __any_sync(0xffffffffu, found);
+}
+
 template <int DIR, int NN>
-__global__ void __launch_bounds__(128) lo_big_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
+__global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
+    extern __shared__ unsigned long long H[];
     if (failed(&a.ctr->status)) return;
+    const int lane = threadIdx.x;
     const int cnt = *d_count;
-    FloodStat fs;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    int mx = 0;
+    long long tot = 0;
+    for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int rid = list[k];
         const int m = a.reg_size[rid];
         const int s = a.reg_saddle[rid];
         const int st0 = a.reg_start[rid];
         const long long off = (long long)st0 + rid;
-        BigStore<NN> T{a.lo_v + off, a.lo_L + off, a.lo_L2 + off, a.lo_heap + off, a.lo_flag + off,
-                       g, a.owner, a.loc, -2 - rid, s, m};
-        for (int i = 0; i < m; ++i) T.V(i) = a.members[st0 + i];
-        T.V(m) = s;
-        for (int i = 0; i <= m; ++i) {
-            const int vtx = T.V(i);
+        WarpRegion R{a.lo_v + off, a.lo_L + off, a.lo_L2 + off, a.lo_flag + off, g, a.owner, a.loc, -2 - rid, s, m,
+                     m + 1};
+        for (int i = lane; i <= m; i += 32) {
+            const int vtx = i < m ? a.members[st0 + i] : s;
+            R.V[i] = vtx;
             int x, y, z;
             coords_of(g, vtx, x, y, z);
             unsigned char fl = 0;
             for (int q = 0; q < NN; ++q) {
                 const int nb = nbr_of(g, x, y, z, q);
-                if (nb >= 0 && nb != s && __ldg(a.owner + nb) != T.tag) fl = kBnd;
+                if (nb >= 0 && nb != s && __ldg(a.owner + nb) != R.tag) fl = kBnd;
             }
-            T.F(i) = fl;
-            T.L(i) = od<DIR>(__ldg(a.O + vtx), g.n);
+            R.F[i] = fl;
+            R.L[i] = i < m ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
         }
-        T.L(m) = INT_MAX;
-        const int nfl = local_order_run<NN>(T, m);
-        fs.add(a.ctr, nfl);
-        if (nfl < 0) continue;
-        for (int i = 0; i < m; ++i) a.lhat[st0 + i] = T.L(i);
+        __syncwarp();
+        int nfl = -1;
+        bool overflow = false;
+        // the minus-infinity vertex: lowest boundary-adjacent member whose removal keeps R connected
+        bool ok = false;
+        for (;;) {
+            int best = INT_MAX, bi = -1;
+            for (int i = lane; i < m; i += 32)
+                if ((R.F[i] & (kBnd | kTried)) == kBnd && R.L[i] < best) { best = R.L[i]; bi = i; }
+            const int K = __reduce_min_sync(0xffffffffu, best);
+            if (K == INT_MAX) break;
+            const int ai = __shfl_sync(0xffffffffu, bi, __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1);
+            __syncwarp();
+            if (lane == 0) R.L[ai] = INT_MIN;
+            __syncwarp();
+            const int last = wr_flood<true, NN>(R, H, lane);
+            if (last == -3) { overflow = true; break; }
+            if (last == -2) break;
+            if (last == ai) { ok = true; break; }
+            if (lane == 0) { R.L[ai] = K; R.F[ai] |= kTried; }
+            __syncwarp();
+        }
+        if (ok) {
+            nfl = 1;
+            const int cap = 2 * R.r + 2;
+            for (;;) {
+                for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
+                __syncwarp();
+                if (!wr_has_extremum<true, NN>(R, lane)) break;
+                const int rmin = wr_flood<false, NN>(R, H, lane);
+                if (rmin == -3) { overflow = true; break; }
+                if (rmin < 0) { nfl = -1; break; }
+                ++nfl;
+                for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
+                __syncwarp();
+                if (!wr_has_extremum<false, NN>(R, lane)) break;
+                const int rmax = wr_flood<true, NN>(R, H, lane);
+                if (rmax == -3) { overflow = true; break; }
+                if (rmax < 0) { nfl = -1; break; }
+                ++nfl;
+                if (nfl > cap) { nfl = -1; break; }
+            }
+        }
+        __syncwarp();
+        if (overflow) {
+            // the frontier outgrew the heap: lane 0 redoes the region on the single-thread path
+            nfl = -1;
+            if (lane == 0) {
+                BigStore<NN> T{a.lo_v + off, a.lo_L + off, a.lo_L2 + off, a.lo_heap + off, a.lo_flag + off,
+                               g, a.owner, a.loc, -2 - rid, s, m};
+                for (int i = 0; i <= m; ++i) {
+                    T.F(i) &= kBnd;
+                    T.L(i) = i < m ? od<DIR>(__ldg(a.O + T.V(i)), g.n) : INT_MAX;
+                }
+                nfl = local_order_run<NN>(T, m);
+            }
+            nfl = __shfl_sync(0xffffffffu, nfl, 0);
+        }
+        if (nfl < 0) {
+            if (lane == 0) set_status(&a.ctr->status, LTS_ERR_INTERNAL);
+            continue;
+        }
+        for (int i = lane; i < m; i += 32) a.lhat[st0 + i] = R.L[i];
+        mx = max(mx, nfl);
+        tot += nfl;
+        __syncwarp();
     }
-    __syncwarp();
-    fs.flush(a.ctr);
+    if (lane != 0) { mx = 0; tot = 0; }
+    warp_atomic_max(&a.ctr->max_floods, mx);
+    warp_atomic_add64(&a.ctr->total_floods, tot);
 }
 
 template <int DIR, int NN>
@@ -603,14 +808,20 @@ void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t
     const int q = w.class_cap / 4;
     constexpr size_t small = 4 * dense_smem_per_warp<NN, 128>();
     constexpr size_t large = dense_smem_per_warp<NN, kMedR>();
+    constexpr size_t huge = dense_smem_per_warp<NN, kHugeR>();
+    static_assert(huge <= 227 * 1024, "shared memory of the 4096-vertex tier");
     cudaFuncSetAttribute(lo_dense_kernel<DIR, NN, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small);
     cudaFuncSetAttribute(lo_dense_kernel<DIR, NN, kMedR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)large);
+    cudaFuncSetAttribute(lo_dense_kernel<DIR, NN, kHugeR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)huge);
     const int* tl = w.tier_list + w.class_cap;
     lo_team_kernel<DIR, NN, 16><<<sms * 12, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t16);
     lo_team_kernel<DIR, NN, 32><<<sms * 12, 128, 0, s>>>(g, a, tl, &w.ctr->n_t32);
     lo_dense_kernel<DIR, NN, 128, 4><<<sms * 10, 128, small, s>>>(g, a, tl + q, &w.ctr->n_med);
     lo_dense_kernel<DIR, NN, kMedR, 1><<<sms * 5, 32, large, s>>>(g, a, tl + 2 * q, &w.ctr->n_large);
-    lo_big_kernel<DIR, NN><<<sms, 128, 0, s>>>(g, a, tl + 3 * q, &w.ctr->n_big);
+    lo_dense_kernel<DIR, NN, kHugeR, 1><<<sms, 32, huge, s>>>(g, a, tl + 3 * q, &w.ctr->n_huge);
+    constexpr size_t heap_bytes = kWarpHeapCap * sizeof(unsigned long long);
+    cudaFuncSetAttribute(lo_warp_kernel<DIR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heap_bytes);
+    lo_warp_kernel<DIR, NN><<<sms, 32, heap_bytes, s>>>(g, a, tl + 3 * q + q / 2, &w.ctr->n_big);
 }
 
 }  // namespace
@@ -621,7 +832,7 @@ cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStre
              w.lo_v, w.lo_L, w.lo_L2, w.lo_heap, w.lo_flag, w.tier_list, w.ctr};
     if (g.nn == 14) launch_tiers<DIR, 14>(w, g, a, sms, s);
     else launch_tiers<DIR, 6>(w, g, a, sms, s);
-    w.launches += 5;
+    w.launches += 6;
     return cudaGetLastError();
 }
 
@@ -630,5 +841,6 @@ template cudaError_t local_orders<-1>(Work&, const Geom&, const int*, int, cudaS
 
 int local_order_tiny_max() { return 16; }
 int local_order_med_max() { return kMedR; }
+int local_order_huge_max() { return kHugeR; }
 
 }  // namespace lts

@@ -98,6 +98,7 @@ struct DevCounters {
     int n_t32;             // regions for the 32-lane team tier of step 2
     int n_med;             // regions for the small dense warp tier of step 2
     int n_large;           // regions for the large dense warp tier of step 2
+    int n_huge;            // regions for the 4096-vertex dense warp tier of step 2
     int n_big;             // regions for the HBM tier of step 2
     int n_tasks;           // propagation tasks left after the first step
 };
@@ -190,6 +191,7 @@ cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms
 cudaError_t pass_reset(Work& w, cudaStream_t s);
 int local_order_tiny_max();
 int local_order_med_max();
+int local_order_huge_max();
 
 // warp-level reductions before one atomic (all 32 lanes must call)
 __device__ __forceinline__ void warp_atomic_max(int* dst, int v) {

@@ -110,7 +110,9 @@ __device__ __forceinline__ unsigned long long pack(int key, int v) {
     return ((unsigned long long)(unsigned)key << 32) | (unsigned)v;
 }
 
-// The overflow heap of a team (binary max-heap in HBM), used by lane 0 only.
+// The overflow heap of a team: a 32-ary max-heap in HBM (so a pop sifts down
+// one level per coalesced load of 32 children and a team reduction).  Lane 0
+// holds the state and pushes; pops are run by the whole team.
 struct Overflow {
     unsigned long long* h;
     int n, cap;
@@ -129,7 +131,7 @@ __device__ bool ov_push(Overflow& H, unsigned long long e, const PropArgs& a) {
     }
     int i = H.n++;
     while (i > 0) {
-        const int p = (i - 1) >> 1;
+        const int p = (i - 1) >> 5;
         const unsigned long long pe = H.h[p];
         if (pe >= e) break;
         H.h[i] = pe;
@@ -137,26 +139,6 @@ __device__ bool ov_push(Overflow& H, unsigned long long e, const PropArgs& a) {
     }
     H.h[i] = e;
     return true;
-}
-
-__device__ unsigned long long ov_pop(Overflow& H) {
-    const unsigned long long top = H.h[0];
-    const int n = --H.n;
-    if (n == 0) return top;
-    const unsigned long long last = H.h[n];
-    int i = 0;
-    for (;;) {
-        const int l = 2 * i + 1;
-        if (l >= n) break;
-        int c = l;
-        unsigned long long ce = H.h[l];
-        if (l + 1 < n && H.h[l + 1] > ce) { c = l + 1; ce = H.h[l + 1]; }
-        if (ce <= last) break;
-        H.h[i] = ce;
-        i = c;
-    }
-    H.h[i] = last;
-    return top;
 }
 
 template <int NN>
@@ -179,6 +161,40 @@ __device__ __forceinline__ void ov_sync(TeamState<NN>& T) {
     int top = n > 0 ? (int)(T.ov.h[0] >> 32) : -1;
     T.ovn = __shfl_sync(T.tmask, n, T.tb);
     T.ov_top = __shfl_sync(T.tmask, top, T.tb);
+}
+
+// Pops the top of the team's overflow heap (all team lanes call it).
+template <int NN>
+__device__ unsigned long long ov_pop_team(TeamState<NN>& T) {
+    __syncwarp(T.tmask);                       // the leader's pushes before the team's loads
+    unsigned long long* h = reinterpret_cast<unsigned long long*>(
+        __shfl_sync(T.tmask, reinterpret_cast<unsigned long long>(T.ov.h), T.tb));
+    const int n = __shfl_sync(T.tmask, T.ov.n, T.tb) - 1;
+    const bool leader = T.lane == T.tb;
+    const unsigned long long top = __ldcg(h);
+    if (n > 0) {
+        const unsigned long long last = __ldcg(h + n);
+        int i = 0;
+        for (;;) {
+            const int c0 = 32 * i + 1;
+            if (c0 >= n) break;
+            const int c = c0 + (T.lane - T.tb);
+            const bool in = c < n;
+            const unsigned long long ce = in ? __ldcg(h + c) : 0ull;
+            const unsigned hi = (unsigned)(ce >> 32), lo = (unsigned)ce;
+            const unsigned kh = __reduce_max_sync(T.tmask, hi);
+            const unsigned kl = __reduce_max_sync(T.tmask, hi == kh ? lo : 0u);
+            const int L = __ffs(__ballot_sync(T.tmask, in && hi == kh && lo == kl)) - 1;
+            const unsigned long long mv = ((unsigned long long)kh << 32) | kl;
+            if (mv <= last) break;
+            if (leader) __stcg(h + i, mv);
+            i = c0 + (L - T.tb);
+        }
+        if (leader) __stcg(h + i, last);
+    }
+    if (leader) T.ov.n = n;
+    __syncwarp(T.tmask);
+    return top;
 }
 
 // Adds one candidate per lane (has, key, vert) to the team frontier.
@@ -442,9 +458,7 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                 break;
             }
             if (T.ov_top > K) {
-                unsigned long long e = 0;
-                if (leader) e = ov_pop(T.ov);
-                e = __shfl_sync(T.tmask, e, T.tb);
+                const unsigned long long e = ov_pop_team(T);
                 ov_sync(T);
                 v = (int)(e & 0xffffffffu);
                 kv = (int)(e >> 32);

@@ -110,7 +110,7 @@ __global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int
 // last, and no vertex lacks an outside neighbour, so lhat(m) = 0 after one
 // propagation.
 __global__ void tiers_kernel(const int* __restrict__ reg_size, const int* __restrict__ reg_start, int* lhat,
-                             int* tier_list, int cap, int q, int med_max, DevCounters* ctr) {
+                             int* tier_list, int cap, int q, int med_max, int huge_max, DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
     int trivial = 0;
@@ -125,15 +125,18 @@ __global__ void tiers_kernel(const int* __restrict__ reg_size, const int* __rest
         const bool t32 = sz > 16 && sz <= 32;
         const bool med = sz > 32 && sz <= 128;
         const bool lrg = sz > 128 && sz <= med_max;
-        const bool big = sz > med_max;
+        const bool huge = sz > med_max && sz <= huge_max;
+        const bool big = sz > huge_max;
         const int p32 = warp_reserve(&ctr->n_t32, t32);
         const int pm = warp_reserve(&ctr->n_med, med);
         const int pl = warp_reserve(&ctr->n_large, lrg);
+        const int ph = warp_reserve(&ctr->n_huge, huge);
         const int pb = warp_reserve(&ctr->n_big, big);
         if (t32) rest[p32] = r;
         if (med) rest[q + pm] = r;
         if (lrg) rest[2 * q + pl] = r;
-        if (big) rest[3 * q + pb] = r;
+        if (huge) rest[3 * q + ph] = r;
+        if (big) rest[3 * q + q / 2 + pb] = r;
     }
     if (trivial) atomicMax(&ctr->max_floods, 1);
     warp_atomic_add64(&ctr->total_floods, trivial);
@@ -201,7 +204,7 @@ cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaS
     siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.sib_head, w.sib_next,
                                     w.class2reg, w.reg_place, w.reg_att, w.rblk, w.ctr);
     tiers_kernel<<<B, T, 0, s>>>(w.reg_size, w.reg_start, w.lhat, w.tier_list, w.class_cap, w.class_cap / 4,
-                                 local_order_med_max(), w.ctr);
+                                 local_order_med_max(), local_order_huge_max(), w.ctr);
     w.launches += 6;
     return cudaGetLastError();
 }
