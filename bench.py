@@ -43,6 +43,11 @@ FALLBACK_HBM_GBS = 6800.0
 #   classify:    read the order field once per pass (2 x 4)
 #   reorder:     read + write the order field per pass (2 x 8)
 BYTES_PER_VERTEX = {"order_field": 4 + 4 + 48 + 8, "classify": 8, "reorder": 16}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the six
+# order-field kernels per vertex, from an ncu capture of the 256^3 case of the
+# same recipe, scaled by the vertex count (the 512^3 call is too large to
+# capture with all metrics); only the order-field stage has a capture.
+TRAFFIC_PER_VERTEX = {"order_field": 67.4}
 PATH_BYTES_PER_VERTEX = 100   # sort + classify + flatten, both passes
 
 
@@ -425,8 +430,11 @@ def main():
                    "authorized": int(ids.size), "mode": "both", "l2": "inputs (512 MB) larger than L2",
                    "parallelism": f"replicas x{world}"},
         "parity_vs_oracle": bool(parity),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+        "roofline": {"bound": "hbm", "kernel": dom + (" (histogram/copy, 4 onesweep passes, inverse)"
+                                                      if dom == "order_field" else ""),
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": (int(TRAFFIC_PER_VERTEX[dom] * n) if dom in TRAFFIC_PER_VERTEX else None),
                      "peak_kind": kind, "bytes_per_vertex": BYTES_PER_VERTEX[dom]},
         "path_roofline": {"bytes_per_vertex": PATH_BYTES_PER_VERTEX, "achieved": round(path_achieved, 1),
                           "peak": peak, "unit": "GB/s", "frac": round(path_achieved / peak, 4)},
