@@ -220,6 +220,7 @@ struct LOArgs {
     const int* reg_size; const int* reg_saddle; int* lhat;
     int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
     const int* tier_list; DevCounters* ctr;
+    int* lo_adj; long long lo_adj_cap;
 };
 
 // ---- tiers 1-2: one region per team of TS lanes (r <= TS), registers ----
@@ -562,6 +563,7 @@ constexpr int kWarpHeapCap = 28672;
 struct WarpRegion {
     int* V; int* L; int* L2; unsigned char* F;
     Geom g; const int* owner; const int* loc; int tag; int s; int m; int r;
+    int* adj;          // local index of neighbour q of local vertex i at [i * NN + q], or null
 };
 
 __device__ __forceinline__ int wr_nbr(const WarpRegion& R, int vtx, int q) {
@@ -572,6 +574,12 @@ __device__ __forceinline__ int wr_nbr(const WarpRegion& R, int vtx, int q) {
     if (nb == R.s) return R.m;
     if (__ldg(R.owner + nb) != R.tag) return -1;
     return __ldg(R.loc + nb);
+}
+
+// neighbour q of local vertex i (local index, -1 outside R)
+template <int NN>
+__device__ __forceinline__ int wr_nbr_of(const WarpRegion& R, int i, int q) {
+    return R.adj ? R.adj[(long long)i * NN + q] : wr_nbr(R, R.V[i], q);
 }
 
 // biased key: unsigned order of the (max-first) or reversed (min-first) key
@@ -658,10 +666,9 @@ __device__ int wr_flood(const WarpRegion& R, unsigned long long* H, int lane) {
         if (lane == 0) R.L2[i] = MAXF ? R.r - 1 - cnt : cnt;
         ++cnt;
         last = i;
-        const int vtx = R.V[i];
         int j = -1, key = 0;
         if (lane < NN) {
-            j = wr_nbr(R, vtx, lane);
+            j = wr_nbr_of<NN>(R, i, lane);
             if (j >= 0 && !(R.F[j] & kVis)) {
                 R.F[j] |= kVis;
                 key = R.L[j];
@@ -691,10 +698,10 @@ __device__ bool wr_has_extremum(const WarpRegion& R, int lane) {
     const int lim = MINF ? R.r : R.m;
     for (int i = lane; i < lim && !found; i += 32) {
         if (MINF && (R.F[i] & kBnd)) continue;
-        const int li = R.L[i], vtx = R.V[i];
+        const int li = R.L[i];
         bool ext = true;
         for (int q = 0; q < NN && ext; ++q) {
-            const int j = wr_nbr(R, vtx, q);
+            const int j = wr_nbr_of<NN>(R, i, q);
             if (j >= 0 && (MINF ? R.L[j] < li : R.L[j] > li)) ext = false;
         }
         found = ext;
@@ -717,7 +724,13 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         const int st0 = a.reg_start[rid];
         const long long off = (long long)st0 + rid;
         WarpRegion R{a.lo_v + off, a.lo_L + off, a.lo_L2 + off, a.lo_flag + off, g, a.owner, a.loc, -2 - rid, s, m,
-                     m + 1};
+                     m + 1, nullptr};
+        // the local adjacency, from a bump pool (recomputed per pop when the pool is spent)
+        long long abase = 0;
+        if (lane == 0) abase = (long long)atomicAdd((unsigned long long*)&a.ctr->lo_adj_cursor,
+                                                    (unsigned long long)NN * (m + 1));
+        abase = __shfl_sync(0xffffffffu, abase, 0);
+        int* adj = abase + (long long)NN * (m + 1) <= a.lo_adj_cap ? a.lo_adj + abase : nullptr;
         for (int i = lane; i <= m; i += 32) {
             const int vtx = i < m ? a.members[st0 + i] : s;
             R.V[i] = vtx;
@@ -726,11 +739,18 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
             unsigned char fl = 0;
             for (int q = 0; q < NN; ++q) {
                 const int nb = nbr_of(g, x, y, z, q);
-                if (nb >= 0 && nb != s && __ldg(a.owner + nb) != R.tag) fl = kBnd;
+                int j = -1;
+                if (nb == s) j = m;
+                else if (nb >= 0) {
+                    if (__ldg(a.owner + nb) != R.tag) fl = kBnd;
+                    else j = __ldg(a.loc + nb);
+                }
+                if (adj) adj[(long long)i * NN + q] = j;
             }
             R.F[i] = fl;
             R.L[i] = i < m ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
         }
+        R.adj = adj;
         __syncwarp();
         int nfl = -1;
         bool overflow = false;
@@ -829,7 +849,7 @@ void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t
 template <int DIR>
 cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s) {
     LOArgs a{O, w.owner, w.loc, w.members, w.reg_start, w.reg_size, w.reg_saddle, w.lhat,
-             w.lo_v, w.lo_L, w.lo_L2, w.lo_heap, w.lo_flag, w.tier_list, w.ctr};
+             w.lo_v, w.lo_L, w.lo_L2, w.lo_heap, w.lo_flag, w.tier_list, w.ctr, w.lo_adj, w.lo_adj_cap};
     if (g.nn == 14) launch_tiers<DIR, 14>(w, g, a, sms, s);
     else launch_tiers<DIR, 6>(w, g, a, sms, s);
     w.launches += 6;

@@ -105,6 +105,7 @@ size_t bytes_for(const Sizes& z) {
     b += 11 * 4 * (size_t)z.half;                   // region records
     b += 3 * 4 * (size_t)z.n;                       // members, member regions, lhat
     b += 17 * (size_t)z.lo_cap;                     // local-order scratch
+    b += 16 * (size_t)z.n;                          // local adjacency of the largest regions
     b += sizeof(RankBlk) * (size_t)z.nblk + 2 * 4 * (size_t)z.half;
     b += 8 * (size_t)z.scan_tiles + sizeof(DevCounters) + 2 * sizeof(PassStats);
     return b;
@@ -170,7 +171,9 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     ok = ok && dev_alloc(L, &w.members, z.n) && dev_alloc(L, &w.lhat, z.n) && dev_alloc(L, &w.tier_list, 2 * z.half) &&
          dev_alloc(L, &w.member_reg, z.n);
     ok = ok && dev_alloc(L, &w.lo_v, z.lo_cap) && dev_alloc(L, &w.lo_L, z.lo_cap) && dev_alloc(L, &w.lo_L2, z.lo_cap) &&
-         dev_alloc(L, &w.lo_heap, z.lo_cap) && dev_alloc(L, &w.lo_flag, z.lo_cap);
+         dev_alloc(L, &w.lo_heap, z.lo_cap) && dev_alloc(L, &w.lo_flag, z.lo_cap) &&
+         dev_alloc(L, &w.lo_adj, 4 * z.n + 4096);
+    w.lo_adj_cap = 4 * z.n + 4096;
     ok = ok && dev_alloc(L, &w.rblk, z.nblk) && dev_alloc(L, &w.sad_att, z.half) && dev_alloc(L, &w.cumA, z.half + 1);
     ok = ok && dev_alloc(L, &w.scan_tmp, z.scan_tiles) && dev_alloc(L, &w.ctr, 1) && dev_alloc(L, &w.pstats, 2);
     if (ok && cudaMallocHost((void**)&w.h_ctr, sizeof(DevCounters) + 2 * sizeof(PassStats)) != cudaSuccess) ok = false;

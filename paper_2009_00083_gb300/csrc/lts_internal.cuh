@@ -101,6 +101,7 @@ struct DevCounters {
     int n_huge;            // regions for the 4096-vertex dense warp tier of step 2
     int n_big;             // regions for the HBM tier of step 2
     int n_tasks;           // propagation tasks left after the first step
+    long long lo_adj_cursor; // local adjacency pool of the largest local-order tier (ints)
 };
 
 __device__ __forceinline__ void set_oom(DevCounters* ctr, int pool) {
@@ -160,6 +161,7 @@ struct Work {
     int* tier_list;                      // [0,cap): 16-lane tier; then quarters of cap: 32-lane, dense <=128, dense <=1024, HBM
     // local-order scratch (slots: members + one saddle per region)
     int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
+    int* lo_adj; long long lo_adj_cap;   // local adjacency of the largest regions (bump pool)
     long long lo_cap;
     // reorder
     RankBlk* rblk; int nblk; int nblk_cur;

@@ -175,20 +175,28 @@ __device__ unsigned long long ov_pop_team(TeamState<NN>& T) {
     if (n > 0) {
         const unsigned long long last = __ldcg(h + n);
         int i = 0;
+        constexpr int TS = TeamState<NN>::TS, K = 32 / TS;   // children per lane
         for (;;) {
             const int c0 = 32 * i + 1;
             if (c0 >= n) break;
-            const int c = c0 + (T.lane - T.tb);
-            const bool in = c < n;
-            const unsigned long long ce = in ? __ldcg(h + c) : 0ull;
+            unsigned long long ce = 0ull;
+            int ci = -1;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int c = c0 + (T.lane - T.tb) + kk * TS;
+                if (c < n) {
+                    const unsigned long long e = __ldcg(h + c);
+                    if (ci < 0 || e > ce) { ce = e; ci = c; }
+                }
+            }
             const unsigned hi = (unsigned)(ce >> 32), lo = (unsigned)ce;
             const unsigned kh = __reduce_max_sync(T.tmask, hi);
             const unsigned kl = __reduce_max_sync(T.tmask, hi == kh ? lo : 0u);
-            const int L = __ffs(__ballot_sync(T.tmask, in && hi == kh && lo == kl)) - 1;
+            const int L = __ffs(__ballot_sync(T.tmask, ci >= 0 && hi == kh && lo == kl)) - 1;
             const unsigned long long mv = ((unsigned long long)kh << 32) | kl;
             if (mv <= last) break;
             if (leader) __stcg(h + i, mv);
-            i = c0 + (L - T.tb);
+            i = __shfl_sync(T.tmask, ci, L);
         }
         if (leader) __stcg(h + i, last);
     }
@@ -396,8 +404,8 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                 if (task_lo == task_hi) {
                     // guided batches: large while many tasks remain, single ones at the end
                     const int rem = nT - *(volatile int*)&ctr->seed_cursor;
-                    const int nwarps = gridDim.x * (blockDim.x / 32);
-                    const int bsz = max(1, min(kSeedBatch, rem / (4 * nwarps)));
+                    const int nteams = gridDim.x * (blockDim.x / TS);
+                    const int bsz = max(1, min(kSeedBatch, rem / (4 * nteams)));
                     const int b = atomicAdd(&ctr->seed_cursor, bsz);
                     task_lo = b;
                     task_hi = min(b + bsz, nT);
