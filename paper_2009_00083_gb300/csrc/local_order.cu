@@ -690,6 +690,108 @@ __device__ int wr_flood(const WarpRegion& R, unsigned long long* H, int lane) {
     return cnt == R.r ? last : -2;
 }
 
+// ---- floods in key space (after the first flood L is a permutation of 0..r-1) ----
+// NK[k * NN + q] holds the key of neighbour q of the vertex with key k (-1 if
+// none), so a step is one load; the frontier is a three-level bitmap over the
+// keys in shared memory (pops find the highest or lowest set bit, pushes are
+// lane-parallel atomicOr, no capacity limit) and the visited set a bitmap.
+struct KeyQueue {
+    unsigned* q1; unsigned* q2; unsigned* q3; unsigned* vis;
+    int n1, n2, n3;                        // words per level (n3 <= 32)
+};
+
+__device__ __forceinline__ void kq_push(const KeyQueue& Q, int k) {
+    atomicOr(Q.q1 + (k >> 5), 1u << (k & 31));
+    atomicOr(Q.q2 + (k >> 10), 1u << ((k >> 5) & 31));
+    atomicOr(Q.q3 + (k >> 15), 1u << ((k >> 10) & 31));
+}
+
+template <bool MAXF>
+__device__ __forceinline__ int kq_pop(const KeyQueue& Q, int lane) {
+    const unsigned w3l = lane < Q.n3 ? Q.q3[lane] : 0u;
+    const unsigned m3 = __ballot_sync(0xffffffffu, w3l != 0u);
+    if (!m3) return -1;
+    const int l3 = MAXF ? 31 - __clz(m3) : __ffs(m3) - 1;
+    const unsigned w3 = __shfl_sync(0xffffffffu, w3l, l3);
+    const int b3 = MAXF ? 31 - __clz(w3) : __ffs(w3) - 1;
+    const int i2 = l3 * 32 + b3;
+    if (i2 >= Q.n2) return -1;                 // inconsistent levels: reported as empty (an error)
+    const unsigned w2 = Q.q2[i2];
+    if (w2 == 0u) return -1;
+    const int b2 = MAXF ? 31 - __clz(w2) : __ffs(w2) - 1;
+    const int i1 = i2 * 32 + b2;
+    if (i1 >= Q.n1) return -1;
+    const unsigned w1 = Q.q1[i1];
+    if (w1 == 0u) return -1;
+    const int b1 = MAXF ? 31 - __clz(w1) : __ffs(w1) - 1;
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned n1 = w1 & ~(1u << b1);
+        Q.q1[i1] = n1;
+        if (!n1) {
+            const unsigned n2 = w2 & ~(1u << b2);
+            Q.q2[i2] = n2;
+            if (!n2) Q.q3[l3] = w3 & ~(1u << b3);
+        }
+    }
+    __syncwarp();
+    return i1 * 32 + b1;
+}
+
+// One propagation in key space over the keys Lk (a permutation of 0..r-1; Lk
+// may be L2 itself); L2 gets the visiting order.  Returns the last key popped (the maxima flood) or
+// 0, or -2 if R was not covered.
+template <bool MAXF, int NN>
+__device__ int wr_flood_keys(const WarpRegion& R, const int* Lk, int* NK, int* ordk, const KeyQueue& Q, int lane) {
+    const int r = R.r;
+    for (int i = lane; i < r; i += 32) {
+        const int k = Lk[i];
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const int j = R.adj[(long long)i * NN + q];
+            NK[(long long)k * NN + q] = j >= 0 ? Lk[j] : -1;
+        }
+    }
+    for (int w = lane; w < Q.n1; w += 32) { Q.q1[w] = 0u; Q.vis[w] = 0u; }
+    for (int w = lane; w < Q.n2; w += 32) Q.q2[w] = 0u;
+    if (lane < Q.n3) Q.q3[lane] = 0u;
+    __syncwarp();
+    if (MAXF) {
+        if (lane == 0) {
+            const int k = Lk[R.m];
+            atomicOr(Q.vis + (k >> 5), 1u << (k & 31));
+            kq_push(Q, k);
+        }
+    } else {
+        for (int i = lane; i < R.m; i += 32)
+            if (R.F[i] & kBnd) {
+                const int k = Lk[i];
+                atomicOr(Q.vis + (k >> 5), 1u << (k & 31));
+                kq_push(Q, k);
+            }
+    }
+    __syncwarp();
+    int cnt = 0, last = -1;
+    for (;;) {
+        const int k = kq_pop<MAXF>(Q, lane);
+        if (k < 0 || cnt == r) break;               // at most r pops: every key is pushed once
+        if (lane == 0) ordk[k] = MAXF ? r - 1 - cnt : cnt;
+        ++cnt;
+        last = k;
+        if (lane < NN) {
+            const int kk = NK[(long long)k * NN + lane];
+            if (kk >= 0) {
+                const unsigned bit = 1u << (kk & 31);
+                if (!(atomicOr(Q.vis + (kk >> 5), bit) & bit)) kq_push(Q, kk);
+            }
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < r; i += 32) R.L2[i] = ordk[Lk[i]];
+    __syncwarp();
+    return cnt == r ? (MAXF ? last : 0) : -2;
+}
+
 // some vertex (not s, for minima: without an outside neighbour) is a strict
 // local minimum (MINF) or maximum of L
 template <bool MINF, int NN>
@@ -731,6 +833,21 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
                                                     (unsigned long long)NN * (m + 1));
         abase = __shfl_sync(0xffffffffu, abase, 0);
         int* adj = abase + (long long)NN * (m + 1) <= a.lo_adj_cap ? a.lo_adj + abase : nullptr;
+        // the key-space table of the later floods, from the same pool, and the bitmaps in shared memory
+        long long nbase = 0;
+        if (lane == 0 && adj) nbase = (long long)atomicAdd((unsigned long long*)&a.ctr->lo_adj_cursor,
+                                                           (unsigned long long)NN * (m + 1));
+        nbase = __shfl_sync(0xffffffffu, nbase, 0);
+        KeyQueue Q;
+        Q.n1 = (m + 1 + 31) >> 5;                   // keys 0..m
+        Q.n2 = (Q.n1 + 31) >> 5;
+        Q.n3 = (Q.n2 + 31) >> 5;
+        unsigned* sm = reinterpret_cast<unsigned*>(H);
+        Q.q1 = sm; Q.vis = sm + Q.n1; Q.q2 = sm + 2 * Q.n1; Q.q3 = sm + 2 * Q.n1 + Q.n2;
+        const bool keyspace = adj && nbase + (long long)NN * (m + 1) <= a.lo_adj_cap && Q.n3 <= 32 &&
+                              2LL * Q.n1 + Q.n2 + 32 <= 2LL * kWarpHeapCap;
+        int* NK = keyspace ? a.lo_adj + nbase : nullptr;
+        int* ordk = a.lo_heap + off;
         for (int i = lane; i <= m; i += 32) {
             const int vtx = i < m ? a.members[st0 + i] : s;
             R.V[i] = vtx;
@@ -754,6 +871,54 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         __syncwarp();
         int nfl = -1;
         bool overflow = false;
+        // Dense ranks of Od for the candidate tries in key space: a bitmap over
+        // the members' Od range and its prefix popcounts.  V then holds the
+        // ranks 0..m-1 of the members (nothing reads the vertex ids again); a
+        // try with candidate a uses the keys a: 0, members below a: rank + 1,
+        // members above a: rank, s: m, a permutation of 0..m.
+        bool dense = false;
+        if (keyspace) {
+            int mn = INT_MAX, mx = INT_MIN;
+            for (int i = lane; i < m; i += 32) { mn = min(mn, R.L[i]); mx = max(mx, R.L[i]); }
+            mn = __reduce_min_sync(0xffffffffu, mn);
+            mx = __reduce_max_sync(0xffffffffu, mx);
+            const long long words = ((long long)mx - mn + 1 + 31) >> 5;
+            long long bbase = 0;
+            if (lane == 0) bbase = (long long)atomicAdd((unsigned long long*)&a.ctr->lo_adj_cursor,
+                                                        (unsigned long long)(2 * words));
+            bbase = __shfl_sync(0xffffffffu, bbase, 0);
+            if (bbase + 2 * words <= a.lo_adj_cap) {
+                unsigned* bm = reinterpret_cast<unsigned*>(a.lo_adj + bbase);
+                int* pre = a.lo_adj + bbase + words;
+                for (long long w = lane; w < words; w += 32) bm[w] = 0u;
+                __syncwarp();
+                for (int i = lane; i < m; i += 32) {
+                    const int o = R.L[i] - mn;
+                    atomicOr(bm + (o >> 5), 1u << (o & 31));
+                }
+                __syncwarp();
+                int run = 0;
+                for (long long b = 0; b < words; b += 32) {
+                    const long long w = b + lane;
+                    const int c = w < words ? __popc(bm[w]) : 0;
+                    int x = c;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, d);
+                        if (lane >= d) x += y;
+                    }
+                    if (w < words) pre[w] = run + x - c;
+                    run += __shfl_sync(0xffffffffu, x, 31);
+                }
+                __syncwarp();
+                for (int i = lane; i < m; i += 32) {
+                    const int o = R.L[i] - mn;
+                    R.V[i] = pre[o >> 5] + __popc(bm[o >> 5] & ((1u << (o & 31)) - 1u));
+                }
+                __syncwarp();
+                dense = true;
+            }
+        }
         // the minus-infinity vertex: lowest boundary-adjacent member whose removal keeps R connected
         bool ok = false;
         for (;;) {
@@ -764,6 +929,21 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
             if (K == INT_MAX) break;
             const int ai = __shfl_sync(0xffffffffu, bi, __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1);
             __syncwarp();
+            if (dense) {
+                // key space: the candidate takes key 0, below every other
+                const int ra = R.V[ai];
+                for (int i = lane; i <= m; i += 32) {
+                    const int ri = i < m ? R.V[i] : m;
+                    R.L2[i] = i == ai ? 0 : (i < m && ri < ra ? ri + 1 : ri);
+                }
+                __syncwarp();
+                const int lk = wr_flood_keys<true, NN>(R, R.L2, NK, ordk, Q, lane);
+                if (lk == -2) break;
+                if (lk == 0) { ok = true; break; }
+                if (lane == 0) R.F[ai] |= kTried;
+                __syncwarp();
+                continue;
+            }
             if (lane == 0) R.L[ai] = INT_MIN;
             __syncwarp();
             const int last = wr_flood<true, NN>(R, H, lane);
@@ -780,14 +960,16 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
                 for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
                 __syncwarp();
                 if (!wr_has_extremum<true, NN>(R, lane)) break;
-                const int rmin = wr_flood<false, NN>(R, H, lane);
+                const int rmin = keyspace ? wr_flood_keys<false, NN>(R, R.L, NK, ordk, Q, lane)
+                                          : wr_flood<false, NN>(R, H, lane);
                 if (rmin == -3) { overflow = true; break; }
                 if (rmin < 0) { nfl = -1; break; }
                 ++nfl;
                 for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
                 __syncwarp();
                 if (!wr_has_extremum<false, NN>(R, lane)) break;
-                const int rmax = wr_flood<true, NN>(R, H, lane);
+                const int rmax = keyspace ? wr_flood_keys<true, NN>(R, R.L, NK, ordk, Q, lane)
+                                          : wr_flood<true, NN>(R, H, lane);
                 if (rmax == -3) { overflow = true; break; }
                 if (rmax < 0) { nfl = -1; break; }
                 ++nfl;
