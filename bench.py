@@ -189,6 +189,23 @@ def run_reference(args):
     }))
 
 
+def slowest_rank_ms(ms, dist, device):
+    """The largest per-step time over the ranks (the job is as fast as its
+    slowest replica); the local time when there is one rank."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mvps(n, world, ms):
+    """Vertices of all ranks' replicas over the slowest rank's time."""
+    return world * n / (ms / 1e3) / 1e6
+
+
 def _load_set(name, make_field, specs):
     """Fields of a stored multi-field workload (hash-checked) and their authorized lists."""
     from tests.golden import store as mg
@@ -372,13 +389,9 @@ def main():
                 stage_us[k] += v
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, dist, dev)
     stage_us = {k: v / args.steps for k, v in stage_us.items()}
-    value = world * n / (ms / 1e3) / 1e6
+    value = whole_job_mvps(n, world, ms)
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -400,12 +413,8 @@ def main():
             oh.copy_(o, non_blocking=True)
         e1.record(stream)
         barrier()
-        ms_e2e = e0.elapsed_time(e1) / args.steps
-        if dist is not None:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": round(world * n / (ms_e2e / 1e3) / 1e6, 3), "unit": "Mvertices/s",
+        ms_e2e = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, dist, dev)
+        e2e = {"value": round(whole_job_mvps(n, world, ms_e2e), 3), "unit": "Mvertices/s",
                "h2d_bytes_per_step": int(f.nbytes + ids.nbytes), "d2h_bytes_per_step": int(2 * f.nbytes),
                "ms_per_step": round(ms_e2e, 3)}
 
