@@ -16,6 +16,8 @@ Public functions (numpy in, numpy out):
     local_orders(...)                 Sec. 4.2 step 2 (Eq. 3-5)
     apply(...)                        Sec. 4.2 steps 3-4 (Eq. 6)
     lts(f, auth_ids, mode)            the whole method
+    pers_select(f, O, dir, eps)       Sec. 4.5 (propagations from every extremum, stopped at eps)
+    pers_lts(f, eps, mode)            Sec. 4.5 (Elder-rule selection per pass, then the pass)
 """
 from __future__ import annotations
 
@@ -94,6 +96,7 @@ def _get():
         lib.orc_apply.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P]
         lib.orc_lts.argtypes = [ctypes.c_int, P, P, P, i64, ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_uint64]
         lib.orc_pass.argtypes = [ctypes.c_int, P, ctypes.c_int, P, i64, P, P, P, ctypes.c_int, ctypes.c_uint64]
+        lib.orc_pers_select.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, P]
         lib.orc_link_edges.argtypes = [ctypes.c_int, P]
         lib.orc_link_triangles.argtypes = [ctypes.c_int, P]
         lib.orc_neighbour_offsets.argtypes = [ctypes.c_int, P]
@@ -259,3 +262,42 @@ def one_pass(g, O, auth_ids, direction, method=0, seed=0):
                            ctypes.byref(st), method, seed)
     _check(code, "pass")
     return g, O, st.as_dict()
+
+
+def persistent_by_elder(g, O, direction, eps):
+    """Sec. 3.3 applied as Sec. 4.5 selects: the maxima (direction +1) or
+    minima (-1) of (g, O) whose Elder-rule persistence exceeds eps, plus the
+    global one of that kind."""
+    pmin, pmax = persistence(g, O)
+    p = (pmax if direction > 0 else pmin).reshape(-1)
+    keep = np.nan_to_num(p, nan=-1.0) > eps
+    flat = np.asarray(O).reshape(-1)
+    keep[int(np.argmax(flat) if direction > 0 else np.argmin(flat))] = True
+    return np.nonzero(keep)[0].astype(np.int32)
+
+
+def pers_select(f, O, direction, eps, seed=0):
+    """Sec. 4.5 as the paper runs it: a propagation from every maximum
+    (direction +1) or minimum (-1), each ended once its scalar difference to
+    the class's highest extremum exceeds eps.  Returns the ids it keeps."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    nd, dims = _dims(f.shape)
+    mask = np.empty(f.shape, dtype=np.uint8)
+    _check(_get().orc_pers_select(nd, _p(dims), _p(f), _p(np.ascontiguousarray(O, dtype=np.int32)), direction,
+                                  float(eps), seed, _p(mask)), "pers_select")
+    return np.nonzero(mask.reshape(-1))[0].astype(np.int32)
+
+
+def pers_lts(f, eps, mode="both"):
+    """Persistence-driven LTS (Sec. 4.5): each pass (minima, then maxima)
+    keeps the extrema of its kind that are more persistent than eps on the
+    field it receives, and simplifies the others."""
+    if not (eps >= 0.0):
+        raise ValueError("eps must be a non-negative number")
+    g = np.array(f, dtype=np.float32, copy=True)
+    O = order_field(g)
+    if _MODES[mode] & MODE_MIN:
+        g, O, _ = one_pass(g, O, persistent_by_elder(g, O, -1, eps), -1)
+    if _MODES[mode] & MODE_MAX:
+        g, O, _ = one_pass(g, O, persistent_by_elder(g, O, +1, eps), +1)
+    return g, O

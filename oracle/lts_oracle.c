@@ -18,6 +18,7 @@
  *   - local to global order (step 3), pair order ...................... Sec. 4.2, Eq. 6
  *   - symbolic to numerical perturbation (step 4) ..................... Sec. 4.2
  *   - minima processed symmetrically to maxima ........................ Sec. 4
+ *   - persistence-driven selection by eps-bounded propagations ........ Sec. 4.5
  *
  * Readings taken where the paper is silent (each is listed in the design
  * notes of the repository):
@@ -669,6 +670,137 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Persistence-driven selection by propagations (Sec. 4.5): step 1 started  */
+/* from every maximum of Od.  Each class keeps its highest maximum m (the    */
+/* oldest of the classes it absorbed) and, at every pop of a vertex v, the   */
+/* scalar difference between m and v: f(m) - f(v) in the maxima pass,       */
+/* f(v) - f(m) in the minima pass, in double precision.  Once it exceeds     */
+/* eps the propagation ends and m is persistent.  A class whose queue runs   */
+/* dry has covered the whole grid: its maximum is the global one, which is   */
+/* kept as well.  Every other maximum ends inside a class that merged into   */
+/* an older one, or that waits for ever at a saddle: it is not persistent.   */
+/* ------------------------------------------------------------------------ */
+
+static int pers_flood_run(flood_t* F, const float* f, int dir, double eps, int32_t* top,
+                          uint8_t* persistent, int32_t* pc, int64_t budget) {
+    int32_t c = *pc;
+    for (;;) {
+        if (budget == 0) { *pc = c; return 1; }
+        if (budget > 0) --budget;
+        if (F->heap[c].n == 0) { persistent[top[c]] = 1; return 0; }
+        hitem it = heap_pop(&F->heap[c]);
+        int32_t v = it.v;
+        if (F->owner[v] >= 0 && cls_find(F->parent, F->owner[v]) == c) continue;
+        double d = dir > 0 ? (double)f[top[c]] - (double)f[v] : (double)f[v] - (double)f[top[c]];
+        if (d > eps) { persistent[top[c]] = 1; return 0; }
+        if (F->owner[v] < 0) F->owner[v] = c;
+        int32_t nb[14];
+        int kn = nbrs(F->G, v, nb);
+        int h = 0, k = 0;
+        for (int j = 0; j < kn; ++j) {
+            int32_t u = nb[j];
+            if (F->Od[u] <= F->Od[v]) continue;
+            ++h;
+            if (F->owner[u] >= 0 && cls_find(F->parent, F->owner[u]) == c) ++k;
+        }
+        if (k == h) {
+            int st = push_lower_not_in(F, v, c);
+            if (st) return -st;
+            continue;
+        }
+        if (F->cnt[v] < 0) F->cnt[v] = h;
+        F->cnt[v] -= k;
+        F->wait_next[c] = F->wait_head[v];
+        F->wait_head[v] = c;
+        if (F->cnt[v] > 0) { *pc = c; return 0; }
+        int32_t root = c;
+        for (int32_t w = F->wait_head[v]; w >= 0; w = F->wait_next[w]) {
+            if (w == root) continue;
+            int32_t a = cls_find(F->parent, w), b = cls_find(F->parent, root);
+            if (a == b) continue;
+            if (F->heap[a].n > F->heap[b].n) { int32_t t = a; a = b; b = t; }
+            int st = heap_meld(&F->heap[b], &F->heap[a]);
+            if (st) return -st;
+            F->parent[a] = b;
+            if (F->Od[top[a]] > F->Od[top[b]]) top[b] = top[a];   /* the elder survives */
+            root = b;
+        }
+        F->wait_head[v] = -1;
+        c = cls_find(F->parent, root);
+        int st = push_lower_not_in(F, v, c);
+        if (st) return -st;
+    }
+}
+
+static int pers_select(const grid_t* G, const float* f, const int32_t* O, int dir, double eps, uint64_t seed,
+                       uint8_t* persistent) {
+    int64_t n = G->n;
+    int st = ORC_OK;
+    int64_t nu = 0;
+    int32_t* Od = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* U = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * n);
+    flood_t F;
+    memset(&F, 0, sizeof F);
+    int32_t* top = NULL;
+    int32_t* q2 = NULL;
+    if (!Od || !U || !perm) { st = ORC_ERR_OOM; goto done; }
+    for (int64_t v = 0; v < n; ++v) {
+        Od[v] = dir > 0 ? O[v] : (int32_t)(n - 1 - O[v]);
+        persistent[v] = 0;
+    }
+    for (int64_t v = 0; v < n; ++v) perm[Od[v]] = (int32_t)v;
+    for (int64_t i = n - 1; i >= 0; --i) {             /* every maximum of Od, highest first */
+        int32_t v = perm[i];
+        int32_t nb[14];
+        int k = nbrs(G, v, nb), ismax = 1;
+        for (int j = 0; j < k; ++j) if (Od[nb[j]] > Od[v]) { ismax = 0; break; }
+        if (ismax) U[nu++] = v;
+    }
+    F.G = G; F.Od = Od;
+    F.owner = (int32_t*)malloc(sizeof(int32_t) * n);
+    F.cnt = (int32_t*)malloc(sizeof(int32_t) * n);
+    F.wait_head = (int32_t*)malloc(sizeof(int32_t) * n);
+    F.wait_next = (int32_t*)malloc(sizeof(int32_t) * nu);
+    F.parent = (int32_t*)malloc(sizeof(int32_t) * nu);
+    F.heap = (heap_t*)calloc((size_t)nu, sizeof(heap_t));
+    top = (int32_t*)malloc(sizeof(int32_t) * nu);
+    q2 = (int32_t*)malloc(sizeof(int32_t) * (nu + 1));
+    if (!F.owner || !F.cnt || !F.wait_head || !F.wait_next || !F.parent || !F.heap || !top || !q2) {
+        st = ORC_ERR_OOM; goto done;
+    }
+    for (int64_t v = 0; v < n; ++v) { F.owner[v] = -1; F.cnt[v] = -1; F.wait_head[v] = -1; }
+    for (int64_t c = 0; c < nu; ++c) {
+        F.parent[c] = (int32_t)c; F.wait_next[c] = -1; top[c] = U[c];
+        st = heap_push(&F.heap[c], Od[U[c]], U[c]);
+        if (st) goto done;
+        q2[c] = (int32_t)c;
+    }
+    uint64_t rs = seed;
+    if (seed) {
+        for (int64_t i = nu - 1; i > 0; --i) {
+            int64_t j = (int64_t)(sm64(&rs) % (uint64_t)(i + 1));
+            int32_t t = q2[i]; q2[i] = q2[j]; q2[j] = t;
+        }
+    }
+    {
+        int64_t qh = 0, qn = nu, qcap = nu + 1;
+        while (qn > 0) {
+            int32_t c = q2[qh]; qh = (qh + 1) % qcap; --qn;
+            int64_t budget = seed ? (int64_t)(1 + sm64(&rs) % 7) : -1;
+            int r = pers_flood_run(&F, f, dir, eps, top, persistent, &c, budget);
+            if (r < 0) { st = -r; goto done; }
+            if (r == 1) { q2[(qh + qn) % qcap] = c; ++qn; }
+        }
+    }
+done:
+    if (F.heap) for (int64_t c = 0; c < nu; ++c) heap_free(&F.heap[c]);
+    free(F.owner); free(F.cnt); free(F.wait_head); free(F.wait_next); free(F.parent); free(F.heap);
+    free(top); free(q2); free(Od); free(U); free(perm);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Step 1, method B: a global join-tree sweep (superlevel set components by  */
 /* decreasing order, union-find over vertices).  A component is protected    */
 /* when it holds an authorized maximum.  At a vertex whose higher neighbours */
@@ -1146,4 +1278,18 @@ int orc_pass(int ndim, const int64_t* dims, int dir, const int32_t* auth_ids, in
     st = one_pass(&G, dir, auth, method, seed, g, O, S);
     free(auth);
     return st;
+}
+
+/* Persistence-driven selection (Sec. 4.5) on (f, O): persistent[v] = 1 for the
+ * maxima (dir = +1) or minima (dir = -1) that the eps-bounded propagations
+ * keep.  seed != 0 runs the propagations in a shuffled, sliced schedule. */
+int orc_pers_select(int ndim, const int64_t* dims, const float* f, const int32_t* O, int dir, double eps,
+                    uint64_t seed, uint8_t* persistent) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    if (dir != 1 && dir != -1) return ORC_ERR_ARG;
+    for (int64_t v = 0; v < G.n; ++v)
+        if (isnan(f[v])) return ORC_ERR_NAN;
+    return pers_select(&G, f, O, dir, eps, seed, persistent);
 }
