@@ -113,6 +113,29 @@ lts_status lts_simplify(lts_ctx* ctx, const lts_grid* g, const float* d_field,
                         const int32_t* d_authorized, int64_t n_authorized, lts_mode mode,
                         float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats);
 
+/* Persistence-driven simplification (Sec. 4.5): removes every extremum whose
+ * persistence is at most epsilon, with no list of authorized extrema.
+ * Each pass (minima, then maxima, as `mode` says) first starts a propagation
+ * from every extremum of its kind on the field it receives (f for the
+ * minima pass; for the maxima pass of LTS_MODE_BOTH, the output of the
+ * minima pass).  A propagation tracks the scalar difference between the
+ * highest extremum of its class and the vertex it takes next, |f(m) - f(v)|
+ * computed in double precision from the float32 values, and ends once that
+ * difference exceeds epsilon: its extremum is persistent.  The propagation
+ * that covers the whole grid (the global extremum's) is persistent as well.
+ * The kept extrema are thus those whose Elder-rule persistence (Sec. 3.3)
+ * exceeds epsilon, plus the global one of each kind; the pass then runs as
+ * in lts_simplify with them authorized.  The result satisfies
+ * |d_out_field - d_field| <= epsilon everywhere.
+ *   epsilon   absolute threshold in the units of f, >= 0 (else LTS_ERR_ARG)
+ * Other arguments, outputs, waiting and errors as in lts_simplify (there is
+ * no LTS_ERR_NO_AUTHORIZED: the global extremum is always kept).  In
+ * opt_stats, stage_us[1] (classification) includes the selection's
+ * propagations, and removed[] counts the extrema found not persistent. */
+lts_status lts_simplify_persistence(lts_ctx* ctx, const lts_grid* g, const float* d_field, double epsilon,
+                                    lts_mode mode, float* d_out_field, int32_t* d_out_order,
+                                    lts_stats* opt_stats);
+
 /* Simplifies nf independent fields (Sec. 4 on each; the paper runs one field
  * at a time, and batching is this library's addition).  Array arguments
  * hold one entry per field, with the meaning they have in lts_simplify;

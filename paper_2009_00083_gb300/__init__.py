@@ -15,7 +15,7 @@ import os
 __all__ = [
     "LtsGrid", "LtsStats", "LtsError", "Context", "lts_create", "lts_simplify", "lts_destroy",
     "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "lts_simplify_batch", "lts_submit",
-    "lts_poll", "library_path", "load", "simplify",
+    "lts_poll", "lts_simplify_persistence", "library_path", "load", "simplify", "simplify_persistence",
     "MODE_MIN", "MODE_MAX", "MODE_BOTH", "ORDER_STATIC_MAX_VERTICES",
 ]
 
@@ -87,6 +87,9 @@ def load():
         lib.lts_simplify.argtypes = [P, ctypes.POINTER(LtsGrid), P, P, ctypes.c_int64, ctypes.c_int, P, P,
                                      ctypes.POINTER(LtsStats)]
         lib.lts_simplify.restype = ctypes.c_int
+        lib.lts_simplify_persistence.argtypes = [P, ctypes.POINTER(LtsGrid), P, ctypes.c_double, ctypes.c_int, P, P,
+                                                 ctypes.POINTER(LtsStats)]
+        lib.lts_simplify_persistence.restype = ctypes.c_int
         lib.lts_last_error.argtypes = [P]
         lib.lts_last_error.restype = ctypes.c_char_p
         lib.lts_destroy.argtypes = [P]
@@ -141,6 +144,13 @@ def lts_simplify(ctx, grid: LtsGrid, d_field: int, d_authorized: int, n_authoriz
     return load().lts_simplify(ctx, ctypes.byref(grid), ctypes.c_void_p(d_field), ctypes.c_void_p(d_authorized),
                                int(n_authorized), _MODES[mode], ctypes.c_void_p(d_out_field),
                                ctypes.c_void_p(d_out_order), ctypes.byref(stats) if stats is not None else None)
+
+
+def lts_simplify_persistence(ctx, grid: LtsGrid, d_field: int, epsilon: float, mode, d_out_field: int,
+                             d_out_order: int, stats: LtsStats | None = None) -> int:
+    return load().lts_simplify_persistence(ctx, ctypes.byref(grid), ctypes.c_void_p(d_field), float(epsilon),
+                                           _MODES[mode], ctypes.c_void_p(d_out_field), ctypes.c_void_p(d_out_order),
+                                           ctypes.byref(stats) if stats is not None else None)
 
 
 def lts_last_error(ctx) -> str:
@@ -233,6 +243,22 @@ class Context:
             raise LtsError(code, lts_last_error(self._ctx))
         return g, o, (st.as_dict() if st is not None else None)
 
+    def simplify_persistence(self, field, epsilon, mode="both", out_field=None, out_order=None, with_stats=True):
+        """Persistence-driven simplification (Sec. 4.5): removes the extrema
+        whose persistence is at most epsilon.  Returns (g, order, stats or None)."""
+        import torch
+
+        if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
+            raise ValueError("field must be a contiguous CUDA float32 tensor")
+        grid = grid_of_shape(tuple(field.shape))
+        g = out_field if out_field is not None else torch.empty_like(field)
+        o = out_order if out_order is not None else torch.empty(field.shape, dtype=torch.int32, device=field.device)
+        st = LtsStats() if with_stats else None
+        code = lts_simplify_persistence(self._ctx, grid, field.data_ptr(), epsilon, mode, g.data_ptr(), o.data_ptr(),
+                                        st)
+        if code != 0:
+            raise LtsError(code, lts_last_error(self._ctx))
+        return g, o, (st.as_dict() if st is not None else None)
 
     def simplify_batch(self, fields, authorized, mode="both", with_stats=True):
         """fields: list of CUDA float32 tensors; authorized: list of CUDA int32
@@ -295,5 +321,14 @@ def simplify(field, authorized, mode="both"):
     ctx = Context(field.numel(), device=field.device.index)
     try:
         return ctx.simplify(field, authorized, mode)
+    finally:
+        ctx.close()
+
+
+def simplify_persistence(field, epsilon, mode="both"):
+    """One-shot persistence-driven simplification (Sec. 4.5)."""
+    ctx = Context(field.numel(), device=field.device.index)
+    try:
+        return ctx.simplify_persistence(field, epsilon, mode)
     finally:
         ctx.close()

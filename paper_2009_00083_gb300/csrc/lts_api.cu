@@ -98,7 +98,7 @@ size_t bytes_for(const Sizes& z) {
     b += (size_t)z.tiles * 256 * 8 + 4096 * 3;      // look-back words, histograms
     b += ((size_t)z.n + 31) / 32 * 4;               // authorized bitmap
     b += 2 * 4 * (size_t)z.n + 8 * (size_t)z.n;     // owner, loc, qmark
-    b += 8 * 4 * (size_t)z.half;                    // U and class records
+    b += 10 * 4 * (size_t)z.half;                   // U and class records
     b += 32 * (size_t)z.half;                       // task records, heap records
     b += 4 * (size_t)z.n;                           // saddle arrival counters
     b += 4 * (size_t)z.spill_cap + 8 * (size_t)z.heap_cap + 4 * (size_t)z.log_cap;
@@ -158,6 +158,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     ok = ok && dev_alloc(L, &w.authbits, (z.n + 31) / 32);
     ok = ok && dev_alloc(L, &w.owner, z.n) && dev_alloc(L, &w.loc, z.n) && dev_alloc(L, &w.qmark, z.n);
     ok = ok && dev_alloc(L, &w.U, z.half) && dev_alloc(L, &w.parent, z.half) && dev_alloc(L, &w.wait_v, z.half) &&
+         dev_alloc(L, &w.ctop, z.half) &&
          dev_alloc(L, &w.cnt, z.n) && dev_alloc(L, &w.tasks, z.half) &&
          dev_alloc(L, &w.sib_head, z.half) && dev_alloc(L, &w.sib_next, z.half) &&
          dev_alloc(L, &w.spill_base, z.half) && dev_alloc(L, &w.spill_n, z.half) && dev_alloc(L, &w.heaprec, z.half);
@@ -326,11 +327,22 @@ __global__ void fail_clean_kernel(const DevCounters* ctr, int* owner, int* cnt, 
 
 namespace {
 
+// How a pass selects the extrema it keeps: the caller's list, or
+// persistence above eps measured by the pass itself (Sec. 4.5).
+struct Selection {
+    const int32_t* ids;
+    int64_t n_ids;
+    bool by_persistence;
+    double eps;
+};
+
 // Enqueues one simplification on the lane's stream: stage events ev[0..11],
 // the result capture (when res is set) and the clean-up after a failure.
-cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const int32_t* d_authorized,
-                             int64_t n_authorized, lts_mode mode, float* gout, int* O, int sms, ReqResult* res,
-                             unsigned long long ticket) {
+// With a persistence selection each pass first runs the propagations from
+// every extremum of its kind (counted in the classification stage), which
+// set the authorized bitmap, and then the pass proper.
+cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const Selection& sel, lts_mode mode,
+                             float* gout, int* O, int sms, ReqResult* res, unsigned long long ticket) {
     cudaStream_t s = L.stream;
     Work& w = L.w;
     w.nblk_cur = (g.n + 31) / 32;
@@ -338,7 +350,7 @@ cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const
     cudaMemsetAsync(w.pstats, 0, 2 * sizeof(PassStats), s);
     w.launches = 0;
     cudaEventRecord(L.ev[0], s);
-    build_authbits(w, g, d_authorized, n_authorized, s);
+    if (!sel.by_persistence) build_authbits(w, g, sel.ids, sel.n_ids, s);
     order_field(w, g, d_field, gout, O, s);
     cudaEventRecord(L.ev[1], s);
     int evi = 2;
@@ -349,6 +361,17 @@ cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const
             continue;
         }
         pass_reset(w, s);
+        if (sel.by_persistence) {
+            cudaMemsetAsync(w.authbits, 0, sizeof(unsigned) * (((size_t)g.n + 31) / 32), s);
+            if (side == 0) {
+                classify<-1>(w, g, O, s);
+                select_persistent<-1>(w, g, O, gout, sel.eps, sms, s);
+            } else {
+                classify<1>(w, g, O, s);
+                select_persistent<1>(w, g, O, gout, sel.eps, sms, s);
+            }
+            pass_reset(w, s);
+        }
         if (side == 0) {
             classify<-1>(w, g, O, s);               cudaEventRecord(L.ev[evi++], s);
             propagate<-1>(w, g, O, sms, s);         cudaEventRecord(L.ev[evi++], s);
@@ -470,15 +493,15 @@ void lts_destroy(lts_ctx* c) {
 
 const char* lts_last_error(const lts_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, const int32_t* d_authorized,
-                        int64_t n_authorized, lts_mode mode, float* d_out_field, int32_t* d_out_order,
-                        lts_stats* opt_stats) {
-    if (!c) return LTS_ERR_ARG;
-    c->err.clear();
+}  // extern "C"
+
+namespace {
+
+lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const float* d_field, const Selection& sel, lts_mode mode,
+                        float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats) {
     Lane& L = c->lane[0];
     long long n;
-    lts_status st = check_field(c, gr, L.nmax, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order,
-                                &n, "");
+    lts_status st = check_field(c, gr, L.nmax, d_field, sel.ids, sel.n_ids, mode, d_out_field, d_out_order, &n, "");
     if (st != LTS_OK) return st;
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
     cudaError_t e;
@@ -487,8 +510,7 @@ lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, co
         L.dirty = false;
     }
     const Geom g = geom_of(gr, n);
-    if ((e = enqueue_simplify(L, g, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order, c->sms,
-                              nullptr, 0)) != cudaSuccess)
+    if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, nullptr, 0)) != cudaSuccess)
         return cuda_fail(c, L, e, "launch");
     Work& w = L.w;
     cudaMemcpyAsync(w.h_ctr, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
@@ -502,6 +524,28 @@ lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, co
     }
     if (status != 0) return fail(c, (lts_status)status, status_text(status, w.h_ctr->oom_pool));
     return LTS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, const int32_t* d_authorized,
+                        int64_t n_authorized, lts_mode mode, float* d_out_field, int32_t* d_out_order,
+                        lts_stats* opt_stats) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    const Selection sel{d_authorized, n_authorized, false, 0.0};
+    return simplify_one(c, gr, d_field, sel, mode, d_out_field, d_out_order, opt_stats);
+}
+
+lts_status lts_simplify_persistence(lts_ctx* c, const lts_grid* gr, const float* d_field, double epsilon,
+                                    lts_mode mode, float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    if (!(epsilon >= 0.0)) return fail(c, LTS_ERR_ARG, "epsilon must be a non-negative number");
+    const Selection sel{nullptr, 0, true, epsilon};
+    return simplify_one(c, gr, d_field, sel, mode, d_out_field, d_out_order, opt_stats);
 }
 
 lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, const float* const* d_fields,
@@ -581,8 +625,9 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
         load[l] += n[i];
         Lane& L = c->lane[l];
         const Geom g = geom_of(&grids[i], n[i]);
-        if ((e = enqueue_simplify(L, g, d_fields[i], d_authorized[i], n_authorized[i], mode, d_out_fields[i],
-                                  d_out_orders[i], c->sms, c->batch_dev + i, 0)) != cudaSuccess)
+        const Selection sel{d_authorized[i], n_authorized[i], false, 0.0};
+        if ((e = enqueue_simplify(L, g, d_fields[i], sel, mode, d_out_fields[i], d_out_orders[i], c->sms,
+                                  c->batch_dev + i, 0)) != cudaSuccess)
             return cuda_fail(c, L, e, "launch");
         launches[i] = L.w.launches;
     }
@@ -629,8 +674,9 @@ lts_status lts_submit(lts_ctx* c, const lts_grid* gr, const float* d_field, cons
     if (t > kRing && (e = cudaEventSynchronize(c->ring_ev[slot])) != cudaSuccess) return cuda_fail(c, L, e, "wait");
     c->ring_host[slot].ticket = 0;
     const Geom g = geom_of(gr, n);
-    if ((e = enqueue_simplify(L, g, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order, c->sms,
-                              c->ring_dev + slot, t)) != cudaSuccess)
+    const Selection sel{d_authorized, n_authorized, false, 0.0};
+    if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, c->ring_dev + slot, t)) !=
+        cudaSuccess)
         return cuda_fail(c, L, e, "launch");
     if ((e = cudaEventRecord(c->ring_ev[slot], L.stream)) != cudaSuccess) return cuda_fail(c, L, e, "record");
     c->next_ticket = t + 1;

@@ -147,6 +147,7 @@ struct Work {
     int* loc;                            // per vertex: local index within its region
     int* U;                              // unauthorized extrema
     int* parent; int* wait_v;            // per class
+    int2* ctop;                          // per class: highest extremum and its Od (persistence-driven selection)
     int* sib_head; int* sib_next;        // per class: regions listed under the claimer of their saddle
     int4* tasks;                         // propagation tasks after the first step
     int* cnt;                            // per vertex: arrival counter of a saddle
@@ -184,6 +185,9 @@ template <int DIR>
 cudaError_t classify(Work& w, const Geom& g, const int* O, cudaStream_t s);
 template <int DIR>
 cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
+template <int DIR>
+cudaError_t select_persistent(Work& w, const Geom& g, const int* O, const float* F, double eps, int sms,
+                              cudaStream_t s);
 template <int DIR>
 cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
 template <int DIR>

@@ -42,6 +42,20 @@
 // resets it with a plain store.
 // Decisions that read shared mutable state (owner[], parent[]) are taken by
 // one lane and broadcast, so a team never diverges.
+//
+// Persistence-driven selection (Sec. 4.5) runs the same engine from every
+// extremum of the pass (PERS = true): a class also keeps its highest
+// extremum (the oldest of the classes it absorbed; a stopped class leaves it
+// in ctop[]) and, before it takes a popped vertex v, compares the scalar
+// difference between that extremum and v with eps in double precision.
+// Beyond eps the class ends and its highest extremum is marked persistent
+// in the authorized bitmap; a class whose queue runs dry has covered the
+// grid and its extremum, the global one, is marked too.  A class that
+// waits at a saddle for ever, or that was absorbed, marks nothing.  The
+// selection is then the set of extrema whose Elder-rule persistence exceeds
+// eps (with the global one): at a saddle where a class stops for good, the
+// class on the other side has a higher extremum, and a class that crossed a
+// saddle was within eps of its extremum there.
 #include <climits>
 
 #include <cuda/atomic>
@@ -80,7 +94,24 @@ struct PropArgs {
     long long log_cap;
     const int4* tasks;           // (class, u, Od(u), seed; -1 after a meeting at u)
     DevCounters* ctr;
+    // persistence-driven selection only
+    const float* F;              // the field of the pass
+    double eps;
+    int2* ctop;                  // per class: (highest extremum, its Od), written when the class stops
+    unsigned* authbits;          // persistent extrema are set here
 };
+
+// The difference between the class's highest extremum and v exceeds eps
+// (maxima pass: f(top) - f(v); minima pass: f(v) - f(top)).
+template <int DIR>
+__device__ __forceinline__ bool beyond_eps(float ftop, float fv, double eps) {
+    const double d = DIR > 0 ? (double)ftop - (double)fv : (double)fv - (double)ftop;
+    return d > eps;
+}
+
+__device__ __forceinline__ void mark_persistent(unsigned* bits, int v) {
+    atomicOr(bits + (v >> 5), 1u << (v & 31));
+}
 
 // Union-find root with path halving; parent links only ever point to
 // ancestors, so the benign races of halving keep every path valid.
@@ -303,13 +334,13 @@ __device__ __forceinline__ bool rebuild_first_queue(TeamState<NN>& T, const Geom
 // u's count makes a task that melds every class waiting at u.  The others
 // stop here.  u is not a seed, so its claim never meets a seed's plain store,
 // and u's neighbourhood overlaps m's, so most of its loads hit L1.
-template <int DIR, int NN>
+template <int DIR, int NN, bool PERS>
 __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __restrict__ O, PropArgs a, int4* tasks) {
     __shared__ int s_n, s_base;
     DevCounters* ctr = a.ctr;
     if (failed(&ctr->status)) return;
     const int nU = ctr->n_unauth;
-    if (nU > 0 && ctr->n_auth_ext == 0) {
+    if (!PERS && nU > 0 && ctr->n_auth_ext == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&ctr->status, LTS_ERR_NO_AUTHORIZED);
         return;
     }
@@ -322,13 +353,13 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
     for (long long b = (long long)blockIdx.x * blockDim.x; b < nU; b += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(b + threadIdx.x);
         int4 task = make_int4(-1, 0, 0, 0);
+        int m = -1, u = -1, ku = -1;
         if (c < nU) {
-            const int m = __ldg(a.U + c);
+            m = __ldg(a.U + c);
             a.owner[m] = c;
             a.vlog[c] = m;
             int x, y, z;
             coords_of(g, m, x, y, z);
-            int ku = -1, u = -1;
 #pragma unroll
             for (int q = 0; q < NN; ++q) {
                 const int nb = nbr_q<NN>(g, x, y, z, q);
@@ -337,9 +368,20 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
                     if (k > ku) { ku = k; u = nb; }
                 }
             }
+            if (PERS) {
+                a.ctop[c] = make_int2(m, od<DIR>(__ldg(O + m), g.n));
+                if (beyond_eps<DIR>(__ldg(a.F + m), __ldg(a.F + u), a.eps)) {   // ends before its first pop
+                    mark_persistent(a.authbits, m);
+                    a.vlog[nU + c] = -1;
+                    u = -1;
+                }
+            }
+        }
+        if (u >= 0) {
             a.wait_v[c] = u;
             const int prev = atomicCAS(a.owner + u, -1, c);
             a.vlog[nU + c] = prev == -1 ? u : -1;
+            int x, y, z;
             coords_of(g, u, x, y, z);
             int h = 0;
 #pragma unroll
@@ -369,7 +411,7 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
     }
 }
 
-template <int DIR, int NN>
+template <int DIR, int NN, bool PERS>
 __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
     constexpr int TS = TeamCfg<NN>::TS, E = TeamCfg<NN>::E;
     DevCounters* ctr = a.ctr;
@@ -394,6 +436,8 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
     long long sp_pos = 0, sp_end = 0;
     int c = -1;
     bool merged = false;     // c has absorbed other classes: membership needs find_root
+    int top_v = -1, top_k = -1;   // persistence-driven: the class's highest extremum and its Od (uniform)
+    float top_f = 0.f;
 
     for (;;) {
         int v, kv;
@@ -424,6 +468,11 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
             bool ok;
             if (seed >= 0) {                           // u has one higher neighbour, the seed of c
                 merged = false;
+                if (PERS) {
+                    top_v = seed;
+                    top_k = od<DIR>(__ldg(O + seed), g.n);
+                    top_f = __ldg(a.F + seed);
+                }
                 ok = rebuild_first_queue<DIR, NN>(T, g, O, seed, u, mk, a, tl);
             } else {
                 // a meeting at u: its higher neighbours are the seeds of the classes that met
@@ -432,12 +481,18 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                 coords_of(g, u, ux, uy, uz);
                 const int unb = tl < NN ? nbr_q<NN>(g, ux, uy, uz, tl) : -1;
                 bool hi = false;
-                int own = -1;
+                int own = -1, ok_u = -1;
                 if (unb >= 0) {
-                    hi = od<DIR>(__ldg(O + unb), g.n) > kv;
+                    ok_u = od<DIR>(__ldg(O + unb), g.n);
+                    hi = ok_u > kv;
                     own = __ldcg(a.owner + unb);
                 }
                 unsigned hm = __ballot_sync(T.tmask, hi);
+                if (PERS) {                            // the highest of the seeds that met at u
+                    top_k = __reduce_max_sync(T.tmask, hi ? ok_u : -1);
+                    top_v = __shfl_sync(T.tmask, unb, __ffs(__ballot_sync(T.tmask, hi && ok_u == top_k)) - 1);
+                    top_f = __ldg(a.F + top_v);
+                }
                 ok = true;
                 while (hm && ok) {
                     const int L = __ffs(hm) - 1;
@@ -461,8 +516,13 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
             for (int e = 0; e < E; ++e)
                 if (T.sk[e] > bk) { bk = T.sk[e]; bs = e; }
             const int K = __reduce_max_sync(T.tmask, bk);
-            if (K < 0 && T.ov_top < 0) {                  // cannot happen with an authorized maximum
-                if (leader) set_status(st, LTS_ERR_INTERNAL);
+            if (K < 0 && T.ov_top < 0) {
+                if (PERS) {                            // the class covered the grid: the global extremum
+                    if (leader) mark_persistent(a.authbits, top_v);
+                    c = -1;
+                    continue;
+                }
+                if (leader) set_status(st, LTS_ERR_INTERNAL);   // cannot happen with an authorized maximum
                 break;
             }
             if (T.ov_top > K) {
@@ -488,7 +548,11 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
         const unsigned long long mark = a.tag | (unsigned)c;
         // the leader claims v first, so that the atomic overlaps the neighbour loads
         int prev = 0;
-        if (leader && !resumed) prev = atomicCAS(a.owner + v, -1, c);
+        float fv = 0.f;
+        if (leader && !resumed) {
+            if (PERS) fv = __ldg(a.F + v);
+            prev = atomicCAS(a.owner + v, -1, c);
+        }
         // ---- one round of loads: order, owner, mark of every neighbour ----
         int x, y, z;
         coords_of(g, v, x, y, z);
@@ -501,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
             qm = __ldcg(a.qmark + nb);
         }
         // the leader claims v (or learns its owner) and broadcasts the outcome
-        int decision = 0;             // 0 skip, 1 claimed (or resumed), 2 owned by another class
+        int decision = 0;             // 0 skip, 1 claimed (or resumed), 2 owned by another class, 3 ends (Sec. 4.5)
         if (leader) {
             if (resumed) {
                 decision = 1;
@@ -520,10 +584,17 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
             } else {
                 decision = (prev == c || (merged && find_root(a.parent, prev) == c)) ? 0 : 2;
             }
+            // persistence-driven: v is more than eps below the class's extremum
+            if (PERS && decision > 0 && !resumed && beyond_eps<DIR>(top_f, fv, a.eps)) decision = 3;
         }
         decision = __shfl_sync(T.tmask, decision, T.tb);
         if (decision < 0) break;
         if (decision == 0) continue;
+        if (PERS && decision == 3) {                  // the class ends: its extremum is persistent
+            if (leader) mark_persistent(a.authbits, top_v);
+            c = -1;
+            continue;
+        }
         const bool higher = nb >= 0 && on > kv;
         bool inC = nb >= 0 && ow >= 0 && (ow == c || (merged && find_root(a.parent, ow) == c));
         const int h = __popc(__ballot_sync(T.tmask, higher));
@@ -577,6 +648,7 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
                 __stcg(a.wait_v + c, v);
                 const long long ho = T.ov.h ? (long long)(T.ov.h - a.heap_pool) : 0;
                 __stcg(a.heaprec + c, make_int4((int)(ho & 0xffffffffLL), (int)(ho >> 32), T.ov.n, T.ov.cap));
+                if (PERS) __stcg(a.ctop + c, make_int2(top_v, top_k));
                 // release: this class's spill and records; acquire: those of the
                 // classes that arrived before
                 cuda::atomic_ref<int, cuda::thread_scope_device> counter(a.cnt[v]);
@@ -600,13 +672,23 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
             const bool rep_lane = higher && rt != c && rt >= 0 && (__ffs(grp & hmask) - 1) == T.lane;
             int sb = 0, sn = 0;
             int4 hr = make_int4(0, 0, 0, 0);
+            int2 ct = make_int2(-1, -1);
             if (rep_lane) {                            // one lane per class to merge
                 sb = __ldcg(a.spill_base + rt);
                 sn = __ldcg(a.spill_n + rt);
                 if (sn >= 0) hr = __ldcg(a.heaprec + rt);
+                if (PERS) ct = __ldcg(a.ctop + rt);
                 __stcg(a.parent + rt, c);
             }
             unsigned todo = __ballot_sync(T.tmask, rep_lane);
+            if (PERS) {                                // the elder of the merged classes survives
+                const int mk2 = __reduce_max_sync(T.tmask, ct.y);
+                if (mk2 > top_k) {
+                    top_k = mk2;
+                    top_v = __shfl_sync(T.tmask, ct.x, __ffs(__ballot_sync(T.tmask, ct.y == mk2)) - 1);
+                    top_f = __ldg(a.F + top_v);
+                }
+            }
             merged = true;
             bool okm = true;
             while (todo && okm) {
@@ -669,27 +751,62 @@ __global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const i
         while (log_pos < log_end) a.vlog[log_pos++] = -1;
 }
 
-}  // namespace
+// Persistence-driven selection leaves claims and arrival counters behind
+// (classes that ended or wait for ever): clear them for the pass proper.
+__global__ void pers_clear_kernel(const DevCounters* ctr, const int* __restrict__ vlog, const int* __restrict__ wait_v,
+                                  int* owner, int* cnt, long long log_cap) {
+    if (failed(&ctr->status)) return;
+    const long long nlog = min((long long)ctr->log_cursor, log_cap);
+    const int nU = ctr->n_unauth;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlog; i += stride) {
+        const int v = vlog[i];
+        if (v >= 0) owner[v] = -1;
+    }
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nU; c += stride) {
+        const int v = wait_v[c];
+        if (v >= 0) cnt[v] = 0;
+    }
+}
 
-template <int DIR>
-cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s) {
+template <int DIR, bool PERS>
+cudaError_t launch_propagate(Work& w, const Geom& g, const int* O, const float* F, double eps, int sms,
+                             cudaStream_t s) {
     PropArgs a;
     a.U = w.U; a.owner = w.owner; a.qmark = w.qmark; a.tag = (unsigned long long)(++w.pass_tag) << 32;
     a.parent = w.parent; a.wait_v = w.wait_v; a.cnt = w.cnt;
     a.spill_base = w.spill_base; a.spill_n = w.spill_n; a.heaprec = w.heaprec;
     a.spill_pool = w.spill_pool; a.spill_cap = w.spill_cap; a.heap_pool = w.heap_pool; a.heap_cap = w.heap_cap;
     a.vlog = w.vlog; a.log_cap = w.log_cap; a.tasks = w.tasks; a.ctr = w.ctr;
+    a.F = F; a.eps = eps; a.ctop = w.ctop; a.authbits = w.authbits;
     const int pb = sms * 8;
     const int blocks = w.lanes / kThreads;
     if (g.nn == 14) {
-        first_step_kernel<DIR, 14><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
-        propagate_kernel<DIR, 14><<<blocks, kThreads, 0, s>>>(g, O, a);
+        first_step_kernel<DIR, 14, PERS><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
+        propagate_kernel<DIR, 14, PERS><<<blocks, kThreads, 0, s>>>(g, O, a);
     } else {
-        first_step_kernel<DIR, 6><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
-        propagate_kernel<DIR, 6><<<blocks, kThreads, 0, s>>>(g, O, a);
+        first_step_kernel<DIR, 6, PERS><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
+        propagate_kernel<DIR, 6, PERS><<<blocks, kThreads, 0, s>>>(g, O, a);
     }
     w.launches += 2;
+    if (PERS) {
+        pers_clear_kernel<<<sms * 4, 256, 0, s>>>(w.ctr, w.vlog, w.wait_v, w.owner, w.cnt, w.log_cap);
+        w.launches += 1;
+    }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+template <int DIR>
+cudaError_t propagate(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s) {
+    return launch_propagate<DIR, false>(w, g, O, nullptr, 0.0, sms, s);
+}
+
+template <int DIR>
+cudaError_t select_persistent(Work& w, const Geom& g, const int* O, const float* F, double eps, int sms,
+                              cudaStream_t s) {
+    return launch_propagate<DIR, true>(w, g, O, F, eps, sms, s);
 }
 
 int propagate_lanes(int sms) { return sms * 10 * kThreads; }
@@ -700,5 +817,7 @@ long long propagate_heap_slack(int lanes) { return (long long)(lanes / 32) * 204
 
 template cudaError_t propagate<1>(Work&, const Geom&, const int*, int, cudaStream_t);
 template cudaError_t propagate<-1>(Work&, const Geom&, const int*, int, cudaStream_t);
+template cudaError_t select_persistent<1>(Work&, const Geom&, const int*, const float*, double, int, cudaStream_t);
+template cudaError_t select_persistent<-1>(Work&, const Geom&, const int*, const float*, double, int, cudaStream_t);
 
 }  // namespace lts

@@ -9,6 +9,11 @@ order field (mode both: minima pass, then maxima pass) with its statistics.
     python tests/golden/make_golden.py boxnoise3d_512
     python tests/golden/make_golden.py mixed_batch_256    # config 3, 256 fields
     python tests/golden/make_golden.py serve_pool_16      # config 4, the first 16 requests
+    python tests/golden/make_golden.py pers boxnoise3d_512   # persistence-driven (Sec. 4.5)
+
+The persistence-driven records ({name}_pers.json) hold, for eps = thr * range
+of the field (range = max - min in double precision), the hashes of the
+oracle's pers_lts output (mode both) and the number of extrema each pass keeps.
 
 The GPU tests regenerate the field, check its hash, run the library with the
 stored authorized list and compare the hashes of its outputs; bench.py uses
@@ -102,11 +107,37 @@ def main_set(name, procs=8):
     print(name, len(specs), "fields,", int(off[-1]), "authorized ids,", rec["oracle_seconds"], "s")
 
 
+def main_pers(name):
+    """Persistence-driven LTS (Sec. 4.5) on a single-field workload."""
+    cfg, shape = TARGETS[name]
+    t0 = time.time()
+    f = W.make_config_field(cfg, shape=shape)
+    thr = W.CONFIGS[cfg]["thr"]
+    eps = thr * float(np.float64(f.max()) - np.float64(f.min()))
+    g = f.copy()
+    O = oracle.order_field(f)
+    kept = []
+    for d in (-1, 1):
+        ids = oracle.persistent_by_elder(g, O, d, eps)
+        kept.append(int(ids.size))
+        g, O, _ = oracle.one_pass(g, O, ids, d)
+    rec = {"workload": name, "config": cfg, "shape": list(f.shape), "thr": thr, "eps": eps,
+           "field_sha256": W.sha256_of(f), "kept_min": kept[0], "kept_max": kept[1],
+           "g_sha256": W.sha256_of(g), "order_sha256": W.sha256_of(O),
+           "max_abs_change": float(np.max(np.abs(g.astype(np.float64) - f))),
+           "oracle_seconds": round(time.time() - t0, 1)}
+    with open(os.path.join(HERE, f"{name}_pers.json"), "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(json.dumps(rec, indent=1))
+
+
 from tests.golden.store import load_authorized, load_record, load_set_authorized  # noqa: E402,F401
 
 
 if __name__ == "__main__":
-    if sys.argv[1] in SETS:
+    if sys.argv[1] == "pers":
+        main_pers(sys.argv[2])
+    elif sys.argv[1] in SETS:
         main_set(sys.argv[1])
     else:
         main(sys.argv[1])

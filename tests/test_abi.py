@@ -26,7 +26,7 @@ def lib():
 def test_header_declares_the_boundary():
     assert declared_entry_points() == sorted(
         ["lts_create", "lts_workspace_bytes", "lts_simplify", "lts_last_error", "lts_destroy",
-         "lts_order_field_static", "lts_simplify_batch", "lts_submit", "lts_poll"])
+         "lts_order_field_static", "lts_simplify_batch", "lts_submit", "lts_poll", "lts_simplify_persistence"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -49,6 +49,7 @@ def test_argument_checks_need_no_device(lib):
     bad.ndim = 4
     assert lts.lts_workspace_bytes(bad) == 0
     assert lts.load().lts_simplify(None, ctypes.byref(g), None, None, 0, 3, None, None, None) == 1
+    assert lts.load().lts_simplify_persistence(None, ctypes.byref(g), None, 0.5, 3, None, None, None) == 1
     assert lts.load().lts_simplify_batch(None, 1, None, None, None, None, 3, None, None, None) == 1
     assert lts.load().lts_submit(None, ctypes.byref(g), None, None, 0, 3, None, None, None) == 1
     assert lts.load().lts_poll(None, 1, None) == 1
