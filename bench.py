@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-pers", action="store_true")
+    p.add_argument("--no-sweep", action="store_true")
     return p.parse_args()
 
 
@@ -304,17 +306,18 @@ def serve_leg(lts, torch, dev, nreq=2000, warm=100, rate=200.0, max_inflight=64,
             overloaded = True
         while i < nreq and not overloaded and arr[i] <= now and len(pending) < max_inflight:
             k = i % len(fields)
-            g, o = outs[k]
+            # requests in flight side by side never share output buffers
+            g, o = torch.empty_like(fields[k]), torch.empty(fields[k].shape, dtype=torch.int32, device=dev)
             code, t = lts.lts_submit(ctx._ctx, grids[k], fields[k].data_ptr(), ids[k].data_ptr(), ids[k].numel(),
                                      "both", g.data_ptr(), o.data_ptr())
             if code != 0:
                 raise lts.LtsError(code, lts.lts_last_error(ctx._ctx))
-            pending[t] = i
+            pending[t] = (i, g, o)
             i += 1
         for t in list(pending):
             code, done = lts.lts_poll(ctx._ctx, t)
             if done:
-                j = pending.pop(t)
+                j = pending.pop(t)[0]
                 lat[j] = time.perf_counter() - t0 - arr[j]
                 errors += code != 0
         if not pending and i < nreq and not overloaded:
@@ -328,11 +331,91 @@ def serve_leg(lts, torch, dev, nreq=2000, warm=100, rate=200.0, max_inflight=64,
     served = served[~np.isnan(served)]
     pct = (lambda q: round(float(np.percentile(served, q)), 3)) if served.size else (lambda q: None)
     return {"workload": "serve_3d: Poisson arrivals, 3D cubes of side 32..256 (pool of 16 cycled)",
+            "admission": "up to 7 serving workspaces of 256^3 side by side, HBM budget 120 GiB",
             "requests": nreq, "served": int(i), "warmup_excluded": warm, "rate_hz": rate,
             "mean_vertices": int(np.mean([sizes[j % len(sizes)] for j in range(nreq)])),
             "p50_ms": pct(50), "p99_ms": pct(99),
             "mean_ms": round(float(np.mean(served)), 3) if served.size else None, "errors": int(errors),
             "overloaded": bool(overloaded)}
+
+
+def pers_leg(lts, torch, ctx, fd, f, name, steps=3):
+    """Persistence-driven LTS (Sec. 4.5) on the same field: eps = threshold x
+    range, no authorized list; every pass selects its persistent extrema with
+    its own propagations first.  CUDA events on the context's stream around
+    `steps` calls after one warm-up; parity against the stored oracle hashes."""
+    from tests.golden import store as mg
+
+    try:
+        rec = mg.load_record(f"{name}_pers")
+    except FileNotFoundError:
+        return None
+    eps = rec["thr"] * float(np.float64(f.max()) - np.float64(f.min()))
+    g = torch.empty_like(fd)
+    o = torch.empty(fd.shape, dtype=torch.int32, device=fd.device)
+    _, _, st = ctx.simplify_persistence(fd, eps, "both", out_field=g, out_order=o)
+    torch.cuda.synchronize(fd.device)
+    parity = (W.sha256_of(o.cpu().numpy()) == rec["order_sha256"] and W.sha256_of(g.cpu().numpy()) == rec["g_sha256"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = ctx.stream
+    sel_us = 0.0
+    torch.cuda.synchronize(fd.device)
+    e0.record(stream)
+    for _ in range(steps):
+        _, _, s = ctx.simplify_persistence(fd, eps, "both", out_field=g, out_order=o)
+        sel_us += s["stage_us"]["classify"]
+    e1.record(stream)
+    torch.cuda.synchronize(fd.device)
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": f"{name}, eps = {rec['thr']} x range, mode both, no authorized list",
+            "eps": eps, "ms_per_call": round(ms, 3), "mvps": round(fd.numel() / (ms * 1e-3) / 1e6, 3),
+            "selection_and_classify_ms": round(sel_us / steps / 1e3, 3),
+            "kept": [rec["kept_min"], rec["kept_max"]], "removed": st["removed"],
+            "parity_vs_oracle": bool(parity)}
+
+
+def sweep_leg(lts, torch, dev, side=256, points=(0, 10, 20, 30, 40, 50, 60, 70, 80, 90, 95, 99), reps=3):
+    """Output sensitivity (Fig. 6): time of one mode-both call on a white-noise
+    cube (uniform [0, 1) float32, seeded) as a function of the share of
+    extrema removed.  For a share p, a random p% of the vertices (never the
+    global minimum or maximum) is left out of an otherwise complete authorized
+    list, so about p% of the extrema of each pass are removed; the exact
+    counts come back in the call's statistics.  CUDA events on the context's
+    stream, median of `reps` calls after one warm-up."""
+    f = W.uniform_noise_field((side, side, side), W.seed_of(5))
+    n = f.size
+    flat = f.reshape(-1)
+    keep = [int(np.flatnonzero(flat == flat.min()).min()), int(np.flatnonzero(flat == flat.max()).max())]
+    rng = np.random.Generator(np.random.PCG64(W.seed_of(5, 1)))
+    perm = rng.permutation(n).astype(np.int32)
+    perm = perm[~np.isin(perm, keep)]
+    ctx = lts.Context(n, device=dev.index)
+    fd = torch.from_numpy(f).to(dev)
+    g = torch.empty_like(fd)
+    o = torch.empty(fd.shape, dtype=torch.int32, device=dev)
+    rows = []
+    try:
+        for p in points:
+            drop = int(round(p / 100.0 * n))
+            ids = np.sort(perm[drop:]) if drop < perm.size else np.zeros(0, np.int32)
+            ids = np.concatenate([ids, np.array(keep, np.int32)]).astype(np.int32)
+            idd = torch.from_numpy(ids).to(dev)
+            _, _, st = ctx.simplify(fd, idd, "both", out_field=g, out_order=o)
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                ctx.simplify(fd, idd, "both", out_field=g, out_order=o, with_stats=False)
+                e1.record(ctx.stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            rows.append({"removed_pct": p, "ms": round(statistics.median(times), 3), "removed": st["removed"],
+                         "regions": st["regions"], "max_region": st["max_region"],
+                         "region_vertices": st["region_vertices"]})
+    finally:
+        ctx.close()
+    return {"workload": f"white noise {side}^3 (uniform [0,1) float32), a random share of the extrema removed",
+            "points": rows}
 
 
 def main():
@@ -431,6 +514,8 @@ def main():
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     batch = None if args.no_batch or world > 1 else batch_leg(lts, torch, dev)
     serve = None if args.no_serve or world > 1 else serve_leg(lts, torch, dev)
+    pers = None if args.no_pers or world > 1 else pers_leg(lts, torch, ctx, fd, f, args.workload)
+    sweep = None if args.no_sweep or world > 1 else sweep_leg(lts, torch, dev)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mvertices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
@@ -454,6 +539,8 @@ def main():
         "e2e": e2e,
         "batch": batch,
         "serve": serve,
+        "persistence_driven": pers,
+        "output_sensitivity": sweep,
         "clocks": clk.summary(),
         "gpu_launches": int(st.get("launches", 0)) * args.steps,
     }

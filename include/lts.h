@@ -153,20 +153,40 @@ lts_status lts_simplify_batch(lts_ctx* ctx, int32_t nf, const lts_grid* grids, c
                               const int32_t* const* d_authorized, const int64_t* n_authorized, lts_mode mode,
                               float* const* d_out_fields, int32_t* const* d_out_orders, lts_stats* opt_stats);
 
-/* Serving.  lts_submit enqueues one simplification (arguments as in
- * lts_simplify) on the context's stream and returns at once with a ticket
- * (> 0); requests run in submission order.  lts_poll sets *done to 1 once the
- * request is finished and then returns its status (LTS_OK or the error it
- * met); while it runs, *done is 0 and the return is LTS_OK.  The result of a
- * ticket stays readable until 1024 newer requests have been submitted
- * (later polls give LTS_ERR_ARG); lts_submit waits for the request 1024
- * places before it if that one is still running.  A failed request leaves
- * the workspace clean for the requests behind it.  The first lts_submit on
- * a context allocates its pinned request ring. */
+/* Serving (continuous batching).  lts_submit enqueues one simplification
+ * (arguments as in lts_simplify) and returns at once with a ticket (> 0).
+ * Requests run on the context's serving workspaces, each with its own stream
+ * and each sized for the context's max_vertices: a request goes to an idle
+ * workspace, or to a new one while the serving budget (lts_serve_config) and
+ * the device's free memory allow, or else behind the requests of the
+ * workspace with the fewest outstanding vertices.  Requests on different
+ * workspaces run concurrently on the device; each starts after the work the
+ * caller had enqueued on the context's stream when it was submitted.  A
+ * request's result is the one lts_simplify gives for the same arguments,
+ * whatever runs beside it.  Both outputs are working arrays of the passes
+ * until the request is done, so requests in flight at the same time must not
+ * share an output buffer (inputs may be shared).  lts_poll sets *done to 1 once the request is
+ * finished and then returns its status (LTS_OK or the error it met); while it
+ * runs, *done is 0 and the return is LTS_OK.  The result of a ticket stays
+ * readable until 1024 newer requests have been submitted (later polls give
+ * LTS_ERR_ARG); lts_submit waits for the request 1024 places before it if
+ * that one is still running.  A failed request leaves its workspace clean for
+ * the requests behind it.  The first lts_submit on a context allocates its
+ * pinned request ring.  When no serving workspace can be allocated, requests
+ * run one after another on the context's own workspace and stream. */
 lts_status lts_submit(lts_ctx* ctx, const lts_grid* g, const float* d_field, const int32_t* d_authorized,
                       int64_t n_authorized, lts_mode mode, float* d_out_field, int32_t* d_out_order,
                       uint64_t* ticket);
 lts_status lts_poll(lts_ctx* ctx, uint64_t ticket, int* done);
+
+/* Serving limits: at most max_concurrent serving workspaces (0..7; 0 runs
+ * every request on the context's own workspace and stream, in submission
+ * order) and at most hbm_budget_bytes of device memory for them together
+ * (each takes lts_workspace_bytes of the largest grid).  Defaults: 7
+ * workspaces, 120 GiB.  Workspaces already allocated are kept; the limits
+ * apply to later allocations and to the choice of workspace.
+ * Errors: LTS_ERR_ARG (max_concurrent outside [0, 7], negative budget). */
+lts_status lts_serve_config(lts_ctx* ctx, int32_t max_concurrent, int64_t hbm_budget_bytes);
 
 /* Message describing the last error on this context ("" if none). */
 const char* lts_last_error(const lts_ctx* ctx);

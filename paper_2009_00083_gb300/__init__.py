@@ -15,7 +15,7 @@ import os
 __all__ = [
     "LtsGrid", "LtsStats", "LtsError", "Context", "lts_create", "lts_simplify", "lts_destroy",
     "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "lts_simplify_batch", "lts_submit",
-    "lts_poll", "lts_simplify_persistence", "library_path", "load", "simplify", "simplify_persistence",
+    "lts_poll", "lts_simplify_persistence", "lts_serve_config", "library_path", "load", "simplify", "simplify_persistence",
     "MODE_MIN", "MODE_MAX", "MODE_BOTH", "ORDER_STATIC_MAX_VERTICES",
 ]
 
@@ -107,6 +107,8 @@ def load():
         lib.lts_submit.restype = ctypes.c_int
         lib.lts_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
         lib.lts_poll.restype = ctypes.c_int
+        lib.lts_serve_config.argtypes = [P, ctypes.c_int32, ctypes.c_int64]
+        lib.lts_serve_config.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -189,6 +191,10 @@ def lts_poll(ctx, ticket: int):
     d = ctypes.c_int(0)
     code = load().lts_poll(ctx, ctypes.c_uint64(ticket), ctypes.byref(d))
     return int(code), bool(d.value)
+
+
+def lts_serve_config(ctx, max_concurrent: int, hbm_budget_bytes: int) -> int:
+    return load().lts_serve_config(ctx, int(max_concurrent), int(hbm_budget_bytes))
 
 
 def lts_order_field_static(device: int, grid: LtsGrid, d_field: int, d_order: int, cuda_stream: int = 0):
@@ -281,6 +287,11 @@ class Context:
         if code != 0:
             raise LtsError(code, lts_last_error(self._ctx))
         return outs, ([st[i].as_dict() for i in range(len(fields))] if st is not None else None)
+
+    def serve_config(self, max_concurrent: int, hbm_budget_bytes: int = 120 << 30):
+        code = lts_serve_config(self._ctx, max_concurrent, hbm_budget_bytes)
+        if code != 0:
+            raise LtsError(code, lts_last_error(self._ctx))
 
     def submit(self, field, authorized, mode="both"):
         """Queues a simplification; returns a ticket.  The tensors are kept

@@ -4,7 +4,9 @@
 // workspaces at once (lts_simplify_batch), or as queued requests
 // (lts_submit / lts_poll).
 #include <algorithm>
+#include <climits>
 #include <cstdio>
+#include <deque>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -34,7 +36,8 @@ struct ReqResult {
 
 namespace {
 
-constexpr int kMaxLanes = 4;       // the context's own workspace and up to 3 more for batches
+constexpr int kMaxLanes = 8;       // the context's own workspace and up to 7 more
+constexpr int kBatchLanes = 4;     // workspaces a batch spreads over
 constexpr int kRing = 1024;        // serving requests in flight per context
 
 // A workspace with the stream its work is enqueued on.
@@ -69,6 +72,9 @@ struct lts_ctx {
     cudaEvent_t ring_ev[kRing];
     bool ring_ready = false;
     unsigned long long next_ticket = 1;
+    int serve_max = kMaxLanes - 1;    // serving workspaces (lanes 1..serve_max); 0: the context's own
+    long long serve_budget = 120LL << 30;
+    std::deque<std::pair<unsigned long long, long long>> inflight[kMaxLanes];   // (ticket, vertices) per lane
 };
 
 namespace {
@@ -444,6 +450,70 @@ lts_status ensure_ring(lts_ctx* c) {
     return LTS_OK;
 }
 
+// Outstanding vertices of a lane's served requests (finished ones retired).
+long long lane_backlog(lts_ctx* c, int li) {
+    auto& q = c->inflight[li];
+    while (!q.empty()) {
+        const unsigned long long t = q.front().first;
+        // a ticket whose ring slot was reused is finished (submit waited for it)
+        if (t + kRing < c->next_ticket || cudaEventQuery(c->ring_ev[t % kRing]) == cudaSuccess) {
+            q.pop_front();
+            continue;
+        }
+        cudaGetLastError();
+        break;
+    }
+    long long b = 0;
+    for (const auto& r : q) b += r.second;
+    return b;
+}
+
+// Continuous batching: a request goes to an idle serving workspace, or to a
+// new one while the budget and the device's free memory allow, or else to the
+// workspace with the fewest outstanding vertices.  Every serving workspace
+// fits the context's largest grid and runs on its own stream.  With no
+// serving workspace (serve_max == 0, or nothing could be allocated) requests
+// run on the context's own workspace and stream, one after another.
+int pick_serve_lane(lts_ctx* c, long long n) {
+    const long long nmax = c->lane[0].nmax;
+    const size_t per_lane = bytes_for(sizes_for(nmax, c->sms));
+    int best = -1;
+    long long best_load = LLONG_MAX;
+    int nalloc = 0, free_slot = -1;
+    for (int i = 1; i <= c->serve_max; ++i) {
+        Lane& L = c->lane[i];
+        if (!L.stream || L.nmax < nmax) {
+            // absent, or a smaller workspace left by a batch: usable once re-allocated while idle
+            if (free_slot < 0 && (!L.stream || (lane_backlog(c, i) == 0 && cudaStreamQuery(L.stream) == cudaSuccess)))
+                free_slot = i;
+            continue;
+        }
+        ++nalloc;
+        const long long b = lane_backlog(c, i);
+        if (b < best_load) { best_load = b; best = i; }
+    }
+    (void)n;
+    if (best >= 0 && best_load == 0) return best;
+    if (free_slot >= 0 && (long long)((nalloc + 1) * per_lane) <= c->serve_budget) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr > per_lane + (1ull << 30)) {
+            Lane& L = c->lane[free_slot];
+            if (L.stream) lane_free(L);
+            cudaStream_t s;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess) {
+                if (lane_alloc(L, nmax, c->sms, s, true) == LTS_OK) {
+                    c->nlanes = std::max(c->nlanes, free_slot + 1);
+                    return free_slot;
+                }
+                cudaStreamDestroy(s);
+                L.stream = nullptr;
+            }
+        }
+        cudaGetLastError();
+    }
+    return best >= 0 ? best : 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -569,7 +639,7 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
     cudaError_t e;
     // workspaces: the context's own, and up to kMaxLanes - 1 more sized for the largest field
-    const int want = std::min(kMaxLanes, nf);
+    const int want = std::min(kBatchLanes, nf);
     for (int i = 1; i < want; ++i) {
         Lane& L = c->lane[i];
         if (L.nmax >= nbig) continue;
@@ -650,35 +720,56 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
     return LTS_OK;
 }
 
+lts_status lts_serve_config(lts_ctx* c, int32_t max_concurrent, int64_t hbm_budget_bytes) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    if (max_concurrent < 0 || max_concurrent > kMaxLanes - 1 || hbm_budget_bytes < 0)
+        return fail(c, LTS_ERR_ARG, "max_concurrent must be in [0, 7] and the budget non-negative");
+    c->serve_max = max_concurrent;
+    c->serve_budget = hbm_budget_bytes;
+    return LTS_OK;
+}
+
 lts_status lts_submit(lts_ctx* c, const lts_grid* gr, const float* d_field, const int32_t* d_authorized,
                       int64_t n_authorized, lts_mode mode, float* d_out_field, int32_t* d_out_order,
                       uint64_t* ticket) {
     if (!c) return LTS_ERR_ARG;
     c->err.clear();
     if (!ticket) return fail(c, LTS_ERR_ARG, "null ticket");
-    Lane& L = c->lane[0];
     long long n;
-    lts_status st = check_field(c, gr, L.nmax, d_field, d_authorized, n_authorized, mode, d_out_field, d_out_order,
-                                &n, "");
+    lts_status st = check_field(c, gr, c->lane[0].nmax, d_field, d_authorized, n_authorized, mode, d_out_field,
+                                d_out_order, &n, "");
     if (st != LTS_OK) return st;
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
     if ((st = ensure_ring(c)) != LTS_OK) return st;
     cudaError_t e;
+    const unsigned long long t = c->next_ticket;
+    const int li = pick_serve_lane(c, n);
+    Lane& L = c->lane[li];
     if (L.dirty) {
         if ((e = clean_workspace(L)) != cudaSuccess) return cuda_fail(c, L, e, "clean");
         L.dirty = false;
     }
-    const unsigned long long t = c->next_ticket;
     const int slot = (int)(t % kRing);
     // the slot's previous request must be finished before the slot is reused
     if (t > kRing && (e = cudaEventSynchronize(c->ring_ev[slot])) != cudaSuccess) return cuda_fail(c, L, e, "wait");
     c->ring_host[slot].ticket = 0;
+    if (li != 0) {
+        // a serving workspace starts after what the caller enqueued on the context's stream
+        if (!c->fork) {
+            cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+            for (auto& j : c->join) cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        }
+        cudaEventRecord(c->fork, c->lane[0].stream);
+        cudaStreamWaitEvent(L.stream, c->fork, 0);
+    }
     const Geom g = geom_of(gr, n);
     const Selection sel{d_authorized, n_authorized, false, 0.0};
     if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, c->ring_dev + slot, t)) !=
         cudaSuccess)
         return cuda_fail(c, L, e, "launch");
     if ((e = cudaEventRecord(c->ring_ev[slot], L.stream)) != cudaSuccess) return cuda_fail(c, L, e, "record");
+    c->inflight[li].emplace_back(t, n);
     c->next_ticket = t + 1;
     *ticket = t;
     return LTS_OK;

@@ -5,6 +5,8 @@ available here; these generators reproduce their sizes and character:
 
 * ``gaussian_field``: a sum of K Gaussian bumps of random sign plus uniform
   noise (a smooth field with many small noise extrema), 2D or 3D.
+* ``uniform_noise_field``: white noise, independent U[0, 1) samples (the
+  random dataset of the output-sensitivity sweep, Fig. 6).
 * ``box_noise_field``: white noise box-filtered with radius r and quantized to
   1024 levels, so that many neighbouring vertices tie and the order field has
   to break ties by vertex id (Section 4.1).
@@ -111,6 +113,13 @@ def box_noise_field(shape, radius, levels, seed, bits=24):
         q = np.zeros_like(v)
     np.minimum(q, levels - 1, out=q)
     return (q / float(levels - 1)).astype(np.float32)
+
+
+def uniform_noise_field(shape, seed):
+    """White noise: independent U[0, 1) samples as float32 (the random field of
+    the output-sensitivity sweep)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.random(int(np.prod(shape)), dtype=np.float32).reshape(shape)
 
 
 def make_config_field(config: int, k: int = 0, shape=None):

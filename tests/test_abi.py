@@ -26,7 +26,8 @@ def lib():
 def test_header_declares_the_boundary():
     assert declared_entry_points() == sorted(
         ["lts_create", "lts_workspace_bytes", "lts_simplify", "lts_last_error", "lts_destroy",
-         "lts_order_field_static", "lts_simplify_batch", "lts_submit", "lts_poll", "lts_simplify_persistence"])
+         "lts_order_field_static", "lts_simplify_batch", "lts_submit", "lts_poll", "lts_simplify_persistence",
+         "lts_serve_config"])
 
 
 def test_library_exports_every_declared_symbol(lib):

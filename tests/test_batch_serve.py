@@ -169,9 +169,13 @@ def test_full_batch_workload_against_stored_oracle_hashes(lts):
         ctx.close()
 
 
-def test_served_pool_against_stored_oracle_hashes(lts):
+@pytest.mark.parametrize("concurrent", [0, 3, 7])
+def test_served_pool_against_stored_oracle_hashes(lts, concurrent):
     """The first 16 served requests (3D cubes of side 32..256) through
-    lts_submit / lts_poll, all queued at once."""
+    lts_submit / lts_poll, all queued at once, each twice (forwards, then
+    backwards), on the context's own workspace one after another
+    (concurrent = 0) or spread over 3 or 7 serving workspaces running side by
+    side: every result equals the oracle's stored one, alone or in the mix."""
     from tests.golden import store as mg
 
     rec = mg.load_record("serve_pool_16")
@@ -184,18 +188,42 @@ def test_served_pool_against_stored_oracle_hashes(lts):
         reqs.append((torch.from_numpy(f).to(dev), torch.from_numpy(a).to(dev)))
     ctx = lts.Context(max(f.numel() for f, _ in reqs), device=0)
     try:
+        ctx.serve_config(concurrent)
         torch.cuda.synchronize()
-        tickets = [ctx.submit(f, a, "both") for f, a in reqs]
+        order = list(range(16)) + list(range(15, -1, -1))
+        tickets = [ctx.submit(*reqs[k], "both") for k in order]
         done = {}
         while len(done) < len(tickets):
-            for k, t in enumerate(tickets):
-                if k not in done:
+            for i, t in enumerate(tickets):
+                if i not in done:
                     r = ctx.poll(t)
                     if r is not None:
-                        done[k] = r
-        for k, fr in enumerate(rec["fields"]):
-            g, o = done[k]
-            assert W.sha256_of(o.cpu().numpy()) == fr["order_sha256"], f"request {k}: order"
-            assert W.sha256_of(g.cpu().numpy()) == fr["g_sha256"], f"request {k}: field"
+                        done[i] = r
+        for i, k in enumerate(order):
+            g, o = done[i]
+            fr = rec["fields"][k]
+            assert W.sha256_of(o.cpu().numpy()) == fr["order_sha256"], f"request {k} (#{i}): order"
+            assert W.sha256_of(g.cpu().numpy()) == fr["g_sha256"], f"request {k} (#{i}): field"
+    finally:
+        ctx.close()
+
+
+def test_serve_config_errors(lts):
+    ctx = lts.Context(1 << 16, device=0)
+    try:
+        for bad in ((-1, 1 << 30), (8, 1 << 30), (2, -5)):
+            with pytest.raises(lts.LtsError) as e:
+                ctx.serve_config(*bad)
+            assert e.value.code == 1
+        # a zero budget allocates no serving workspace: requests run on the context's own
+        ctx.serve_config(7, 0)
+        f = W.make_config_field(0, shape=(64, 48))
+        ids = oracle.authorized_by_persistence(f, 0.05)
+        fd, idd = to_dev(f, ids)
+        t = ctx.submit(fd, idd, "both")
+        r = None
+        while r is None:
+            r = ctx.poll(t)
+        check(r[0], r[1], f, ids, "zero budget")
     finally:
         ctx.close()
