@@ -179,13 +179,16 @@ lts_status lts_submit(lts_ctx* ctx, const lts_grid* g, const float* d_field, con
                       uint64_t* ticket);
 lts_status lts_poll(lts_ctx* ctx, uint64_t ticket, int* done);
 
-/* Serving limits: at most max_concurrent serving workspaces (0..7; 0 runs
+/* Serving limits: at most max_concurrent serving workspaces (0..15; 0 runs
  * every request on the context's own workspace and stream, in submission
  * order) and at most hbm_budget_bytes of device memory for them together
- * (each takes lts_workspace_bytes of the largest grid).  Defaults: 7
+ * (each takes lts_workspace_bytes of the largest grid).  Defaults: 15
  * workspaces, 120 GiB.  Workspaces already allocated are kept; the limits
- * apply to later allocations and to the choice of workspace.
- * Errors: LTS_ERR_ARG (max_concurrent outside [0, 7], negative budget). */
+ * apply to later allocations and to the choice of workspace.  The CUDA
+ * runtime maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8
+ * unless the process sets that variable before CUDA starts, at most 32);
+ * beyond that, workspaces share queues and their work partly serializes.
+ * Errors: LTS_ERR_ARG (max_concurrent outside [0, 15], negative budget). */
 lts_status lts_serve_config(lts_ctx* ctx, int32_t max_concurrent, int64_t hbm_budget_bytes);
 
 /* Message describing the last error on this context ("" if none). */

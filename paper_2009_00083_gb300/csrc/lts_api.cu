@@ -36,7 +36,7 @@ struct ReqResult {
 
 namespace {
 
-constexpr int kMaxLanes = 8;       // the context's own workspace and up to 7 more
+constexpr int kMaxLanes = 16;      // the context's own workspace and up to 15 more
 constexpr int kBatchLanes = 4;     // workspaces a batch spreads over
 constexpr int kRing = 1024;        // serving requests in flight per context
 
@@ -724,7 +724,7 @@ lts_status lts_serve_config(lts_ctx* c, int32_t max_concurrent, int64_t hbm_budg
     if (!c) return LTS_ERR_ARG;
     c->err.clear();
     if (max_concurrent < 0 || max_concurrent > kMaxLanes - 1 || hbm_budget_bytes < 0)
-        return fail(c, LTS_ERR_ARG, "max_concurrent must be in [0, 7] and the budget non-negative");
+        return fail(c, LTS_ERR_ARG, "max_concurrent must be in [0, 15] and the budget non-negative");
     c->serve_max = max_concurrent;
     c->serve_budget = hbm_budget_bytes;
     return LTS_OK;

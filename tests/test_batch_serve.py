@@ -169,12 +169,12 @@ def test_full_batch_workload_against_stored_oracle_hashes(lts):
         ctx.close()
 
 
-@pytest.mark.parametrize("concurrent", [0, 3, 7])
+@pytest.mark.parametrize("concurrent", [0, 3, 15])
 def test_served_pool_against_stored_oracle_hashes(lts, concurrent):
     """The first 16 served requests (3D cubes of side 32..256) through
     lts_submit / lts_poll, all queued at once, each twice (forwards, then
     backwards), on the context's own workspace one after another
-    (concurrent = 0) or spread over 3 or 7 serving workspaces running side by
+    (concurrent = 0) or spread over 3 or 15 serving workspaces running side by
     side: every result equals the oracle's stored one, alone or in the mix."""
     from tests.golden import store as mg
 
@@ -211,7 +211,7 @@ def test_served_pool_against_stored_oracle_hashes(lts, concurrent):
 def test_serve_config_errors(lts):
     ctx = lts.Context(1 << 16, device=0)
     try:
-        for bad in ((-1, 1 << 30), (8, 1 << 30), (2, -5)):
+        for bad in ((-1, 1 << 30), (16, 1 << 30), (2, -5)):
             with pytest.raises(lts.LtsError) as e:
                 ctx.serve_config(*bad)
             assert e.value.code == 1
