@@ -48,6 +48,7 @@ struct Lane {
     bool own_stream = false;
     cudaEvent_t ev[16];
     bool events = false;
+    bool aux = false;              // the workspace's auxiliary streams and their events exist
     void* allocs[64];
     int nallocs = 0;
     bool dirty = false;            // a CUDA error left the workspace in an unknown state
@@ -134,6 +135,14 @@ void lane_free(Lane& L) {
     if (L.events)
         for (auto& e : L.ev) cudaEventDestroy(e);
     L.events = false;
+    if (L.aux) {
+        for (int i = 0; i < 3; ++i) {
+            cudaStreamDestroy(L.w.aux[i]);
+            cudaEventDestroy(L.w.join_ev[i]);
+        }
+        cudaEventDestroy(L.w.fork_ev);
+    }
+    L.aux = false;
     if (L.own_stream && L.stream) cudaStreamDestroy(L.stream);
     L.stream = nullptr;
     L.own_stream = false;
@@ -191,6 +200,16 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     }
     for (auto& e : L.ev) cudaEventCreate(&e);
     L.events = true;
+    bool aux_ok = cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 3 && aux_ok; ++i)
+        aux_ok = cudaStreamCreateWithFlags(&w.aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&w.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!aux_ok) {
+        cudaGetLastError();
+        lane_free(L);
+        return LTS_ERR_CUDA;
+    }
+    L.aux = true;
     cudaStream_t s = L.stream;
     cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, s);
     cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)z.n, s);

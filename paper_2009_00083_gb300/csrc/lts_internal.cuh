@@ -164,6 +164,10 @@ struct Work {
     int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
     int* lo_adj; long long lo_adj_cap;   // local adjacency of the largest regions (bump pool)
     long long lo_cap;
+    // the local-order tiers run side by side: three more streams, forked from
+    // and joined back to the workspace's stream with events
+    cudaStream_t aux[3];
+    cudaEvent_t fork_ev, join_ev[3];
     // reorder
     RankBlk* rblk; int nblk; int nblk_cur;
     int* sad_att; int* cumA;

@@ -123,7 +123,7 @@ __device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsign
 // One digit pass.  FIRST: keys come from f and values are the indices.
 // LAST: instead of writing the sorted pairs, write O[value] = rank.
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(kThreads) onesweep_kernel(
+__global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     const float* __restrict__ f, const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
     unsigned* __restrict__ kout, unsigned* __restrict__ vout, unsigned* bin_cursor, int n, int shift,
     const unsigned* __restrict__ goff, unsigned long long* status, unsigned* tile_ctr, unsigned epoch, int* st) {

@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
 }
 
 template <int DIR, int NN, bool PERS>
-__global__ void __launch_bounds__(kThreads, 10) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
+__global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const int* __restrict__ O, PropArgs a) {
     constexpr int TS = TeamCfg<NN>::TS, E = TeamCfg<NN>::E;
     DevCounters* ctr = a.ctr;
     int* st = &ctr->status;
@@ -809,7 +809,7 @@ cudaError_t select_persistent(Work& w, const Geom& g, const int* O, const float*
     return launch_propagate<DIR, true>(w, g, O, F, eps, sms, s);
 }
 
-int propagate_lanes(int sms) { return sms * 10 * kThreads; }
+int propagate_lanes(int sms) { return sms * 8 * kThreads; }
 // pool slack: every warp may hold one partly used reservation of each pool
 long long propagate_log_slack(int lanes) { return (long long)(lanes / 32) * kLogChunk; }
 long long propagate_spill_slack(int lanes) { return (long long)(lanes / 32) * kSpillChunk; }
