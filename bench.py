@@ -51,7 +51,7 @@ BYTES_PER_VERTEX = {"order_field": 4 + 4 + 48 + 8, "classify": 8, "reorder": 16}
 # order-field kernels per vertex, from an ncu capture of the 256^3 case of the
 # same recipe, scaled by the vertex count (the 512^3 call is too large to
 # capture with all metrics); only the order-field stage has a capture.
-TRAFFIC_PER_VERTEX = {"order_field": 67.4}
+TRAFFIC_PER_VERTEX = {"order_field": 67.3}
 PATH_BYTES_PER_VERTEX = 100   # sort + classify + flatten, both passes
 
 

@@ -1019,19 +1019,25 @@ void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t
     // The tiers hold disjoint regions (each writes only its regions' local
     // orders and scratch slots, and reads the order of their members), so
     // they run side by side: each is latency-bound with a long tail.
-    cudaEventRecord(w.fork_ev, s);
-    for (int i = 0; i < 3; ++i) cudaStreamWaitEvent(w.aux[i], w.fork_ev, 0);
+    cudaStream_t s0 = s, s1 = s, s2 = s;
+    if (w.aux_on) {
+        cudaEventRecord(w.fork_ev, s);
+        for (int i = 0; i < 3; ++i) cudaStreamWaitEvent(w.aux[i], w.fork_ev, 0);
+        s0 = w.aux[0]; s1 = w.aux[1]; s2 = w.aux[2];
+    }
     lo_team_kernel<DIR, NN, 16><<<sms * 12, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t16);
-    lo_team_kernel<DIR, NN, 32><<<sms * 12, 128, 0, w.aux[2]>>>(g, a, tl, &w.ctr->n_t32);
-    lo_dense_kernel<DIR, NN, 128, 4><<<sms * 10, 128, small, w.aux[1]>>>(g, a, tl + q, &w.ctr->n_med);
-    lo_dense_kernel<DIR, NN, kMedR, 1><<<sms * 5, 32, large, w.aux[0]>>>(g, a, tl + 2 * q, &w.ctr->n_large);
-    lo_dense_kernel<DIR, NN, kHugeR, 1><<<sms, 32, huge, w.aux[0]>>>(g, a, tl + 3 * q, &w.ctr->n_huge);
+    lo_team_kernel<DIR, NN, 32><<<sms * 12, 128, 0, s2>>>(g, a, tl, &w.ctr->n_t32);
+    lo_dense_kernel<DIR, NN, 128, 4><<<sms * 10, 128, small, s1>>>(g, a, tl + q, &w.ctr->n_med);
+    lo_dense_kernel<DIR, NN, kMedR, 1><<<sms * 5, 32, large, s0>>>(g, a, tl + 2 * q, &w.ctr->n_large);
+    lo_dense_kernel<DIR, NN, kHugeR, 1><<<sms, 32, huge, s0>>>(g, a, tl + 3 * q, &w.ctr->n_huge);
     constexpr size_t heap_bytes = kWarpHeapCap * sizeof(unsigned long long);
     cudaFuncSetAttribute(lo_warp_kernel<DIR, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)heap_bytes);
-    lo_warp_kernel<DIR, NN><<<sms, 32, heap_bytes, w.aux[0]>>>(g, a, tl + 3 * q + q / 2, &w.ctr->n_big);
-    for (int i = 0; i < 3; ++i) {
-        cudaEventRecord(w.join_ev[i], w.aux[i]);
-        cudaStreamWaitEvent(s, w.join_ev[i], 0);
+    lo_warp_kernel<DIR, NN><<<sms, 32, heap_bytes, s0>>>(g, a, tl + 3 * q + q / 2, &w.ctr->n_big);
+    if (w.aux_on) {
+        for (int i = 0; i < 3; ++i) {
+            cudaEventRecord(w.join_ev[i], w.aux[i]);
+            cudaStreamWaitEvent(s, w.join_ev[i], 0);
+        }
     }
 }
 

@@ -151,7 +151,7 @@ void lane_free(Lane& L) {
 }
 
 // Allocates and initializes a workspace for grids of up to nmax vertices.
-lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, bool own_stream) {
+lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, bool own_stream, bool side_streams) {
     L.stream = stream;
     L.own_stream = own_stream;
     L.nmax = nmax;
@@ -200,16 +200,20 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     }
     for (auto& e : L.ev) cudaEventCreate(&e);
     L.events = true;
-    bool aux_ok = cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) == cudaSuccess;
-    for (int i = 0; i < 3 && aux_ok; ++i)
-        aux_ok = cudaStreamCreateWithFlags(&w.aux[i], cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&w.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
-    if (!aux_ok) {
-        cudaGetLastError();
-        lane_free(L);
-        return LTS_ERR_CUDA;
+    w.aux_on = false;
+    if (side_streams) {
+        bool aux_ok = cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 3 && aux_ok; ++i)
+            aux_ok = cudaStreamCreateWithFlags(&w.aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&w.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!aux_ok) {
+            cudaGetLastError();
+            lane_free(L);
+            return LTS_ERR_CUDA;
+        }
+        L.aux = true;
+        w.aux_on = true;
     }
-    L.aux = true;
     cudaStream_t s = L.stream;
     cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, s);
     cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)z.n, s);
@@ -520,7 +524,7 @@ int pick_serve_lane(lts_ctx* c, long long n) {
             if (L.stream) lane_free(L);
             cudaStream_t s;
             if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess) {
-                if (lane_alloc(L, nmax, c->sms, s, true) == LTS_OK) {
+                if (lane_alloc(L, nmax, c->sms, s, true, false) == LTS_OK) {
                     c->nlanes = std::max(c->nlanes, free_slot + 1);
                     return free_slot;
                 }
@@ -552,7 +556,7 @@ lts_status lts_create(lts_ctx** out, int device, int64_t max_vertices, void* cud
     lts_ctx* c = new lts_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
-    const lts_status st = lane_alloc(c->lane[0], max_vertices, c->sms, static_cast<cudaStream_t>(cuda_stream), false);
+    const lts_status st = lane_alloc(c->lane[0], max_vertices, c->sms, static_cast<cudaStream_t>(cuda_stream), false, true);
     if (st != LTS_OK) {
         delete c;
         return st;
@@ -669,7 +673,7 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
             cudaGetLastError();
             return fail(c, LTS_ERR_CUDA, "cannot create a stream");
         }
-        const lts_status st = lane_alloc(L, nbig, c->sms, s, true);
+        const lts_status st = lane_alloc(L, nbig, c->sms, s, true, false);
         if (st != LTS_OK) {
             cudaStreamDestroy(s);
             L.stream = nullptr;

@@ -165,7 +165,9 @@ struct Work {
     int* lo_adj; long long lo_adj_cap;   // local adjacency of the largest regions (bump pool)
     long long lo_cap;
     // the local-order tiers run side by side: three more streams, forked from
-    // and joined back to the workspace's stream with events
+    // and joined back to the workspace's stream with events (the context's own
+    // workspace only: batches and served requests overlap whole fields)
+    bool aux_on;
     cudaStream_t aux[3];
     cudaEvent_t fork_ev, join_ev[3];
     // reorder
