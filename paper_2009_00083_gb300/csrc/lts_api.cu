@@ -136,11 +136,11 @@ void lane_free(Lane& L) {
         for (auto& e : L.ev) cudaEventDestroy(e);
     L.events = false;
     if (L.aux) {
-        for (int i = 0; i < 3; ++i) {
-            cudaStreamDestroy(L.w.aux[i]);
-            cudaEventDestroy(L.w.join_ev[i]);
-        }
+        for (int i = 0; i < 4; ++i) cudaStreamDestroy(L.w.aux[i]);
+        for (int i = 0; i < 3; ++i) cudaEventDestroy(L.w.join_ev[i]);
         cudaEventDestroy(L.w.fork_ev);
+        cudaEventDestroy(L.w.pre_fork);
+        cudaEventDestroy(L.w.pre_join);
     }
     L.aux = false;
     if (L.own_stream && L.stream) cudaStreamDestroy(L.stream);
@@ -202,10 +202,12 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     L.events = true;
     w.aux_on = false;
     if (side_streams) {
-        bool aux_ok = cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) == cudaSuccess;
-        for (int i = 0; i < 3 && aux_ok; ++i)
+        bool aux_ok = cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&w.pre_fork, cudaEventDisableTiming) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&w.pre_join, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 4 && aux_ok; ++i)
             aux_ok = cudaStreamCreateWithFlags(&w.aux[i], cudaStreamNonBlocking) == cudaSuccess &&
-                     cudaEventCreateWithFlags(&w.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+                     (i == 3 || cudaEventCreateWithFlags(&w.join_ev[i], cudaEventDisableTiming) == cudaSuccess);
         if (!aux_ok) {
             cudaGetLastError();
             lane_free(L);
@@ -401,17 +403,35 @@ cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const
             }
             pass_reset(w, s);
         }
+        // The reorder's rank prefix needs the regions only: on the context's own
+        // workspace it runs on a side stream beside the local orders (its time
+        // is then inside the local-order stage).
+        auto prefix_fork = [&]() {
+            if (w.aux_on) {
+                cudaEventRecord(w.pre_fork, s);
+                cudaStreamWaitEvent(w.aux[3], w.pre_fork, 0);
+                reorder_prefix(w, g, sms, w.aux[3]);
+                cudaEventRecord(w.pre_join, w.aux[3]);
+            } else {
+                reorder_prefix(w, g, sms, s);
+            }
+        };
+        auto prefix_join = [&]() {
+            if (w.aux_on) cudaStreamWaitEvent(s, w.pre_join, 0);
+        };
         if (side == 0) {
             classify<-1>(w, g, O, s);               cudaEventRecord(L.ev[evi++], s);
             propagate<-1>(w, g, O, sms, s);         cudaEventRecord(L.ev[evi++], s);
             extract_regions<-1>(w, g, O, sms, s);   cudaEventRecord(L.ev[evi++], s);
-            local_orders<-1>(w, g, O, sms, s);      cudaEventRecord(L.ev[evi++], s);
+            prefix_fork();
+            local_orders<-1>(w, g, O, sms, s);      prefix_join(); cudaEventRecord(L.ev[evi++], s);
             reorder_flatten<-1>(w, g, O, gout, sms, s); cudaEventRecord(L.ev[evi++], s);
         } else {
             classify<1>(w, g, O, s);                cudaEventRecord(L.ev[evi++], s);
             propagate<1>(w, g, O, sms, s);          cudaEventRecord(L.ev[evi++], s);
             extract_regions<1>(w, g, O, sms, s);    cudaEventRecord(L.ev[evi++], s);
-            local_orders<1>(w, g, O, sms, s);       cudaEventRecord(L.ev[evi++], s);
+            prefix_fork();
+            local_orders<1>(w, g, O, sms, s);       prefix_join(); cudaEventRecord(L.ev[evi++], s);
             reorder_flatten<1>(w, g, O, gout, sms, s); cudaEventRecord(L.ev[evi++], s);
         }
         save_pass_kernel<<<1, 1, 0, s>>>(w.ctr, w.reg_start, w.pstats + side);

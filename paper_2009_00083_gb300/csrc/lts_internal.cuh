@@ -168,8 +168,8 @@ struct Work {
     // and joined back to the workspace's stream with events (the context's own
     // workspace only: batches and served requests overlap whole fields)
     bool aux_on;
-    cudaStream_t aux[3];
-    cudaEvent_t fork_ev, join_ev[3];
+    cudaStream_t aux[4];                 // [0..2] local-order tiers, [3] the reorder's rank prefix
+    cudaEvent_t fork_ev, join_ev[3], pre_fork, pre_join;
     // reorder
     RankBlk* rblk; int nblk; int nblk_cur;
     int* sad_att; int* cumA;
@@ -198,6 +198,7 @@ template <int DIR>
 cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
 template <int DIR>
 cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
+cudaError_t reorder_prefix(Work& w, const Geom& g, int sms, cudaStream_t s);
 template <int DIR>
 cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms, cudaStream_t s);
 cudaError_t pass_reset(Work& w, cudaStream_t s);

@@ -164,8 +164,10 @@ __global__ void saddles_reset_kernel(int* owner, int* cnt, const int* __restrict
 
 }  // namespace
 
-template <int DIR>
-cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms, cudaStream_t s) {
+// The rank prefix of step 3: member and saddle counts before every 32-rank
+// block, and the members attached to each saddle, summed over the saddles.
+// It needs the regions only, not their local orders.
+cudaError_t reorder_prefix(Work& w, const Geom& g, int sms, cudaStream_t s) {
     const int nb = w.nblk_cur;
     const int per_tile = kT * kPer;
     const int nt = (nb + per_tile - 1) / per_tile;
@@ -174,12 +176,18 @@ cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms
     blk_apply_kernel<<<nt, kT, 0, s>>>(w.rblk, nb, w.scan_tmp);
     saddle_index_kernel<<<sms * 8, 256, 0, s>>>(w.rblk, w.reg_head, w.reg_sod, w.reg_att, w.sad_att, w.ctr);
     scan_excl_i32(w, w.sad_att, w.cumA, &w.ctr->n_saddles, g.n / 2 + 1, s);
+    w.launches += 4;
+    return cudaGetLastError();
+}
+
+template <int DIR>
+cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms, cudaStream_t s) {
     stream_kernel<DIR><<<sms * 8, kT, 0, s>>>(g.n, O, w.rblk, w.cumA, w.ctr);
     members_place_kernel<DIR><<<sms * 8, 256, 0, s>>>(g.n, O, gout, w.owner, w.members, w.member_reg, w.lhat,
                                                       w.reg_saddle, w.reg_sod, w.reg_place, w.reg_start, w.rblk,
                                                       w.cumA, w.ctr);
     saddles_reset_kernel<<<sms * 4, 256, 0, s>>>(w.owner, w.cnt, w.reg_saddle, w.ctr);
-    w.launches += 7;
+    w.launches += 3;
     return cudaGetLastError();
 }
 
