@@ -103,6 +103,7 @@ size_t bytes_for(const Sizes& z) {
     size_t b = 0;
     b += 4 * 4 * (size_t)z.n;                       // sort key/value double buffers
     b += (size_t)z.tiles * 256 * 8 + 4096 * 3;      // look-back words, histograms
+    b += 3 * 4 * 8192 + 48;                         // distinct-key table
     b += ((size_t)z.n + 31) / 32 * 4;               // authorized bitmap
     b += 2 * 4 * (size_t)z.n + 8 * (size_t)z.n;     // owner, loc, qmark
     b += 10 * 4 * (size_t)z.half;                   // U and class records
@@ -168,7 +169,9 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     ok = ok && dev_alloc(L, &w.keyA, z.n) && dev_alloc(L, &w.valA, z.n) && dev_alloc(L, &w.keyB, z.n) &&
          dev_alloc(L, &w.valB, z.n);
     ok = ok && dev_alloc(L, &w.sort_status, (size_t)z.tiles * 256) && dev_alloc(L, &w.sort_hist, 1024) &&
-         dev_alloc(L, &w.sort_offsets, 1024) && dev_alloc(L, &w.tile_counter, 4) &&
+         dev_alloc(L, &w.sort_offsets, 1024) && dev_alloc(L, &w.tile_counter, 8) &&
+         dev_alloc(L, &w.dk_keys, 8192) && dev_alloc(L, &w.dk_cnts, 8192) && dev_alloc(L, &w.dk_rank, 8192) &&
+         dev_alloc(L, &w.dk_info, 4) &&
          dev_alloc(L, &w.bin_cursor, 1024);
     ok = ok && dev_alloc(L, &w.authbits, (z.n + 31) / 32);
     ok = ok && dev_alloc(L, &w.owner, z.n) && dev_alloc(L, &w.loc, z.n) && dev_alloc(L, &w.qmark, z.n);

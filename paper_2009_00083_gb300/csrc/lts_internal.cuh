@@ -137,6 +137,8 @@ struct Work {
     unsigned int* sort_offsets;          // 4 x 256
     unsigned int* tile_counter;          // 4
     unsigned int* bin_cursor;            // id bins of the last radix pass
+    unsigned int* dk_keys; unsigned int* dk_cnts; unsigned int* dk_rank;   // distinct keys (hash table)
+    unsigned int* dk_info;               // distinct count, overflow flag, two-pass mode
     unsigned int epoch;
     // authorized bitmap
     unsigned int* authbits;              // ceil(n/32)

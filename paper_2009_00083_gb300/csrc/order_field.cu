@@ -11,6 +11,17 @@
 // DRAM sector each): it appends the (id, rank) pairs to bins of 2^22 ids,
 // and an inverse pass then writes O bin by bin, so that the random writes of
 // one bin stay inside a 16 MB window of O that L2 merges into full sectors.
+//
+// Few distinct values (quantized fields; heavy ties): the histogram pass also
+// collects the distinct keys with their counts in a hash table (per block in
+// shared memory, then globally).  If there are at most kDkMax of them, one
+// small kernel replaces every key by its rank among the distinct keys (an
+// order-preserving compression to 12 bits) and derives the two digit
+// histograms of the compressed keys from the counts; the sort then takes two
+// digit passes instead of four (the first pass looks the compressed key up,
+// the second is the last).  Ties keep their id order: the passes are stable
+// whatever the keys.  The choice is made on the device: the passes of the
+// other path are launched too and return at once.
 #include <cstdio>
 #include <mutex>
 
@@ -26,6 +37,74 @@ constexpr int kTile = kThreads * kItems;   // 4096 keys
 constexpr int kWarps = kThreads / 32;
 constexpr int kBinShift = 22;
 constexpr int kMaxBins = 1 << (31 - kBinShift);
+constexpr int kDkMax = 4096;             // distinct keys for the two-pass sort (12-bit compressed keys)
+constexpr int kDkSlots = 2 * kDkMax;     // global hash table slots
+constexpr int kDkLocal = 1024;           // per-block hash table slots
+constexpr int kDkProbe = 64;             // local probes before a key goes to the global table
+constexpr unsigned kDkEmpty = 0xffffffffu;   // no order key has this value (it is a NaN pattern)
+
+// dk_info words
+constexpr int kDkCount = 0;              // distinct keys inserted in the global table
+constexpr int kDkOverflow = 1;           // more than kDkMax distinct keys (or a probe limit hit)
+constexpr int kDkMode = 2;               // 1: the compressed two-pass sort runs
+
+__device__ __forceinline__ unsigned dk_hash(unsigned k) { return (k * 0x9E3779B1u) >> 19; }   // 13 bits
+
+// Adds cnt occurrences of key to the global table (bounded probing).
+__device__ void dk_insert_global(unsigned* keys, unsigned* cnts, unsigned* info, unsigned key, unsigned cnt) {
+    unsigned h = dk_hash(key) & (kDkSlots - 1);
+    for (int p = 0; p < kDkSlots; ++p) {
+        if (*(volatile unsigned*)(info + kDkOverflow)) return;
+        unsigned cur = *(volatile unsigned*)(keys + h);
+        if (cur == kDkEmpty) {
+            if (*(volatile unsigned*)(info + kDkCount) >= (unsigned)kDkMax) {
+                atomicExch(info + kDkOverflow, 1u);
+                return;
+            }
+            cur = atomicCAS(keys + h, kDkEmpty, key);
+            if (cur == kDkEmpty) {
+                atomicAdd(cnts + h, cnt);
+                if (atomicAdd(info + kDkCount, 1u) + 1u > (unsigned)kDkMax) atomicExch(info + kDkOverflow, 1u);
+                return;
+            }
+        }
+        if (cur == key) {
+            atomicAdd(cnts + h, cnt);
+            return;
+        }
+        h = (h + 1) & (kDkSlots - 1);
+    }
+    atomicExch(info + kDkOverflow, 1u);
+}
+
+// Adds cnt occurrences of key to the block's table; false if it did not fit.
+__device__ bool dk_insert_local(unsigned* lk, unsigned* lc, unsigned key, unsigned cnt) {
+    unsigned h = dk_hash(key) & (kDkLocal - 1);
+    for (int p = 0; p < kDkProbe; ++p) {
+        unsigned cur = *(volatile unsigned*)(lk + h);
+        if (cur == kDkEmpty) cur = atomicCAS(lk + h, kDkEmpty, key);
+        if (cur == kDkEmpty || cur == key) {
+            atomicAdd(lc + h, cnt);
+            return true;
+        }
+        h = (h + 1) & (kDkLocal - 1);
+    }
+    return false;
+}
+
+// The compressed key of an order key present in the global table.
+__device__ __forceinline__ unsigned dk_lookup(const unsigned* __restrict__ keys, const unsigned* __restrict__ rank,
+                                              unsigned key, int* st) {
+    unsigned h = dk_hash(key) & (kDkSlots - 1);
+    for (int p = 0; p < kDkSlots; ++p) {
+        const unsigned cur = __ldg(keys + h);
+        if (cur == key) return __ldg(rank + h);
+        if (cur == kDkEmpty) break;
+        h = (h + 1) & (kDkSlots - 1);
+    }
+    set_status(st, LTS_ERR_INTERNAL);
+    return 0;
+}
 
 // IEEE order as unsigned order; -0.0 is folded onto +0.0.
 __device__ __forceinline__ unsigned order_key(float x, int* st) {
@@ -38,11 +117,25 @@ __device__ __forceinline__ unsigned order_key(float x, int* st) {
 // Histograms of the four digits; each thread walks 16 consecutive keys and
 // flushes a digit count only when the digit changes (runs of equal high
 // digits are common in smooth fields, so this avoids contended atomics).
+// With dk_keys set, also collects the distinct keys and their counts: runs
+// of equal keys within a thread's 16 are counted once, the block's table takes
+// them, and the table is added to the global one at the end.
 __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __restrict__ f, float* __restrict__ gout,
-                                                             int n, unsigned* __restrict__ hist, int* st) {
+                                                             int n, unsigned* __restrict__ hist, int* st,
+                                                             unsigned* dk_keys, unsigned* dk_cnts, unsigned* dk_info) {
     __shared__ unsigned sh[4][256];
+    __shared__ unsigned lk[kDkLocal], lc[kDkLocal];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&sh[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kDkLocal; i += blockDim.x) { lk[i] = kDkEmpty; lc[i] = 0; }
     __syncthreads();
+    unsigned run_key = kDkEmpty, run_cnt = 0;
+    auto dk_add = [&](unsigned k) {
+        if (k == run_key) { ++run_cnt; return; }
+        if (run_cnt && !dk_insert_local(lk, lc, run_key, run_cnt))
+            dk_insert_global(dk_keys, dk_cnts, dk_info, run_key, run_cnt);
+        run_key = k;
+        run_cnt = 1;
+    };
     const long long chunk = 16;
     const long long nchunks = (n + chunk - 1) / chunk;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nchunks;
@@ -51,6 +144,7 @@ __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __rest
         unsigned cur[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
         unsigned cc[4] = {0, 0, 0, 0};
         const bool vec = ((reinterpret_cast<unsigned long long>(f) | reinterpret_cast<unsigned long long>(gout)) & 15ull) == 0;
+        const bool dk = dk_keys != nullptr && !*(volatile unsigned*)(dk_info + kDkOverflow);
         if (vec && b + chunk <= n) {
             const float4* p = reinterpret_cast<const float4*>(f + b);
             float4* q = reinterpret_cast<float4*>(gout + b);
@@ -64,6 +158,7 @@ __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __rest
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 unsigned k = order_key(v[j], st);
+                if (dk) dk_add(k);
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {
                     unsigned dg = (k >> (8 * d)) & 255u;
@@ -75,10 +170,12 @@ __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __rest
                 }
             }
         } else {
-            for (long long i = b; i < n; ++i) {
+            const long long e = b + chunk < n ? b + chunk : (long long)n;
+            for (long long i = b; i < e; ++i) {
                 float x = f[i];
                 gout[i] = x;
                 unsigned k = order_key(x, st);
+                if (dk) dk_add(k);
                 for (int d = 0; d < 4; ++d) {
                     unsigned dg = (k >> (8 * d)) & 255u;
                     if (dg != cur[d]) {
@@ -93,11 +190,60 @@ __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __rest
         for (int d = 0; d < 4; ++d)
             if (cc[d]) atomicAdd(&sh[d][cur[d]], cc[d]);
     }
+    if (dk_keys) {
+        if (run_cnt && !dk_insert_local(lk, lc, run_key, run_cnt))
+            dk_insert_global(dk_keys, dk_cnts, dk_info, run_key, run_cnt);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
         unsigned v = (&sh[0][0])[i];
         if (v) atomicAdd(&hist[i], v);
     }
+    if (dk_keys)
+        for (int i = threadIdx.x; i < kDkLocal; i += blockDim.x)
+            if (lk[i] != kDkEmpty) dk_insert_global(dk_keys, dk_cnts, dk_info, lk[i], lc[i]);
+}
+
+// Ranks the distinct keys (if there are at most kDkMax) and replaces the
+// histograms of digits 0 and 1 by those of the compressed keys.  One block.
+__global__ void __launch_bounds__(1024) dense_keys_kernel(const unsigned* __restrict__ dk_keys,
+                                                          const unsigned* __restrict__ dk_cnts, unsigned* dk_rank,
+                                                          unsigned* dk_info, unsigned* hist, const int* st) {
+    __shared__ unsigned s_key[kDkMax];
+    __shared__ unsigned short s_slot[kDkMax];
+    __shared__ unsigned s_h[2][256];
+    __shared__ int s_n;
+    if (dk_info[kDkOverflow] || failed(st)) {
+        if (threadIdx.x == 0) dk_info[kDkMode] = 0;
+        return;
+    }
+    if (threadIdx.x == 0) s_n = 0;
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kDkSlots; i += blockDim.x) {
+        const unsigned k = dk_keys[i];
+        if (k == kDkEmpty) continue;
+        const int at = atomicAdd(&s_n, 1);
+        if (at < kDkMax) { s_key[at] = k; s_slot[at] = (unsigned short)i; }
+    }
+    __syncthreads();
+    const int D = s_n;
+    if (D > kDkMax) {                                // cannot happen without the overflow flag
+        if (threadIdx.x == 0) dk_info[kDkMode] = 0;
+        return;
+    }
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+        const unsigned k = s_key[i];
+        unsigned r = 0;
+        for (int j = 0; j < D; ++j) r += s_key[j] < k;
+        dk_rank[s_slot[i]] = r;
+        const unsigned c = dk_cnts[s_slot[i]];
+        atomicAdd(&s_h[0][r & 255u], c);
+        atomicAdd(&s_h[1][r >> 8], c);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) hist[i] = (&s_h[0][0])[i];
+    if (threadIdx.x == 0) dk_info[kDkMode] = 1;
 }
 
 // Exclusive prefix of each digit's histogram: global start of every bucket.
@@ -120,13 +266,19 @@ __device__ __forceinline__ unsigned long long pack_status(unsigned epoch, unsign
     return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | val;
 }
 
-// One digit pass.  FIRST: keys come from f and values are the indices.
-// LAST: instead of writing the sorted pairs, write O[value] = rank.
+// Which sort a pass belongs to (read from dk_info on the device).
+constexpr int kRoleAlways = 0, kRoleFourPass = 1, kRoleTwoPass = 2;
+
+// One digit pass.  FIRST: keys come from f (compressed when the two-pass
+// sort runs) and values are the indices.  LAST: instead of writing the sorted
+// pairs, write (id, rank) pairs binned by id for the inverse pass.  A pass
+// of the sort that does not run returns at once.
 template <bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     const float* __restrict__ f, const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
     unsigned* __restrict__ kout, unsigned* __restrict__ vout, unsigned* bin_cursor, int n, int shift,
-    const unsigned* __restrict__ goff, unsigned long long* status, unsigned* tile_ctr, unsigned epoch, int* st) {
+    const unsigned* __restrict__ goff, unsigned long long* status, unsigned* tile_ctr, unsigned epoch, int* st,
+    const unsigned* __restrict__ dk_keys, const unsigned* __restrict__ dk_rank, const unsigned* dk_info, int role) {
     __shared__ unsigned s_tile;
     __shared__ unsigned wh[kWarps][256];
     __shared__ unsigned s_gstart[256];
@@ -138,6 +290,8 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     __shared__ unsigned s_bstart[LAST ? kMaxBins : 1];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool two_pass = dk_info != nullptr && dk_info[kDkMode] == 1u;
+    if ((role == kRoleFourPass && two_pass) || (role == kRoleTwoPass && !two_pass)) return;
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
     for (int i = tid; i < kWarps * 256; i += kThreads) (&wh[0][0])[i] = 0;
     __syncthreads();
@@ -149,7 +303,11 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     for (int i = 0; i < kItems; ++i) {
         const long long idx = base + i * 32 + lane;
         if (idx < n) {
-            if (FIRST) { key[i] = order_key(__ldg(f + idx), st); val[i] = (unsigned)idx; }
+            if (FIRST) {
+                key[i] = order_key(__ldg(f + idx), st);
+                if (two_pass) key[i] = dk_lookup(dk_keys, dk_rank, key[i], st);
+                val[i] = (unsigned)idx;
+            }
             else { key[i] = __ldcs(kin + idx); val[i] = __ldcs(vin + idx); }
         } else {
             key[i] = 0xffffffffu; val[i] = 0xffffffffu;   // sorts last within the tile, never written
@@ -159,7 +317,22 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         const unsigned d = (key[i] >> shift) & 255u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit: in the first pass the keys come in vertex
+        // order, where a smooth field gives long runs of equal digits, and
+        // eight ballots beat the match instruction there (measured); later
+        // passes use the match instruction
+        unsigned peers;
+        if (FIRST) {
+            peers = 0xffffffffu;
+#pragma unroll
+            for (int bt = 0; bt < 8; ++bt) {
+                const bool on = (d >> bt) & 1u;
+                const unsigned bb = __ballot_sync(0xffffffffu, on);
+                peers &= on ? bb : ~bb;
+            }
+        } else {
+            peers = __match_any_sync(0xffffffffu, d);
+        }
         const int leader = __ffs(peers) - 1;
         unsigned b = 0;
         if (lane == leader) b = atomicAdd(&wh[warp][d], (unsigned)__popc(peers));
@@ -314,39 +487,51 @@ cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int
     const int tiles = (n + kTile - 1) / kTile;
     int* st = &w.ctr->status;
     cudaMemsetAsync(w.sort_hist, 0, 1024 * sizeof(unsigned), s);
-    cudaMemsetAsync(w.tile_counter, 0, 4 * sizeof(unsigned), s);
+    cudaMemsetAsync(w.tile_counter, 0, 8 * sizeof(unsigned), s);
+    cudaMemsetAsync(w.dk_keys, 0xff, kDkSlots * sizeof(unsigned), s);
+    cudaMemsetAsync(w.dk_cnts, 0, kDkSlots * sizeof(unsigned), s);
+    cudaMemsetAsync(w.dk_info, 0, 4 * sizeof(unsigned), s);
     {
         long long nch = (n + 15) / 16;
         int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, 152LL * 8);
-        hist_copy_kernel<<<blocks, kThreads, 0, s>>>(f, gout, n, w.sort_hist, st);
+        hist_copy_kernel<<<blocks, kThreads, 0, s>>>(f, gout, n, w.sort_hist, st, w.dk_keys, w.dk_cnts, w.dk_info);
     }
+    dense_keys_kernel<<<1, 1024, 0, s>>>(w.dk_keys, w.dk_cnts, w.dk_rank, w.dk_info, w.sort_hist, st);
     digit_offsets_kernel<<<4, 256, 0, s>>>(w.sort_hist, w.sort_offsets);
     const int nbins = (int)(((unsigned)n + (1u << kBinShift) - 1) >> kBinShift);
     bin_init_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(w.bin_cursor, nbins);
-    w.launches += 8;
+    w.launches += 10;
+    unsigned ep[4];
     for (int p = 0; p < 4; ++p) {
-        unsigned epoch = ++w.epoch;
+        ep[p] = ++w.epoch;
         if (w.epoch >= (1u << 30) - 8) {   // epoch wrap: clear the look-back words
             cudaMemsetAsync(w.sort_status, 0, (size_t)w.max_tiles * 256 * sizeof(unsigned long long), s);
             w.epoch = 1;
-            epoch = 1;
+            ep[p] = 1;
         }
-        const unsigned* goff = w.sort_offsets + 256 * p;
-        unsigned* tc = w.tile_counter + p;
-        if (p == 0)
-            onesweep_kernel<true, false><<<tiles, kThreads, 0, s>>>(f, nullptr, nullptr, w.keyA, w.valA, nullptr, n, 0,
-                                                                    goff, w.sort_status, tc, epoch, st);
-        else if (p == 1)
-            onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB, nullptr, n,
-                                                                     8, goff, w.sort_status, tc, epoch, st);
-        else if (p == 2)
-            onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyB, w.valB, w.keyA, w.valA, nullptr, n,
-                                                                     16, goff, w.sort_status, tc, epoch, st);
-        else
-            onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB,
-                                                                    w.bin_cursor, n, 24, goff, w.sort_status, tc,
-                                                                    epoch, st);
     }
+    const unsigned* dkk = w.dk_keys;
+    const unsigned* dkr = w.dk_rank;
+    const unsigned* dki = w.dk_info;
+    // digit 0 (both sorts); digit 1: middle pass of the four-pass sort, last
+    // pass of the two-pass sort (both write the binned pairs to B); digits 2, 3
+    onesweep_kernel<true, false><<<tiles, kThreads, 0, s>>>(f, nullptr, nullptr, w.keyA, w.valA, nullptr, n, 0,
+                                                            w.sort_offsets, w.sort_status, w.tile_counter + 0, ep[0],
+                                                            st, dkk, dkr, dki, kRoleAlways);
+    onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB, nullptr, n, 8,
+                                                             w.sort_offsets + 256, w.sort_status, w.tile_counter + 1,
+                                                             ep[1], st, dkk, dkr, dki, kRoleFourPass);
+    onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB, w.bin_cursor, n,
+                                                            8, w.sort_offsets + 256, w.sort_status,
+                                                            w.tile_counter + 4, ep[1], st, dkk, dkr, dki,
+                                                            kRoleTwoPass);
+    onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyB, w.valB, w.keyA, w.valA, nullptr, n, 16,
+                                                             w.sort_offsets + 512, w.sort_status, w.tile_counter + 2,
+                                                             ep[2], st, dkk, dkr, dki, kRoleFourPass);
+    onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB, w.bin_cursor, n,
+                                                            24, w.sort_offsets + 768, w.sort_status,
+                                                            w.tile_counter + 3, ep[3], st, dkk, dkr, dki,
+                                                            kRoleFourPass);
     inverse_kernel<<<152 * 8, 256, 0, s>>>(w.keyB, w.valB, O, n);
     return cudaGetLastError();
 }
@@ -477,20 +662,25 @@ extern "C" lts_status lts_order_field_static(int device, const lts_grid* gr, con
     {
         const long long nch = (n + 15) / 16;
         const int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, 152LL * 8);
-        hist_copy_kernel<<<blocks, kThreads, 0, s>>>(d_field, reinterpret_cast<float*>(keyB), ni, hist, st);
+        hist_copy_kernel<<<blocks, kThreads, 0, s>>>(d_field, reinterpret_cast<float*>(keyB), ni, hist, st, nullptr,
+                                                     nullptr, nullptr);
     }
     digit_offsets_kernel<<<4, 256, 0, s>>>(hist, goff);
     const int nbins = (int)(((unsigned)ni + (1u << kBinShift) - 1) >> kBinShift);
     bin_init_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(bins, nbins);
     // the look-back words were zeroed above, so the passes take epochs 1..4
     onesweep_kernel<true, false><<<tiles, kThreads, 0, s>>>(d_field, nullptr, nullptr, keyA, valA, nullptr, ni, 0,
-                                                            goff, look, ticket, 1u, st);
+                                                            goff, look, ticket, 1u, st, nullptr, nullptr, nullptr,
+                                                            kRoleAlways);
     onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, keyA, valA, keyB, valB, nullptr, ni, 8,
-                                                             goff + 256, look, ticket + 1, 2u, st);
+                                                             goff + 256, look, ticket + 1, 2u, st, nullptr, nullptr,
+                                                             nullptr, kRoleAlways);
     onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, keyB, valB, keyA, valA, nullptr, ni, 16,
-                                                             goff + 512, look, ticket + 2, 3u, st);
+                                                             goff + 512, look, ticket + 2, 3u, st, nullptr, nullptr,
+                                                             nullptr, kRoleAlways);
     onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, keyA, valA, keyB, valB, bins, ni, 24,
-                                                            goff + 768, look, ticket + 3, 4u, st);
+                                                            goff + 768, look, ticket + 3, 4u, st, nullptr, nullptr,
+                                                            nullptr, kRoleAlways);
     inverse_kernel<<<152 * 8, 256, 0, s>>>(keyB, valB, d_order, ni);
     cudaError_t e = cudaGetLastError();
     int h_status = 0;

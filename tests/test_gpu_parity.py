@@ -194,3 +194,55 @@ def test_errors(lts, ctx_small):
     g_ref, o_ref = oracle.lts(f, ids, mode="both")
     g, o, _ = run_gpu(ctx_small, f, ids)
     assert_same(g, o, g_ref, o_ref, "after errors")
+
+
+# ---------------------------------------------------------------------------
+# the order field's two sorts (few distinct values: two digit passes on
+# compressed keys; otherwise four) and pointers that are not 16-byte aligned
+# ---------------------------------------------------------------------------
+
+def order_by_simplify(lts, ctx, f):
+    """lts_simplify with every vertex authorized returns (f, order field of f)."""
+    dev = torch.device("cuda", 0)
+    g, o, st = ctx.simplify(torch.from_numpy(np.ascontiguousarray(f)).to(dev),
+                            torch.arange(f.size, dtype=torch.int32, device=dev), "both")
+    torch.cuda.synchronize()
+    assert st["removed"] == [0, 0]
+    return o.cpu().numpy()
+
+
+@pytest.mark.parametrize("distinct", [1, 2, 255, 256, 4095, 4096, 4097, 9000])
+def test_order_field_around_the_distinct_key_threshold(lts, ctx_small, distinct):
+    rng = np.random.default_rng(1000 + distinct)
+    shape = (96, 150)                       # 14,400 vertices, several tiles and a ragged tail
+    vals = np.arange(shape[0] * shape[1]) % distinct
+    vals = rng.permutation(vals).astype(np.float32) * np.float32(0.37) - np.float32(700.0)
+    f = vals.reshape(shape)
+    if distinct in (255, 9000):
+        f.reshape(-1)[:3] = [-0.0, 0.0, np.inf]   # -0 == +0 (one key), infinities are keys too
+    o = order_by_simplify(lts, ctx_small, f)
+    assert np.array_equal(o, oracle.order_field(f))
+
+
+def test_unaligned_input_and_output_pointers(lts, ctx_small):
+    """Views one float into larger buffers: the histogram pass takes its
+    scalar path for every chunk."""
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(31)
+    for shape, levels in [((61, 77), 9), ((13, 17, 19), None)]:
+        f = W.random_tiny_field(rng, shape, levels)
+        ids = random_ids(rng, f, 0.1)
+        g_ref, o_ref = oracle.lts(f, ids, mode="both")
+        n = f.size
+        fb = torch.zeros(n + 1, dtype=torch.float32, device=dev)
+        fb[1:] = torch.from_numpy(f.reshape(-1)).to(dev)
+        gb = torch.empty(n + 1, dtype=torch.float32, device=dev)
+        ob = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        fv, gv, ov = fb[1:].view(shape), gb[1:].view(shape), ob[1:].view(shape)
+        assert fv.data_ptr() % 16 != 0 and gv.data_ptr() % 16 != 0
+        idd = torch.from_numpy(ids).to(dev)
+        code = lts.lts_simplify(ctx_small._ctx, lts.grid_of_shape(shape), fv.data_ptr(), idd.data_ptr(), idd.numel(),
+                                "both", gv.data_ptr(), ov.data_ptr())
+        assert code == 0, lts.lts_last_error(ctx_small._ctx)
+        torch.cuda.synchronize()
+        assert_same(gv.cpu().numpy(), ov.cpu().numpy(), g_ref, o_ref, f"unaligned {shape}")
