@@ -560,7 +560,9 @@ def main():
                    "authorized": int(ids.size), "mode": "both", "l2": "inputs (512 MB) larger than L2",
                    "parallelism": f"replicas x{world}"},
         "parity_vs_oracle": bool(parity),
-        "roofline": {"bound": "hbm", "kernel": dom + (" (histogram/copy, 4 onesweep passes, inverse)"
+        "roofline": {"bound": "hbm", "kernel": dom + (" (histogram/copy with distinct-key count, onesweep digit "
+                                                      "passes: two on compressed keys for this quantized field, "
+                                                      "four otherwise; inverse)"
                                                       if dom == "order_field" else ""),
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),

@@ -40,7 +40,7 @@ constexpr int kMaxBins = 1 << (31 - kBinShift);
 constexpr int kDkMax = 4096;             // distinct keys for the two-pass sort (12-bit compressed keys)
 constexpr int kDkSlots = 2 * kDkMax;     // global hash table slots
 constexpr int kDkLocal = 1024;           // per-block hash table slots
-constexpr int kDkProbe = 64;             // local probes before a key goes to the global table
+constexpr int kDkProbe = 8;              // local probes before a key goes to the global table
 constexpr unsigned kDkEmpty = 0xffffffffu;   // no order key has this value (it is a NaN pattern)
 
 // dk_info words
@@ -51,40 +51,63 @@ constexpr int kDkMode = 2;               // 1: the compressed two-pass sort runs
 __device__ __forceinline__ unsigned dk_hash(unsigned k) { return (k * 0x9E3779B1u) >> 19; }   // 13 bits
 
 // Adds cnt occurrences of key to the global table (bounded probing).
-__device__ void dk_insert_global(unsigned* keys, unsigned* cnts, unsigned* info, unsigned key, unsigned cnt) {
+// Returns false once there are too many distinct keys: collecting stops.
+__device__ bool dk_insert_global(unsigned* keys, unsigned* cnts, unsigned* info, unsigned key, unsigned cnt) {
     unsigned h = dk_hash(key) & (kDkSlots - 1);
     for (int p = 0; p < kDkSlots; ++p) {
-        if (*(volatile unsigned*)(info + kDkOverflow)) return;
+        if (*(volatile unsigned*)(info + kDkOverflow)) return false;
         unsigned cur = *(volatile unsigned*)(keys + h);
         if (cur == kDkEmpty) {
             if (*(volatile unsigned*)(info + kDkCount) >= (unsigned)kDkMax) {
                 atomicExch(info + kDkOverflow, 1u);
-                return;
+                return false;
             }
             cur = atomicCAS(keys + h, kDkEmpty, key);
             if (cur == kDkEmpty) {
                 atomicAdd(cnts + h, cnt);
-                if (atomicAdd(info + kDkCount, 1u) + 1u > (unsigned)kDkMax) atomicExch(info + kDkOverflow, 1u);
-                return;
+                if (atomicAdd(info + kDkCount, 1u) + 1u > (unsigned)kDkMax) {
+                    atomicExch(info + kDkOverflow, 1u);
+                    return false;
+                }
+                return true;
             }
         }
         if (cur == key) {
             atomicAdd(cnts + h, cnt);
-            return;
+            return true;
         }
         h = (h + 1) & (kDkSlots - 1);
     }
     atomicExch(info + kDkOverflow, 1u);
+    return false;
 }
 
-// Adds cnt occurrences of key to the block's table; false if it did not fit.
-__device__ bool dk_insert_local(unsigned* lk, unsigned* lc, unsigned key, unsigned cnt) {
+// Adds cnt occurrences of key to the block's table; false if it did not fit
+// in kDkProbe probes.  At three quarters full the table takes no new keys
+// (*full), so that a block with many distinct keys does not probe a full one.
+__device__ bool dk_insert_local(unsigned* lk, unsigned* lc, int* count, int* full, unsigned key, unsigned cnt) {
+    if (*(volatile int*)full) {
+        // only keys already present
+        unsigned h = dk_hash(key) & (kDkLocal - 1);
+        for (int p = 0; p < kDkProbe; ++p) {
+            const unsigned cur = *(volatile unsigned*)(lk + h);
+            if (cur == key) { atomicAdd(lc + h, cnt); return true; }
+            if (cur == kDkEmpty) return false;
+            h = (h + 1) & (kDkLocal - 1);
+        }
+        return false;
+    }
     unsigned h = dk_hash(key) & (kDkLocal - 1);
     for (int p = 0; p < kDkProbe; ++p) {
         unsigned cur = *(volatile unsigned*)(lk + h);
-        if (cur == kDkEmpty) cur = atomicCAS(lk + h, kDkEmpty, key);
-        if (cur == kDkEmpty || cur == key) {
+        bool mine = false;
+        if (cur == kDkEmpty) {
+            cur = atomicCAS(lk + h, kDkEmpty, key);
+            mine = cur == kDkEmpty;
+        }
+        if (mine || cur == key) {
             atomicAdd(lc + h, cnt);
+            if (mine && atomicAdd(count, 1) + 1 >= kDkLocal * 3 / 4) *(volatile int*)full = 1;
             return true;
         }
         h = (h + 1) & (kDkLocal - 1);
@@ -125,14 +148,22 @@ __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __rest
                                                              unsigned* dk_keys, unsigned* dk_cnts, unsigned* dk_info) {
     __shared__ unsigned sh[4][256];
     __shared__ unsigned lk[kDkLocal], lc[kDkLocal];
+    __shared__ int s_lcount, s_lfull;
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&sh[0][0])[i] = 0;
     for (int i = threadIdx.x; i < kDkLocal; i += blockDim.x) { lk[i] = kDkEmpty; lc[i] = 0; }
+    if (threadIdx.x == 0) { s_lcount = 0; s_lfull = 0; }
     __syncthreads();
     unsigned run_key = kDkEmpty, run_cnt = 0;
+    bool dk_on = dk_keys != nullptr;       // this thread still collects
+    auto dk_flush = [&]() {
+        if (run_cnt && !dk_insert_local(lk, lc, &s_lcount, &s_lfull, run_key, run_cnt) &&
+            !dk_insert_global(dk_keys, dk_cnts, dk_info, run_key, run_cnt))
+            dk_on = false;
+        run_cnt = 0;
+    };
     auto dk_add = [&](unsigned k) {
         if (k == run_key) { ++run_cnt; return; }
-        if (run_cnt && !dk_insert_local(lk, lc, run_key, run_cnt))
-            dk_insert_global(dk_keys, dk_cnts, dk_info, run_key, run_cnt);
+        dk_flush();
         run_key = k;
         run_cnt = 1;
     };
@@ -144,7 +175,8 @@ __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __rest
         unsigned cur[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
         unsigned cc[4] = {0, 0, 0, 0};
         const bool vec = ((reinterpret_cast<unsigned long long>(f) | reinterpret_cast<unsigned long long>(gout)) & 15ull) == 0;
-        const bool dk = dk_keys != nullptr && !*(volatile unsigned*)(dk_info + kDkOverflow);
+        if (dk_on && *(volatile unsigned*)(dk_info + kDkOverflow)) dk_on = false;
+        const bool dk = dk_on;
         if (vec && b + chunk <= n) {
             const float4* p = reinterpret_cast<const float4*>(f + b);
             float4* q = reinterpret_cast<float4*>(gout + b);
@@ -190,18 +222,15 @@ __global__ void __launch_bounds__(kThreads) hist_copy_kernel(const float* __rest
         for (int d = 0; d < 4; ++d)
             if (cc[d]) atomicAdd(&sh[d][cur[d]], cc[d]);
     }
-    if (dk_keys) {
-        if (run_cnt && !dk_insert_local(lk, lc, run_key, run_cnt))
-            dk_insert_global(dk_keys, dk_cnts, dk_info, run_key, run_cnt);
-    }
+    if (dk_on) dk_flush();
     __syncthreads();
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
         unsigned v = (&sh[0][0])[i];
         if (v) atomicAdd(&hist[i], v);
     }
-    if (dk_keys)
+    if (dk_keys && !*(volatile unsigned*)(dk_info + kDkOverflow))
         for (int i = threadIdx.x; i < kDkLocal; i += blockDim.x)
-            if (lk[i] != kDkEmpty) dk_insert_global(dk_keys, dk_cnts, dk_info, lk[i], lc[i]);
+            if (lk[i] != kDkEmpty && !dk_insert_global(dk_keys, dk_cnts, dk_info, lk[i], lc[i])) break;
 }
 
 // Ranks the distinct keys (if there are at most kDkMax) and replaces the
