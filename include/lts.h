@@ -76,7 +76,10 @@ typedef struct {
     int64_t heap_spills[2];      /* floods whose priority queue left shared memory  */
     float stage_us[8];           /* device time per stage: order field, classify,   */
                                  /* propagation, regions, local order, reorder      */
-                                 /* (summed over passes); [6] total; [7] unused     */
+                                 /* (summed over passes); [6] total; [7] unused.    */
+                                 /* Local order includes the reorder's rank prefix, */
+                                 /* which runs beside it; persistence-driven calls  */
+                                 /* count the selection in classify.                */
     int64_t kernel_launches;     /* CUDA kernels this call launched                 */
 } lts_stats;
 

@@ -2,8 +2,9 @@
 //
 // Onesweep LSD radix sort of 32-bit order-preserving keys with the vertex id
 // as value: one histogram pass over f (which also copies f into the output
-// field g), then four 8-bit digit passes.  Each pass takes tiles in launch
-// order from an atomic counter, ranks its keys with warp match-any groups,
+// field g), then four 8-bit digit passes (two on compressed keys, below).
+// Each pass takes tiles in launch order from an atomic counter, ranks its keys
+// with warp match-any groups (ballots in the first pass),
 // finds its global digit offsets by decoupled look-back over the tiles before
 // it (bounded spins), and scatters through shared memory so that every digit
 // run is written contiguously.  The last pass does not scatter O[id] = rank
