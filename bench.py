@@ -422,21 +422,14 @@ def sweep_leg(lts, torch, dev, side=256, points=(0, 10, 20, 30, 40, 50, 60, 70, 
     stream, median of `reps` calls after one warm-up."""
     f = W.uniform_noise_field((side, side, side), W.seed_of(5))
     n = f.size
-    flat = f.reshape(-1)
-    keep = [int(np.flatnonzero(flat == flat.min()).min()), int(np.flatnonzero(flat == flat.max()).max())]
-    rng = np.random.Generator(np.random.PCG64(W.seed_of(5, 1)))
-    perm = rng.permutation(n).astype(np.int32)
-    perm = perm[~np.isin(perm, keep)]
+    lists = W.sweep_authorized(f, points, W.seed_of(5, 1))
     ctx = lts.Context(n, device=dev.index)
     fd = torch.from_numpy(f).to(dev)
     g = torch.empty_like(fd)
     o = torch.empty(fd.shape, dtype=torch.int32, device=dev)
     rows = []
     try:
-        for p in points:
-            drop = int(round(p / 100.0 * n))
-            ids = np.sort(perm[drop:]) if drop < perm.size else np.zeros(0, np.int32)
-            ids = np.concatenate([ids, np.array(keep, np.int32)]).astype(np.int32)
+        for p, ids in zip(points, lists):
             idd = torch.from_numpy(ids).to(dev)
             _, _, st = ctx.simplify(fd, idd, "both", out_field=g, out_order=o)
             times = []

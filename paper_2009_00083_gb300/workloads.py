@@ -122,6 +122,27 @@ def uniform_noise_field(shape, seed):
     return rng.random(int(np.prod(shape)), dtype=np.float32).reshape(shape)
 
 
+def sweep_authorized(f, removed_pcts, seed):
+    """Authorized lists of the output-sensitivity sweep, one per share in
+    removed_pcts: every vertex except a random share of them (a prefix of one
+    seeded permutation, so larger shares remove supersets), never the global
+    minimum or maximum under (value, id) order; ids ascending, int32."""
+    flat = np.asarray(f).reshape(-1)
+    n = flat.size
+    keep = np.array([int(np.flatnonzero(flat == flat.min()).min()), int(np.flatnonzero(flat == flat.max()).max())])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    perm = rng.permutation(n)
+    perm = perm[(perm != keep[0]) & (perm != keep[1])]
+    out = []
+    for p in removed_pcts:
+        drop = min(int(round(p / 100.0 * n)), perm.size)
+        mask = np.ones(n, dtype=bool)
+        mask[perm[:drop]] = False
+        mask[keep] = True
+        out.append(np.flatnonzero(mask).astype(np.int32))
+    return out
+
+
 def make_config_field(config: int, k: int = 0, shape=None):
     """The field of a numbered configuration (optionally at another shape)."""
     c = CONFIGS[config]
