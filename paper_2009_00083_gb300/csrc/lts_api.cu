@@ -152,6 +152,7 @@ void lane_free(Lane& L) {
 }
 
 // Allocates and initializes a workspace for grids of up to nmax vertices.
+// On failure the lane is freed again, including `stream` if own_stream.
 lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, bool own_stream, bool side_streams) {
     L.stream = stream;
     L.own_stream = own_stream;
@@ -551,8 +552,7 @@ int pick_serve_lane(lts_ctx* c, long long n) {
                     c->nlanes = std::max(c->nlanes, free_slot + 1);
                     return free_slot;
                 }
-                cudaStreamDestroy(s);
-                L.stream = nullptr;
+                // a failed lane_alloc has already freed the lane and destroyed the stream it owned
             }
         }
         cudaGetLastError();
@@ -697,11 +697,8 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
             return fail(c, LTS_ERR_CUDA, "cannot create a stream");
         }
         const lts_status st = lane_alloc(L, nbig, c->sms, s, true, false);
-        if (st != LTS_OK) {
-            cudaStreamDestroy(s);
-            L.stream = nullptr;
+        if (st != LTS_OK)   // lane_alloc has already freed the lane and destroyed the stream it owned
             return fail(c, st, "cannot allocate a batch workspace");
-        }
     }
     c->nlanes = std::max(c->nlanes, want);
     if (!c->fork) {
