@@ -48,7 +48,6 @@ struct Lane {
     bool own_stream = false;
     cudaEvent_t ev[16];
     bool events = false;
-    bool aux = false;              // the workspace's auxiliary streams and their events exist
     void* allocs[64];
     int nallocs = 0;
     bool dirty = false;            // a CUDA error left the workspace in an unknown state
@@ -121,6 +120,7 @@ size_t bytes_for(const Sizes& z) {
 
 template <typename T>
 bool dev_alloc(Lane& L, T** p, size_t count) {
+    if (L.nallocs >= (int)(sizeof L.allocs / sizeof L.allocs[0])) return false;
     void* q = nullptr;
     if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return false;
     L.allocs[L.nallocs++] = q;
@@ -136,14 +136,14 @@ void lane_free(Lane& L) {
     if (L.events)
         for (auto& e : L.ev) cudaEventDestroy(e);
     L.events = false;
-    if (L.aux) {
-        for (int i = 0; i < 4; ++i) cudaStreamDestroy(L.w.aux[i]);
-        for (int i = 0; i < 3; ++i) cudaEventDestroy(L.w.join_ev[i]);
-        cudaEventDestroy(L.w.fork_ev);
-        cudaEventDestroy(L.w.pre_fork);
-        cudaEventDestroy(L.w.pre_join);
-    }
-    L.aux = false;
+    // side streams and their events (null unless created; Work{} zeroes them)
+    for (int i = 0; i < 4; ++i)
+        if (L.w.aux[i]) cudaStreamDestroy(L.w.aux[i]);
+    for (int i = 0; i < 3; ++i)
+        if (L.w.join_ev[i]) cudaEventDestroy(L.w.join_ev[i]);
+    if (L.w.fork_ev) cudaEventDestroy(L.w.fork_ev);
+    if (L.w.pre_fork) cudaEventDestroy(L.w.pre_fork);
+    if (L.w.pre_join) cudaEventDestroy(L.w.pre_join);
     if (L.own_stream && L.stream) cudaStreamDestroy(L.stream);
     L.stream = nullptr;
     L.own_stream = false;
@@ -206,18 +206,24 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     L.events = true;
     w.aux_on = false;
     if (side_streams) {
-        bool aux_ok = cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) == cudaSuccess &&
-                      cudaEventCreateWithFlags(&w.pre_fork, cudaEventDisableTiming) == cudaSuccess &&
-                      cudaEventCreateWithFlags(&w.pre_join, cudaEventDisableTiming) == cudaSuccess;
-        for (int i = 0; i < 4 && aux_ok; ++i)
-            aux_ok = cudaStreamCreateWithFlags(&w.aux[i], cudaStreamNonBlocking) == cudaSuccess &&
-                     (i == 3 || cudaEventCreateWithFlags(&w.join_ev[i], cudaEventDisableTiming) == cudaSuccess);
+        // a handle whose creation failed is left null, so lane_free skips it
+        auto mk_event = [](cudaEvent_t* e) {
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess) return true;
+            *e = nullptr;
+            return false;
+        };
+        auto mk_stream = [](cudaStream_t* st) {
+            if (cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) == cudaSuccess) return true;
+            *st = nullptr;
+            return false;
+        };
+        bool aux_ok = mk_event(&w.fork_ev) && mk_event(&w.pre_fork) && mk_event(&w.pre_join);
+        for (int i = 0; i < 4 && aux_ok; ++i) aux_ok = mk_stream(&w.aux[i]) && (i == 3 || mk_event(&w.join_ev[i]));
         if (!aux_ok) {
             cudaGetLastError();
             lane_free(L);
             return LTS_ERR_CUDA;
         }
-        L.aux = true;
         w.aux_on = true;
     }
     cudaStream_t s = L.stream;
