@@ -30,9 +30,9 @@ CONFIGS = {
     1: dict(name="gauss3d_128", shape=(128, 128, 128), K=64, noise=0.02, thr=0.01, kind="gauss"),
     2: dict(name="boxnoise3d_512", shape=(512, 512, 512), radius=2, levels=1024, thr=0.10, kind="box"),
     # many fields at once: even k a 2D square of side exp(U[ln 64, ln 1024]), odd k a 3D cube of side
-    # exp(U[ln 32, ln 160]); the generator of config 0; threshold U[1%, 10%] per field
+    # exp(U[ln 32, ln 160]); the Gaussian-sum generator of gauss2d_256; threshold U[1%, 10%] per field
     3: dict(name="mixed_batch_256", count=256, K=16, noise=0.05, kind="batch"),
-    # served requests: 3D cubes of side exp(U[ln 32, ln 256]); the generator of config 1; threshold
+    # served requests: 3D cubes of side exp(U[ln 32, ln 256]); the Gaussian-sum generator of gauss3d_128; threshold
     # U[0.5%, 10%] per request; Poisson arrivals at 200/s
     4: dict(name="serve_3d", K=64, noise=0.02, rate_hz=200.0, kind="serve"),
 }
@@ -179,7 +179,7 @@ def log_uniform_int(rng, lo, hi):
 
 def batch_specs(count=256):
     """Shapes, thresholds and seeds of the fields of the batch workload
-    (config 3), drawn in field order from their own generator."""
+    (mixed_batch_256), drawn in field order from their own generator."""
     rng = np.random.Generator(np.random.PCG64(seed_of(3, 999)))
     specs = []
     for k in range(count):
@@ -199,7 +199,7 @@ def batch_field(spec):
 
 
 def serve_specs(count):
-    """Shapes, thresholds and seeds of served requests (config 4)."""
+    """Shapes, thresholds and seeds of served requests (serve_3d)."""
     rng = np.random.Generator(np.random.PCG64(seed_of(4, 999)))
     specs = []
     for k in range(count):

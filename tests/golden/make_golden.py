@@ -7,8 +7,8 @@ extrema always kept), and the SHA-256 of the oracle's simplified field g and
 order field (mode both: minima pass, then maxima pass) with its statistics.
 
     python tests/golden/make_golden.py boxnoise3d_512
-    python tests/golden/make_golden.py mixed_batch_256    # config 3, 256 fields
-    python tests/golden/make_golden.py serve_pool_16      # config 4, the first 16 requests
+    python tests/golden/make_golden.py mixed_batch_256    # the mixed batch, 256 fields
+    python tests/golden/make_golden.py serve_pool_16      # served requests, the first 16
     python tests/golden/make_golden.py pers boxnoise3d_512   # persistence-driven (Sec. 4.5)
 
 The persistence-driven records ({name}_pers.json) hold, for eps = thr * range
