@@ -426,3 +426,25 @@ def test_lts_rejects_bad_arguments():
         oracle.lts(f, np.array([99], np.int32))
     with pytest.raises(oracle.OracleError):
         oracle.lts(np.zeros((1, 4), np.float32), np.array([0], np.int32))
+
+
+# --------------------------------------------------------------------------
+# Statistics the paper publishes for its experiments (Sec. 5): weak checks
+# --------------------------------------------------------------------------
+
+def test_published_statistics_ranges():
+    """Step 2 needs one propagation for nearly every region and at most 6;
+    a realistic level (1% of the range) processes a small share of a smooth
+    3D field; an aggressive level processes up to ~70%."""
+    f = W.make_config_field(1)                                   # 128^3 Gaussian sum + noise
+    g, O, st = oracle.lts(f, oracle.authorized_by_persistence(f, 0.01), "both", return_stats=True)
+    regions = st["regions_min"] + st["regions_max"]
+    processed = (st["region_vertices_min"] + st["region_vertices_max"]) / f.size
+    assert processed < 0.05
+    assert max(st["max_local_floods_min"], st["max_local_floods_max"]) <= 6
+    assert (st["total_local_floods_min"] + st["total_local_floods_max"]) / regions < 1.05
+    f2 = W.make_config_field(0)                                  # 256^2, noisier
+    g2, O2, st2 = oracle.lts(f2, oracle.authorized_by_persistence(f2, 0.05), "both", return_stats=True)
+    processed2 = (st2["region_vertices_min"] + st2["region_vertices_max"]) / f2.size
+    assert 0.05 < processed2 < 0.75
+    assert max(st2["max_local_floods_min"], st2["max_local_floods_max"]) <= 6
