@@ -448,3 +448,28 @@ def test_published_statistics_ranges():
     processed2 = (st2["region_vertices_min"] + st2["region_vertices_max"]) / f2.size
     assert 0.05 < processed2 < 0.75
     assert max(st2["max_local_floods_min"], st2["max_local_floods_max"]) <= 6
+
+
+def test_region_error_bound_and_flat_value():
+    """A maxima pass moves each region's members to the saddle's value, so
+    |f - g| <= f(top) - f(saddle) on the region (Sec. 4.2 step 4) and g = f
+    elsewhere; the regions come from step 1 on the same input."""
+    rng = np.random.default_rng(91)
+    for it in range(30):
+        dim3 = it % 2 == 1
+        shape = tuple(int(rng.integers(3, 7 if dim3 else 14)) for _ in range(3 if dim3 else 2))
+        f = W.random_tiny_field(rng, shape, levels=None if it % 3 else 6)
+        O = oracle.order_field(f)
+        ids = np.nonzero(rng.random(f.size) < 0.15)[0]
+        ids = np.concatenate([ids, [np.argmax(O.reshape(-1))]]).astype(np.int32)
+        auth = np.zeros(f.size, np.uint8)
+        auth[ids] = 1
+        region_of, sad, top = oracle.regions(O, auth)
+        g, Og, _ = oracle.one_pass(f, O, ids, +1)
+        fo, go, ro = f.reshape(-1).astype(np.float64), g.reshape(-1).astype(np.float64), region_of.reshape(-1)
+        assert np.array_equal(go[ro < 0], fo[ro < 0])
+        for r in range(len(sad)):
+            mem = np.nonzero(ro == r)[0]
+            assert mem.size > 0
+            assert np.all(go[mem] == fo[sad[r]])
+            assert np.max(fo[mem] - go[mem]) <= fo[top[r]] - fo[sad[r]]
