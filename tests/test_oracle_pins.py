@@ -473,3 +473,23 @@ def test_region_error_bound_and_flat_value():
             assert mem.size > 0
             assert np.all(go[mem] == fo[sad[r]])
             assert np.max(fo[mem] - go[mem]) <= fo[top[r]] - fo[sad[r]]
+
+
+def test_lowering_a_swallowed_minimum_can_create_a_maximum():
+    """Why the optional restoration of swallowed authorized minima (Sec. 4.2)
+    needs a reading of its own: on this 7x4 grid the maxima pass swallows the
+    authorized minimum a = 0 into a flattened region, and a is the only higher
+    neighbour of y = 1 in the output order, so lowering a below its neighbours
+    (as the paper suggests) would turn y into a new, unauthorized maximum."""
+    f = np.array([[15, 22, 8, 13], [16, 21, 0, 24], [14, 3, 10, 11], [2, 27, 1, 18],
+                  [12, 5, 25, 9], [23, 20, 6, 4], [19, 17, 7, 26]], np.float32)
+    ids = np.array([0, 6, 7, 12, 13, 14, 15, 20, 23], np.int32)
+    nbr = H.neighbour_table(f.shape)
+    O = oracle.order_field(f)
+    mins, _ = H.extrema(O, nbr)
+    assert 0 in mins and 0 in ids
+    g, Og, _ = oracle.one_pass(f, O, ids, +1)
+    o = Og.reshape(-1)
+    mins2, maxs2 = H.extrema(Og, nbr)
+    assert 0 not in mins2 and maxs2 <= set(ids.tolist())
+    assert [u for u in nbr[1] if o[u] > o[1]] == [0]
