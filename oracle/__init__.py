@@ -11,11 +11,12 @@ Public functions (numpy in, numpy out):
     order_field(f)                    Sec. 4.1
     classify(O, shape)                Sec. 3.1 (lower/upper link components)
     persistence(f, O)                 Sec. 3.3 (Elder rule; selector of inputs)
-    authorized_by_persistence(f, thr) Sec. 3.3 (configs' authorized sets)
+    authorized_by_persistence(f, thr) Sec. 3.3 (the workloads' authorized sets)
     regions(Od, auth, method, seed)   Sec. 4.2 step 1, Sec. 4.3, Sec. 4.4
     local_orders(...)                 Sec. 4.2 step 2 (Eq. 3-5)
     apply(...)                        Sec. 4.2 steps 3-4 (Eq. 6)
     lts(f, auth_ids, mode)            the whole method
+    persistent_by_elder(g, O, dir, eps) Sec. 3.3 as Sec. 4.5 selects (Elder rule, one kind)
     pers_select(f, O, dir, eps)       Sec. 4.5 (propagations from every extremum, stopped at eps)
     pers_lts(f, eps, mode)            Sec. 4.5 (Elder-rule selection per pass, then the pass)
 """

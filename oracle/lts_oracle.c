@@ -44,7 +44,14 @@
  *     sibling blocks are ordered by the order of their highest vertex;
  *   - the numerical perturbation uses zeta = 0: every region vertex takes the
  *     saddle's value bit for bit;
- *   - one minima pass, then one maxima pass.
+ *   - one minima pass, then one maxima pass;
+ *   - persistence-driven selection (Sec. 4.5): eps is absolute; the tracked
+ *     difference is f(m) - f(v) (minima pass: f(v) - f(m)) for the class's
+ *     highest extremum m and the vertex v about to be taken, in double
+ *     precision from the float32 values; the propagation ends when it is
+ *     strictly greater than eps, before v is taken; a class whose queue runs
+ *     dry holds the global extremum, which is kept; each pass selects on the
+ *     field it receives.
  */
 #include <stdint.h>
 #include <stdlib.h>
