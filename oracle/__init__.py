@@ -19,6 +19,7 @@ Public functions (numpy in, numpy out):
     persistent_by_elder(g, O, dir, eps) Sec. 3.3 as Sec. 4.5 selects (Elder rule, one kind)
     pers_select(f, O, dir, eps)       Sec. 4.5 (propagations from every extremum, stopped at eps)
     pers_lts(f, eps, mode)            Sec. 4.5 (Elder-rule selection per pass, then the pass)
+    pers_regions(f, O, dir, eps)      Sec. 4.5 (regions read off the eps-bounded propagations)
 """
 from __future__ import annotations
 
@@ -98,6 +99,8 @@ def _get():
         lib.orc_lts.argtypes = [ctypes.c_int, P, P, P, i64, ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_uint64]
         lib.orc_pass.argtypes = [ctypes.c_int, P, ctypes.c_int, P, i64, P, P, P, ctypes.c_int, ctypes.c_uint64]
         lib.orc_pers_select.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, P]
+        lib.orc_pers_regions.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                         P, P, P, P]
         lib.orc_link_edges.argtypes = [ctypes.c_int, P]
         lib.orc_link_triangles.argtypes = [ctypes.c_int, P]
         lib.orc_neighbour_offsets.argtypes = [ctypes.c_int, P]
@@ -302,3 +305,22 @@ def pers_lts(f, eps, mode="both"):
     if _MODES[mode] & MODE_MAX:
         g, O, _ = one_pass(g, O, persistent_by_elder(g, O, +1, eps), +1)
     return g, O
+
+
+def pers_regions(f, O, direction, eps, seed=0):
+    """The regions of LTS with the persistent extrema authorized, read off
+    the eps-bounded propagations of Sec. 4.5 themselves (each merge makes a
+    fresh class; the nodes whose extremum is not persistent and that stop at
+    a saddle for good, or merge there into a persistent one, are the
+    regions).  Returns (region_of, saddle, top) in the order of regions()."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    nd, dims = _dims(f.shape)
+    n = f.size
+    region_of = np.empty(f.shape, dtype=np.int32)
+    sad = np.empty(n, dtype=np.int32)
+    top = np.empty(n, dtype=np.int32)
+    nreg = np.zeros(1, dtype=np.int64)
+    _check(_get().orc_pers_regions(nd, _p(dims), _p(f), _p(np.ascontiguousarray(O, dtype=np.int32)), direction,
+                                   float(eps), seed, _p(region_of), _p(sad), _p(top), _p(nreg)), "pers_regions")
+    k = int(nreg[0])
+    return region_of, sad[:k].copy(), top[:k].copy()

@@ -1300,3 +1300,193 @@ int orc_pers_select(int ndim, const int64_t* dims, const float* f, const int32_t
         if (isnan(f[v])) return ORC_ERR_NAN;
     return pers_select(&G, f, O, dir, eps, seed, persistent);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Regions read off the eps-bounded propagations (Sec. 4.5).  A check of a   */
+/* single-phase formulation, for tests: every merge gives the merged class a */
+/* fresh id, so a claim carries the class as it was when the claim was made, */
+/* and each absorbed class records the saddle of its merge.  A class node    */
+/* whose highest extremum is not persistent, and that waits for ever at a    */
+/* saddle or was merged at a saddle into a node whose extremum is            */
+/* persistent, is a region of LTS with the persistent extrema authorized:    */
+/* its members are the vertices claimed by it and by the nodes merged into   */
+/* it, but that saddle.                                                      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    flood_t F;
+    int32_t* top;       /* per node: highest extremum */
+    int32_t* mparent;   /* per node: the node it was merged into, or -1 */
+    int32_t* msad;      /* per node: the saddle of that merge, or -1 */
+    int32_t next;       /* next fresh node id */
+} pflood_t;
+
+static int pers_flood_run_nodes(pflood_t* P, const float* f, int dir, double eps, uint8_t* persistent,
+                                int32_t* pc, int64_t budget) {
+    flood_t* F = &P->F;
+    int32_t c = *pc;
+    for (;;) {
+        if (budget == 0) { *pc = c; return 1; }
+        if (budget > 0) --budget;
+        if (F->heap[c].n == 0) { persistent[P->top[c]] = 1; return 0; }
+        hitem it = heap_pop(&F->heap[c]);
+        int32_t v = it.v;
+        if (F->owner[v] >= 0 && cls_find(F->parent, F->owner[v]) == c) continue;
+        int32_t m = P->top[c];
+        double d = dir > 0 ? (double)f[m] - (double)f[v] : (double)f[v] - (double)f[m];
+        if (d > eps) { persistent[m] = 1; return 0; }
+        if (F->owner[v] < 0) F->owner[v] = c;
+        int32_t nb[14];
+        int kn = nbrs(F->G, v, nb);
+        int h = 0, k = 0;
+        for (int j = 0; j < kn; ++j) {
+            int32_t u = nb[j];
+            if (F->Od[u] <= F->Od[v]) continue;
+            ++h;
+            if (F->owner[u] >= 0 && cls_find(F->parent, F->owner[u]) == c) ++k;
+        }
+        if (k == h) {
+            int st = push_lower_not_in(F, v, c);
+            if (st) return -st;
+            continue;
+        }
+        if (F->cnt[v] < 0) F->cnt[v] = h;
+        F->cnt[v] -= k;
+        F->wait_next[c] = F->wait_head[v];
+        F->wait_head[v] = c;
+        if (F->cnt[v] > 0) { *pc = c; return 0; }
+        /* last arrival: every class waiting at v becomes a child of a fresh node */
+        int32_t nid = P->next++;
+        F->parent[nid] = nid;
+        P->mparent[nid] = -1;
+        P->msad[nid] = -1;
+        F->wait_next[nid] = -1;
+        int32_t best = -1;
+        for (int32_t w = F->wait_head[v]; w >= 0; w = F->wait_next[w]) {
+            int32_t a = cls_find(F->parent, w);
+            if (a == nid) continue;
+            int st = heap_meld(&F->heap[nid], &F->heap[a]);
+            if (st) return -st;
+            F->parent[a] = nid;
+            P->mparent[a] = nid;
+            P->msad[a] = v;
+            if (best < 0 || F->Od[P->top[a]] > F->Od[best]) best = P->top[a];
+        }
+        P->top[nid] = best;
+        F->wait_head[v] = -1;
+        c = nid;
+        int st = push_lower_not_in(F, v, c);
+        if (st) return -st;
+    }
+}
+
+int orc_pers_regions(int ndim, const int64_t* dims, const float* f, const int32_t* O, int dir, double eps,
+                     uint64_t seed, int32_t* region_of, int32_t* reg_saddle, int32_t* reg_top, int64_t* nreg_out) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    if (dir != 1 && dir != -1) return ORC_ERR_ARG;
+    int64_t n = G.n;
+    pflood_t P;
+    memset(&P, 0, sizeof P);
+    int32_t* Od = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* U = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * n);
+    uint8_t* persistent = (uint8_t*)calloc((size_t)n, 1);
+    int32_t *q2 = NULL, *wsad = NULL, *regid = NULL;
+    reg_t* R = NULL;
+    int64_t nu = 0, cap = 0;
+    if (!Od || !U || !perm || !persistent) { st = ORC_ERR_OOM; goto done; }
+    for (int64_t v = 0; v < n; ++v) Od[v] = dir > 0 ? O[v] : (int32_t)(n - 1 - O[v]);
+    for (int64_t v = 0; v < n; ++v) perm[Od[v]] = (int32_t)v;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int32_t v = perm[i];
+        int32_t nb[14];
+        int k = nbrs(&G, v, nb), ismax = 1;
+        for (int j = 0; j < k; ++j) if (Od[nb[j]] > Od[v]) { ismax = 0; break; }
+        if (ismax) U[nu++] = v;
+    }
+    cap = 2 * nu + 1;                      /* seeds and one fresh node per merge */
+    P.F.G = &G; P.F.Od = Od;
+    P.F.owner = (int32_t*)malloc(sizeof(int32_t) * n);
+    P.F.cnt = (int32_t*)malloc(sizeof(int32_t) * n);
+    P.F.wait_head = (int32_t*)malloc(sizeof(int32_t) * n);
+    P.F.wait_next = (int32_t*)malloc(sizeof(int32_t) * cap);
+    P.F.parent = (int32_t*)malloc(sizeof(int32_t) * cap);
+    P.F.heap = (heap_t*)calloc((size_t)cap, sizeof(heap_t));
+    P.top = (int32_t*)malloc(sizeof(int32_t) * cap);
+    P.mparent = (int32_t*)malloc(sizeof(int32_t) * cap);
+    P.msad = (int32_t*)malloc(sizeof(int32_t) * cap);
+    q2 = (int32_t*)malloc(sizeof(int32_t) * (nu + 1));
+    wsad = (int32_t*)malloc(sizeof(int32_t) * cap);
+    regid = (int32_t*)malloc(sizeof(int32_t) * cap);
+    R = (reg_t*)malloc(sizeof(reg_t) * cap);
+    if (!P.F.owner || !P.F.cnt || !P.F.wait_head || !P.F.wait_next || !P.F.parent || !P.F.heap || !P.top ||
+        !P.mparent || !P.msad || !q2 || !wsad || !regid || !R) { st = ORC_ERR_OOM; goto done; }
+    for (int64_t v = 0; v < n; ++v) { P.F.owner[v] = -1; P.F.cnt[v] = -1; P.F.wait_head[v] = -1; }
+    for (int64_t c = 0; c < cap; ++c) { P.mparent[c] = -1; P.msad[c] = -1; wsad[c] = -1; regid[c] = -1; }
+    for (int64_t c = 0; c < nu; ++c) {
+        P.F.parent[c] = (int32_t)c; P.F.wait_next[c] = -1; P.top[c] = U[c];
+        st = heap_push(&P.F.heap[c], Od[U[c]], U[c]);
+        if (st) goto done;
+        q2[c] = (int32_t)c;
+    }
+    P.next = (int32_t)nu;
+    {
+        uint64_t rs = seed;
+        if (seed) {
+            for (int64_t i = nu - 1; i > 0; --i) {
+                int64_t j = (int64_t)(sm64(&rs) % (uint64_t)(i + 1));
+                int32_t t = q2[i]; q2[i] = q2[j]; q2[j] = t;
+            }
+        }
+        int64_t qh = 0, qn = nu, qcap = nu + 1;
+        while (qn > 0) {
+            int32_t c = q2[qh]; qh = (qh + 1) % qcap; --qn;
+            int64_t budget = seed ? (int64_t)(1 + sm64(&rs) % 7) : -1;
+            int r = pers_flood_run_nodes(&P, f, dir, eps, persistent, &c, budget);
+            if (r < 0) { st = -r; goto done; }
+            if (r == 1) { q2[(qh + qn) % qcap] = c; ++qn; }
+        }
+    }
+    /* classes waiting for ever, and where */
+    for (int64_t v = 0; v < n; ++v)
+        for (int32_t w = P.F.wait_head[v]; w >= 0; w = P.F.wait_next[w]) wsad[w] = (int32_t)v;
+    /* region nodes */
+    {
+        int64_t nr = 0;
+        for (int32_t x = 0; x < P.next; ++x) {
+            if (persistent[P.top[x]]) continue;
+            int32_t p = P.mparent[x];
+            int32_t s = -1;
+            if (p >= 0 && persistent[P.top[p]]) s = P.msad[x];
+            else if (p < 0) s = wsad[x];
+            if (s < 0) continue;
+            R[nr].saddle = s; R[nr].top = P.top[x]; R[nr].cls = x;
+            R[nr].key_s = Od[s]; R[nr].key_t = Od[P.top[x]];
+            ++nr;
+        }
+        qsort(R, (size_t)nr, sizeof(reg_t), cmp_reg);
+        for (int64_t r = 0; r < nr; ++r) {
+            regid[R[r].cls] = (int32_t)r;
+            reg_saddle[r] = R[r].saddle; reg_top[r] = R[r].top;
+        }
+        for (int64_t v = 0; v < n; ++v) {
+            region_of[v] = -1;
+            int32_t y = P.F.owner[v];
+            if (y < 0 || persistent[P.top[y]]) continue;
+            int32_t z = y;
+            while (P.mparent[z] >= 0 && !persistent[P.top[P.mparent[z]]]) z = P.mparent[z];
+            if (regid[z] < 0) { st = ORC_ERR_INTERNAL; goto done; }
+            if (R[regid[z]].saddle == (int32_t)v) continue;     /* its saddle, not a member */
+            region_of[v] = regid[z];
+        }
+        *nreg_out = nr;
+    }
+done:
+    if (P.F.heap) for (int64_t c = 0; c < cap; ++c) heap_free(&P.F.heap[c]);
+    free(P.F.owner); free(P.F.cnt); free(P.F.wait_head); free(P.F.wait_next); free(P.F.parent); free(P.F.heap);
+    free(P.top); free(P.mparent); free(P.msad); free(q2); free(wsad); free(regid); free(R);
+    free(Od); free(U); free(perm); free(persistent);
+    return st;
+}

@@ -123,3 +123,27 @@ def test_negative_or_nan_eps_is_rejected():
         oracle.pers_lts(f, -1.0)
     with pytest.raises(ValueError):
         oracle.pers_lts(f, float("nan"))
+
+
+@pytest.mark.parametrize("dim3", [False, True])
+def test_regions_read_off_the_selection_equal_lts_regions(dim3):
+    """A single-phase formulation of Sec. 4.5: the regions of LTS with the
+    persistent extrema authorized can be read off the eps-bounded
+    propagations (with a fresh class per merge), under any schedule."""
+    rng = np.random.default_rng(811 + dim3)
+    for it in range(40):
+        shape = tuple(int(rng.integers(2, 7 if dim3 else 12)) for _ in range(3 if dim3 else 2))
+        f = W.random_tiny_field(rng, shape, levels=None if it % 3 else 4)
+        O = oracle.order_field(f)
+        n = f.size
+        for eps in _eps_choices(f, O, rng):
+            for d in (1, -1):
+                keep = oracle.pers_select(f, O, d, eps)
+                auth = np.zeros(n, np.uint8)
+                auth[keep] = 1
+                Od = O if d > 0 else (n - 1 - O)
+                want = oracle.regions(Od, auth)
+                for seed in (0, 5):
+                    got = oracle.pers_regions(f, O, d, eps, seed=seed)
+                    assert np.array_equal(got[0], want[0]), (it, shape, eps, d, seed)
+                    assert np.array_equal(got[1], want[1]) and np.array_equal(got[2], want[2])
