@@ -14,6 +14,7 @@ Public functions (numpy in, numpy out):
     authorized_by_persistence(f, thr) Sec. 3.3 (the workloads' authorized sets)
     regions(Od, auth, method, seed)   Sec. 4.2 step 1, Sec. 4.3, Sec. 4.4
     local_orders(...)                 Sec. 4.2 step 2 (Eq. 3-5)
+    local_order_trace(...)            Sec. 4.2 step 2 on one vertex set, with every intermediate order
     apply(...)                        Sec. 4.2 steps 3-4 (Eq. 6)
     lts(f, auth_ids, mode)            the whole method
     persistent_by_elder(g, O, dir, eps) Sec. 3.3 as Sec. 4.5 selects (Elder rule, one kind)
@@ -36,9 +37,13 @@ _LIB = os.path.join(_HERE, "liblts_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OK, ERR_ARG, ERR_NAN, ERR_NO_AUTHORIZED, ERR_OOM, ERR_INTERNAL = 0, 1, 2, 3, 4, 7
+OK, ERR_ARG, ERR_NAN, ERR_NO_AUTHORIZED, ERR_OOM, ERR_INTERNAL, ERR_CYCLE = 0, 1, 2, 3, 4, 7, 8
 MODE_MIN, MODE_MAX, MODE_BOTH = 1, 2, 3
 _MODES = {"min": MODE_MIN, "max": MODE_MAX, "both": MODE_BOTH}
+# step-2 seeding rules: the adopted one (the paper's alternation, all-boundary
+# seeds only for a region where it does not end), the paper's alternation
+# alone (ERR_CYCLE where it does not end), all-boundary seeds alone
+_RULES = {"adopted": 0, "literal": 1, "boundary": 2}
 
 
 class OracleError(RuntimeError):
@@ -57,6 +62,7 @@ class Stats(ctypes.Structure):
         ("max_local_floods", ctypes.c_int32 * 2),
         ("pad", ctypes.c_int32),
         ("total_local_floods", ctypes.c_int64 * 2),
+        ("fallback_regions", ctypes.c_int64 * 2),
     ]
 
     def as_dict(self):
@@ -71,6 +77,8 @@ class Stats(ctypes.Structure):
             "max_local_floods_max": self.max_local_floods[1],
             "total_local_floods_min": self.total_local_floods[0],
             "total_local_floods_max": self.total_local_floods[1],
+            "fallback_regions_min": self.fallback_regions[0],
+            "fallback_regions_max": self.fallback_regions[1],
         }
 
 
@@ -95,6 +103,11 @@ def _get():
         lib.orc_persistence.argtypes = [ctypes.c_int, P, P, P, P, P]
         lib.orc_regions.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_uint64, P, P, P, P]
         lib.orc_local_orders.argtypes = [ctypes.c_int, P, P, P, P, i64, P, P]
+        lib.orc_local_orders_rule.argtypes = [ctypes.c_int, P, P, P, P, i64, ctypes.c_int, P, P, P]
+        lib.orc_local_order_trace.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                              P, P, P, P, ctypes.c_int32, P]
+        lib.orc_lts_rule.argtypes = [ctypes.c_int, P, P, P, i64, ctypes.c_int, P, P, P, ctypes.c_int,
+                                     ctypes.c_uint64, ctypes.c_int]
         lib.orc_apply.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P]
         lib.orc_lts.argtypes = [ctypes.c_int, P, P, P, i64, ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_uint64]
         lib.orc_pass.argtypes = [ctypes.c_int, P, ctypes.c_int, P, i64, P, P, P, ctypes.c_int, ctypes.c_uint64]
@@ -212,17 +225,44 @@ def regions(Od, auth_mask, method=0, seed=0):
     return region_of, sad[:k].copy(), top[:k].copy()
 
 
-def local_orders(Od, region_of, saddle):
+def local_orders(Od, region_of, saddle, rule="adopted", return_fallback=False):
     """Step 2 for every region: lhat per member vertex (-1 elsewhere), and the
-    number of propagations each region needed."""
+    number of propagations each region needed (with return_fallback, also 1
+    for the regions the adopted rule redid with all-boundary seeds)."""
     Od = np.ascontiguousarray(Od, dtype=np.int32)
     nd, dims = _dims(Od.shape)
     lhat = np.empty(Od.shape, dtype=np.int32)
     fl = np.zeros(max(1, len(saddle)), dtype=np.int32)
-    _check(_get().orc_local_orders(nd, _p(dims), _p(Od), _p(np.ascontiguousarray(region_of, dtype=np.int32)),
-                                   _p(np.ascontiguousarray(saddle, dtype=np.int32)), len(saddle), _p(lhat), _p(fl)),
-           "local_orders")
+    fb = np.zeros(max(1, len(saddle)), dtype=np.int32)
+    _check(_get().orc_local_orders_rule(nd, _p(dims), _p(Od), _p(np.ascontiguousarray(region_of, dtype=np.int32)),
+                                        _p(np.ascontiguousarray(saddle, dtype=np.int32)), len(saddle), _RULES[rule],
+                                        _p(lhat), _p(fl), _p(fb)), "local_orders")
+    if return_fallback:
+        return lhat, fl[:len(saddle)].copy(), fb[:len(saddle)].copy()
     return lhat, fl[:len(saddle)].copy()
+
+
+def local_order_trace(Od, verts, sidx, rule="adopted", max_trace=64, allow_cycle=False):
+    """Step 2 on one vertex set R = verts (the saddle verts[sidx]) of the grid
+    of Od.  Returns (lhat over verts, propagations, fell_back, orders) where
+    orders[i] is the local order after propagation i of the returned run.
+    With allow_cycle, a literal run that does not end returns (None, status,
+    False, orders so far) instead of raising."""
+    Od = np.ascontiguousarray(Od, dtype=np.int32)
+    nd, dims = _dims(Od.shape)
+    verts = np.ascontiguousarray(np.asarray(verts, dtype=np.int32).reshape(-1))
+    r = verts.size
+    lhat = np.empty(r, dtype=np.int32)
+    fl = np.zeros(1, dtype=np.int32)
+    fb = np.zeros(1, dtype=np.int32)
+    tr = np.zeros((max_trace, r), dtype=np.int64)
+    nt = np.zeros(1, dtype=np.int32)
+    code = _get().orc_local_order_trace(nd, _p(dims), _p(Od), _p(verts), r, int(sidx), _RULES[rule], _p(lhat),
+                                        _p(fl), _p(fb), _p(tr), max_trace, _p(nt))
+    if allow_cycle and code == ERR_CYCLE:
+        return None, code, False, tr[:int(nt[0])].copy()
+    _check(code, "local_order_trace")
+    return lhat, int(fl[0]), bool(fb[0]), tr[:int(nt[0])].copy()
 
 
 def apply(Od, region_of, saddle, top, lhat, g):
@@ -239,16 +279,17 @@ def apply(Od, region_of, saddle, top, lhat, g):
     return Od2, g2
 
 
-def lts(f, auth_ids, mode="both", method=0, seed=0, return_stats=False):
-    """The whole method: (g, O) after the minima and/or maxima pass."""
+def lts(f, auth_ids, mode="both", method=0, seed=0, return_stats=False, rule="adopted"):
+    """The whole method: (g, O) after the minima and/or maxima pass.  rule
+    picks the step-2 seeding (tests only; the method is "adopted")."""
     f = np.ascontiguousarray(f, dtype=np.float32)
     nd, dims = _dims(f.shape)
     ids = np.ascontiguousarray(np.asarray(auth_ids, dtype=np.int32).reshape(-1))
     g = np.empty(f.shape, dtype=np.float32)
     O = np.empty(f.shape, dtype=np.int32)
     st = Stats()
-    code = _get().orc_lts(nd, _p(dims), _p(f), _p(ids) if ids.size else None, ids.size, _MODES[mode],
-                          _p(g), _p(O), ctypes.byref(st), method, seed)
+    code = _get().orc_lts_rule(nd, _p(dims), _p(f), _p(ids) if ids.size else None, ids.size, _MODES[mode],
+                               _p(g), _p(O), ctypes.byref(st), method, seed, _RULES[rule])
     _check(code, "lts")
     if return_stats:
         return g, O, st.as_dict()

@@ -34,12 +34,15 @@
  *     leaves R connected, the one with the lowest order (with a cut vertex
  *     the first propagation would not end there and could leave no
  *     authorized minimum);
- *   - the sublevel propagation of step 2 starts from every vertex allowed
- *     to be a minimum (every vertex of R other than s with a neighbour
- *     outside R), not only from those that are minima of the current local
- *     order: seeded from the current minima alone, the alternation can cycle
- *     forever (a cluster hanging off a cut vertex swaps its stray minimum and
- *     maximum at every iteration);
+ *   - the sublevel propagation of step 2 starts, as the paper says, from
+ *     the current authorized minima (minima of the current local order with
+ *     a neighbour outside R).  Taken literally the alternation can cycle
+ *     for ever (a cluster hanging off a cut vertex swaps its stray minimum
+ *     and maximum at every iteration); a region whose literal alternation
+ *     has not ended after 2|R|+2 propagations (or that has no authorized
+ *     minimum to start from) is redone from the first propagation's order
+ *     with every vertex allowed to be a minimum (all of R other than s with
+ *     an outside neighbour) as seeds, which always ended;
  *   - the pair order of Eq. 6 is made total for regions sharing a saddle:
  *     sibling blocks are ordered by the order of their highest vertex;
  *   - the numerical perturbation uses zeta = 0: every region vertex takes the
@@ -78,6 +81,7 @@ typedef struct {
     int32_t max_local_floods[2]; /* most propagations any region needed in step 2         */
     int32_t pad;
     int64_t total_local_floods[2];
+    int64_t fallback_regions[2]; /* regions step 2 redid with all-boundary seeds            */
 } orc_stats;
 
 /* ------------------------------------------------------------------------ */
@@ -896,15 +900,33 @@ out:
 /* ------------------------------------------------------------------------ */
 /* Step 2 (Sec. 4.2, Eq. 3-5): local order of one region R with saddle s.    */
 /*   l0 = Od on R, l0(s) = +inf, l0(a) = -inf for the boundary-adjacent       */
-/*   vertex a != s of lowest order.  Then alternate                           */
-/*   - a superlevel set propagation from s (largest first); the inverse of   */
-/*     the visiting order is the new local order;                            */
+/*   vertex a != s of lowest order whose removal keeps R connected.  Then     */
+/*   alternate, as the paper does:                                            */
+/*   - a superlevel set propagation from s, the only authorized maximum       */
+/*     (largest first); the inverse of the visiting order is the new order;  */
 /*   - if some minimum of it has no neighbour outside R, a sublevel set      */
-/*     propagation from every vertex of R\{s} that has one (smallest first); */
-/*     the visiting order is the new local order;                            */
+/*     propagation from all current authorized minima: the minima of the     */
+/*     current order that have a neighbour outside R (smallest first); the   */
+/*     visiting order is the new order;                                      */
 /*   until only authorized extrema remain.  Propagations use only edges      */
 /*   inside R.  lhat gets values 0..|R|-1 with s at |R|-1.                    */
+/*                                                                            */
+/*   Taken literally the alternation can cycle for ever (a cluster hanging   */
+/*   off a cut vertex of R swaps a stray minimum and maximum at every        */
+/*   iteration).  So: if the literal alternation has not ended after         */
+/*   2|R|+2 propagations, or has no authorized minimum to start from, the    */
+/*   region is redone from the first propagation's order with every vertex  */
+/*   allowed to be a minimum (all of R\{s} with an outside neighbour) as the */
+/*   seeds of each sublevel propagation.  A repeated order after a           */
+/*   superlevel propagation proves a cycle; it is detected with Brent's      */
+/*   method (one saved order) and only ends the literal attempt early: the  */
+/*   result is the same as with the cap alone.                               */
 /* ------------------------------------------------------------------------ */
+
+#define ORC_LO_ADOPTED 0      /* literal alternation, all-boundary seeding if it does not end */
+#define ORC_LO_LITERAL 1      /* literal alternation only (ORC_ERR_CYCLE if it does not end) */
+#define ORC_LO_BOUNDARY 2     /* all-boundary seeding only */
+#define ORC_ERR_CYCLE 8
 
 typedef struct {
     const grid_t* G;
@@ -955,24 +977,160 @@ static int cut_vertices(const int32_t* adj, const int8_t* deg, int32_t r, int32_
     return ORC_OK;
 }
 
-static int local_order_one(lo_ctx* C, const int32_t* verts, int32_t r, int32_t sidx,
-                           int32_t* lhat_local, int32_t* floods_out) {
+/* The region's induced graph and the orders of one local simplification. */
+typedef struct {
+    int32_t r, sidx;
+    int32_t* adj;       /* 14 slots per vertex: local indices of neighbours inside R */
+    int8_t* deg;
+    uint8_t* bnd;       /* has a neighbour outside R */
+    uint8_t* seed;      /* seeds of a sublevel set propagation */
+    uint8_t* vis;
+    int64_t* L2;        /* output of a propagation */
+    heap_t H;
+} lo_region;
+
+/* Superlevel set propagation from s by the order L (largest first):
+ * L[q_i] := r-1-i for the i-th visited vertex q_i. */
+static int lo_max_flood(lo_region* Q, int64_t* L) {
+    int32_t r = Q->r;
+    memset(Q->vis, 0, (size_t)r);
+    Q->H.n = 0;
+    int st = heap_push(&Q->H, L[Q->sidx], Q->sidx);
+    if (st) return st;
+    int64_t i = 0;
+    while (Q->H.n > 0) {
+        hitem it = heap_pop(&Q->H);
+        if (Q->vis[it.v]) continue;
+        Q->vis[it.v] = 1;
+        Q->L2[it.v] = (int64_t)r - 1 - i;
+        ++i;
+        for (int j = 0; j < Q->deg[it.v]; ++j) {
+            int32_t u = Q->adj[14 * (size_t)it.v + j];
+            if (!Q->vis[u] && (st = heap_push(&Q->H, L[u], u))) return st;
+        }
+    }
+    if (i != r) return ORC_ERR_INTERNAL;
+    memcpy(L, Q->L2, sizeof(int64_t) * (size_t)r);
+    return ORC_OK;
+}
+
+/* Sublevel set propagation from every vertex with seed[] set (smallest
+ * first): L[q_i] := i. */
+static int lo_min_flood(lo_region* Q, int64_t* L) {
+    int32_t r = Q->r;
+    memset(Q->vis, 0, (size_t)r);
+    Q->H.n = 0;
+    int st;
+    for (int32_t u = 0; u < r; ++u)
+        if (Q->seed[u] && (st = heap_push(&Q->H, -L[u], u))) return st;
+    int64_t i = 0;
+    while (Q->H.n > 0) {
+        hitem it = heap_pop(&Q->H);
+        if (Q->vis[it.v]) continue;
+        Q->vis[it.v] = 1;
+        Q->L2[it.v] = i;
+        ++i;
+        for (int j = 0; j < Q->deg[it.v]; ++j) {
+            int32_t u = Q->adj[14 * (size_t)it.v + j];
+            if (!Q->vis[u] && (st = heap_push(&Q->H, -L[u], u))) return st;
+        }
+    }
+    if (i != r) return ORC_ERR_INTERNAL;
+    memcpy(L, Q->L2, sizeof(int64_t) * (size_t)r);
+    return ORC_OK;
+}
+
+static int lo_is_min(const lo_region* Q, const int64_t* L, int32_t u) {
+    for (int j = 0; j < Q->deg[u]; ++j) if (L[Q->adj[14 * (size_t)u + j]] < L[u]) return 0;
+    return 1;
+}
+
+static int lo_is_max(const lo_region* Q, const int64_t* L, int32_t u) {
+    for (int j = 0; j < Q->deg[u]; ++j) if (L[Q->adj[14 * (size_t)u + j]] > L[u]) return 0;
+    return 1;
+}
+
+/* Unauthorized minima: minima of L without a neighbour outside R. */
+static int lo_has_unauth_min(const lo_region* Q, const int64_t* L) {
+    for (int32_t u = 0; u < Q->r; ++u) if (!Q->bnd[u] && lo_is_min(Q, L, u)) return 1;
+    return 0;
+}
+
+/* Unauthorized maxima: maxima of L other than s. */
+static int lo_has_unauth_max(const lo_region* Q, const int64_t* L) {
+    for (int32_t u = 0; u < Q->r; ++u) if (u != Q->sidx && lo_is_max(Q, L, u)) return 1;
+    return 0;
+}
+
+/* The alternation from L (the order after the first superlevel set
+ * propagation).  literal: sublevel propagations start from the current
+ * authorized minima, with Brent's cycle check on the orders after each
+ * superlevel propagation (saved: the one order kept for it); otherwise from
+ * every vertex allowed to be a minimum.  Returns ORC_OK with L final and
+ * *floods the propagations of the whole run (the first one included), or
+ * ORC_ERR_CYCLE when the run does not end (cycle, cap or no seed). */
+static int lo_alternate(lo_region* Q, int64_t* L, int literal, int64_t* saved, int32_t* floods,
+                        int64_t* trace, int32_t max_trace, int32_t* n_trace) {
+    int32_t r = Q->r;
+    int64_t cap = 2 * (int64_t)r + 2;
+    int32_t fl = 1;
+    int64_t power = 1, lam = 0;
+    int st;
+    if (literal) memcpy(saved, L, sizeof(int64_t) * (size_t)r);
+    for (;;) {
+        if (!lo_has_unauth_min(Q, L)) break;
+        int any = 0;
+        for (int32_t u = 0; u < r; ++u) {
+            Q->seed[u] = (uint8_t)(u != Q->sidx && Q->bnd[u] && (!literal || lo_is_min(Q, L, u)));
+            any |= Q->seed[u];
+        }
+        if (!any) return literal ? ORC_ERR_CYCLE : ORC_ERR_INTERNAL;
+        if (++fl > cap) return literal ? ORC_ERR_CYCLE : ORC_ERR_INTERNAL;
+        if ((st = lo_min_flood(Q, L))) return st;
+        if (trace && *n_trace < max_trace) memcpy(trace + (size_t)(*n_trace)++ * r, L, sizeof(int64_t) * (size_t)r);
+        if (!lo_has_unauth_max(Q, L)) break;
+        if (++fl > cap) return literal ? ORC_ERR_CYCLE : ORC_ERR_INTERNAL;
+        if ((st = lo_max_flood(Q, L))) return st;
+        if (trace && *n_trace < max_trace) memcpy(trace + (size_t)(*n_trace)++ * r, L, sizeof(int64_t) * (size_t)r);
+        if (literal) {
+            if (memcmp(saved, L, sizeof(int64_t) * (size_t)r) == 0) return ORC_ERR_CYCLE;
+            if (++lam == power) { memcpy(saved, L, sizeof(int64_t) * (size_t)r); power *= 2; lam = 0; }
+        }
+    }
+    *floods = fl;
+    return ORC_OK;
+}
+
+/* One region.  rule: ORC_LO_ADOPTED, ORC_LO_LITERAL or ORC_LO_BOUNDARY.
+ * *fell_back = 1 when the adopted rule redid the region with all-boundary
+ * seeds.  trace (optional): the orders after each propagation, first one
+ * included, of the run whose result is returned, max_trace orders at most. */
+static int local_order_one(lo_ctx* C, const int32_t* verts, int32_t r, int32_t sidx, int rule,
+                           int32_t* lhat_local, int32_t* floods_out, int32_t* fell_back,
+                           int64_t* trace, int32_t max_trace, int32_t* n_trace) {
     int st = ORC_OK;
-    int32_t* adj = (int32_t*)malloc(sizeof(int32_t) * 14 * (size_t)r);
-    int8_t* deg = (int8_t*)malloc((size_t)r);
-    uint8_t* bnd = (uint8_t*)malloc((size_t)r);
+    lo_region Q;
+    memset(&Q, 0, sizeof Q);
+    Q.r = r; Q.sidx = sidx;
+    Q.adj = (int32_t*)malloc(sizeof(int32_t) * 14 * (size_t)r);
+    Q.deg = (int8_t*)malloc((size_t)r);
+    Q.bnd = (uint8_t*)malloc((size_t)r);
+    Q.seed = (uint8_t*)malloc((size_t)r);
+    Q.vis = (uint8_t*)malloc((size_t)r);
+    Q.L2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)r);
     int64_t* L = (int64_t*)malloc(sizeof(int64_t) * (size_t)r);
-    int64_t* L2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)r);
-    uint8_t* vis = (uint8_t*)malloc((size_t)r);
-    heap_t H = {0, 0, 0};
-    if (!adj || !deg || !bnd || !L || !L2 || !vis) { st = ORC_ERR_OOM; goto out; }
+    int64_t* L1 = (int64_t*)malloc(sizeof(int64_t) * (size_t)r);
+    int64_t* saved = (int64_t*)malloc(sizeof(int64_t) * (size_t)r);
+    int32_t nt = 0;
+    if (fell_back) *fell_back = 0;
+    if (!Q.adj || !Q.deg || !Q.bnd || !Q.seed || !Q.vis || !Q.L2 || !L || !L1 || !saved) { st = ORC_ERR_OOM; goto out; }
     for (int32_t i = 0; i < r; ++i) {
         int32_t nb[14];
         int k = nbrs(C->G, verts[i], nb);
-        deg[i] = 0; bnd[i] = 0;
+        Q.deg[i] = 0; Q.bnd[i] = 0;
         for (int j = 0; j < k; ++j) {
             int32_t li = C->loc[nb[j]];
-            if (li < 0) bnd[i] = 1; else adj[14 * (size_t)i + deg[i]++] = li;
+            if (li < 0) Q.bnd[i] = 1; else Q.adj[14 * (size_t)i + Q.deg[i]++] = li;
         }
     }
     /* l0.  The vertex set to minus infinity must be visited last by the
@@ -980,91 +1138,40 @@ static int local_order_one(lo_ctx* C, const int32_t* verts, int32_t r, int32_t s
      * as a minimum and no authorized minimum is left; this holds exactly when
      * its removal leaves R connected.  Such a boundary-adjacent vertex always
      * exists because the grid graph is 2-connected. */
-    if ((st = cut_vertices(adj, deg, r, sidx, vis))) goto out;
+    if ((st = cut_vertices(Q.adj, Q.deg, r, sidx, Q.vis))) goto out;
     int32_t a = -1;
     for (int32_t i = 0; i < r; ++i) {
         L[i] = C->Od[verts[i]];
-        if (i != sidx && bnd[i] && !vis[i] && (a < 0 || C->Od[verts[i]] < C->Od[verts[a]])) a = i;
+        if (i != sidx && Q.bnd[i] && !Q.vis[i] && (a < 0 || C->Od[verts[i]] < C->Od[verts[a]])) a = i;
     }
     if (a < 0) { st = ORC_ERR_INTERNAL; goto out; }
     L[sidx] = INT64_MAX;
     L[a] = INT64_MIN;
-
-    int32_t floods = 0;
-    int64_t cap = 2 * (int64_t)r + 2;
-    for (;;) {
-        /* superlevel set propagation from s */
-        if (++floods > cap) { st = ORC_ERR_INTERNAL; goto out; }
-        memset(vis, 0, (size_t)r);
-        H.n = 0;
-        if ((st = heap_push(&H, L[sidx], sidx))) goto out;
-        int64_t i = 0;
-        while (H.n > 0) {
-            hitem it = heap_pop(&H);
-            if (vis[it.v]) continue;
-            vis[it.v] = 1;
-            L2[it.v] = (int64_t)r - 1 - i;
-            ++i;
-            for (int j = 0; j < deg[it.v]; ++j) {
-                int32_t u = adj[14 * (size_t)it.v + j];
-                if (!vis[u] && (st = heap_push(&H, L[u], u))) goto out;
-            }
-        }
-        if (i != r) { st = ORC_ERR_INTERNAL; goto out; }
-        memcpy(L, L2, sizeof(int64_t) * (size_t)r);
-        /* unauthorized minima: minima of L on R without a neighbour outside R */
-        int bad = 0;
-        for (int32_t u = 0; u < r && !bad; ++u) {
-            if (bnd[u] || u == a) continue;
-            int ismin = 1;
-            for (int j = 0; j < deg[u]; ++j) if (L[adj[14 * (size_t)u + j]] < L[u]) { ismin = 0; break; }
-            if (ismin) bad = 1;
-        }
-        if (!bad) break;
-
-        /* sublevel set propagation from every vertex allowed to be a minimum:
-         * all vertices of R other than s with a neighbour outside R */
-        if (++floods > cap) { st = ORC_ERR_INTERNAL; goto out; }
-        memset(vis, 0, (size_t)r);
-        H.n = 0;
-        for (int32_t u = 0; u < r; ++u) {
-            if (u == sidx || !bnd[u]) continue;
-            if ((st = heap_push(&H, -L[u], u))) goto out;
-        }
-        i = 0;
-        while (H.n > 0) {
-            hitem it = heap_pop(&H);
-            if (vis[it.v]) continue;
-            vis[it.v] = 1;
-            L2[it.v] = i;
-            ++i;
-            for (int j = 0; j < deg[it.v]; ++j) {
-                int32_t u = adj[14 * (size_t)it.v + j];
-                if (!vis[u] && (st = heap_push(&H, -L[u], u))) goto out;
-            }
-        }
-        if (i != r) { st = ORC_ERR_INTERNAL; goto out; }
-        memcpy(L, L2, sizeof(int64_t) * (size_t)r);
-        /* unauthorized maxima: maxima of L on R other than s */
-        bad = 0;
-        for (int32_t u = 0; u < r && !bad; ++u) {
-            if (u == sidx) continue;
-            int ismax = 1;
-            for (int j = 0; j < deg[u]; ++j) if (L[adj[14 * (size_t)u + j]] > L[u]) { ismax = 0; break; }
-            if (ismax) bad = 1;
-        }
-        if (!bad) break;
+    /* first iteration: superlevel set propagation from s */
+    if ((st = lo_max_flood(&Q, L))) goto out;
+    memcpy(L1, L, sizeof(int64_t) * (size_t)r);
+    if (trace && nt < max_trace) memcpy(trace + (size_t)nt++ * r, L, sizeof(int64_t) * (size_t)r);
+    st = lo_alternate(&Q, L, rule != ORC_LO_BOUNDARY, saved, floods_out, trace, max_trace, &nt);
+    if (st == ORC_ERR_CYCLE && rule == ORC_LO_ADOPTED) {
+        if (fell_back) *fell_back = 1;
+        memcpy(L, L1, sizeof(int64_t) * (size_t)r);
+        nt = trace && max_trace > 0 ? 1 : 0;
+        st = lo_alternate(&Q, L, 0, saved, floods_out, trace, max_trace, &nt);
     }
+    if (st) goto out;
     for (int32_t u = 0; u < r; ++u) lhat_local[u] = (int32_t)L[u];
-    *floods_out = floods;
 out:
-    free(adj); free(deg); free(bnd); free(L); free(L2); free(vis); heap_free(&H);
+    if (n_trace) *n_trace = nt;
+    free(Q.adj); free(Q.deg); free(Q.bnd); free(Q.seed); free(Q.vis); free(Q.L2); heap_free(&Q.H);
+    free(L); free(L1); free(saved);
     return st;
 }
 
-/* Local orders of all regions.  lhat[v] for every member v (saddles keep -1). */
+/* Local orders of all regions.  lhat[v] for every member v (saddles keep -1);
+ * reg_fallback (optional): 1 for the regions the adopted rule redid. */
 static int local_orders(const grid_t* G, const int32_t* Od, const int32_t* region_of,
-                        const int32_t* reg_saddle, int64_t nreg, int32_t* lhat, int32_t* reg_floods) {
+                        const int32_t* reg_saddle, int64_t nreg, int rule, int32_t* lhat, int32_t* reg_floods,
+                        int32_t* reg_fallback) {
     int64_t n = G->n;
     int st = ORC_OK;
     int64_t* start = (int64_t*)calloc((size_t)nreg + 1, sizeof(int64_t));
@@ -1096,8 +1203,9 @@ static int local_orders(const grid_t* G, const int32_t* Od, const int32_t* regio
         for (int32_t i = 0; i < m; ++i) { verts[i] = members[start[r] + i]; loc[verts[i]] = i; }
         verts[m] = reg_saddle[r];
         loc[reg_saddle[r]] = m;
-        int32_t fl = 0;
-        st = local_order_one(&C, verts, m + 1, m, ll, &fl);
+        int32_t fl = 0, fb = 0;
+        st = local_order_one(&C, verts, m + 1, m, rule, ll, &fl, &fb, NULL, 0, NULL);
+        if (reg_fallback) reg_fallback[r] = fb;
         for (int32_t i = 0; i <= m; ++i) loc[verts[i]] = -1;
         if (st) goto out;
         for (int32_t i = 0; i < m; ++i) lhat[verts[i]] = ll[i];
@@ -1173,7 +1281,41 @@ int orc_local_orders(int ndim, const int64_t* dims, const int32_t* Od, const int
     grid_t G;
     int st = grid_init(&G, ndim, dims);
     if (st) return st;
-    return local_orders(&G, Od, region_of, reg_saddle, nreg, lhat, reg_floods);
+    return local_orders(&G, Od, region_of, reg_saddle, nreg, ORC_LO_ADOPTED, lhat, reg_floods, NULL);
+}
+
+/* Step 2 under a given seeding rule (ORC_LO_*), with the regions redone. */
+int orc_local_orders_rule(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* region_of,
+                          const int32_t* reg_saddle, int64_t nreg, int rule, int32_t* lhat, int32_t* reg_floods,
+                          int32_t* reg_fallback) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    if (rule < ORC_LO_ADOPTED || rule > ORC_LO_BOUNDARY) return ORC_ERR_ARG;
+    return local_orders(&G, Od, region_of, reg_saddle, nreg, rule, lhat, reg_floods, reg_fallback);
+}
+
+/* Step 2 on one vertex set R (verts[0..r-1], the saddle at verts[sidx]) with
+ * the orders after each propagation: trace[i*r + j] is the order of verts[j]
+ * after propagation i (at most max_trace of them, *n_trace written). */
+int orc_local_order_trace(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* verts, int32_t r,
+                          int32_t sidx, int rule, int32_t* lhat_local, int32_t* floods, int32_t* fell_back,
+                          int64_t* trace, int32_t max_trace, int32_t* n_trace) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    if (r < 2 || sidx < 0 || sidx >= r || rule < ORC_LO_ADOPTED || rule > ORC_LO_BOUNDARY) return ORC_ERR_ARG;
+    int32_t* loc = (int32_t*)malloc(sizeof(int32_t) * G.n);
+    if (!loc) return ORC_ERR_OOM;
+    for (int64_t v = 0; v < G.n; ++v) loc[v] = -1;
+    for (int32_t i = 0; i < r; ++i) {
+        if (verts[i] < 0 || verts[i] >= G.n || loc[verts[i]] >= 0) { free(loc); return ORC_ERR_ARG; }
+        loc[verts[i]] = i;
+    }
+    lo_ctx C; C.G = &G; C.Od = Od; C.loc = loc;
+    st = local_order_one(&C, verts, r, sidx, rule, lhat_local, floods, fell_back, trace, max_trace, n_trace);
+    free(loc);
+    return st;
 }
 
 int orc_apply(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* region_of,
@@ -1188,7 +1330,7 @@ int orc_apply(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* r
 /* One pass on (g, O).  dir = +1: maxima pass; dir = -1: minima pass, run as a
  * maxima pass on the mirrored order N-1-O and mirrored back (Sec. 4:
  * minima are processed symmetrically). */
-static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, uint64_t seed,
+static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, uint64_t seed, int rule,
                     float* g, int32_t* O, orc_stats* S) {
     int64_t n = G->n;
     int st = ORC_OK;
@@ -1198,11 +1340,12 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
     int32_t* reg_top = (int32_t*)malloc(sizeof(int32_t) * n);
     int32_t* lhat = (int32_t*)malloc(sizeof(int32_t) * n);
     int32_t* reg_floods = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* reg_fb = (int32_t*)malloc(sizeof(int32_t) * n);
     int32_t* Od2 = (int32_t*)malloc(sizeof(int32_t) * n);
     float* g2 = (float*)malloc(sizeof(float) * n);
     int64_t nreg = 0;
     int side = dir > 0 ? 1 : 0;
-    if (!Od || !region_of || !reg_saddle || !reg_top || !lhat || !reg_floods || !Od2 || !g2) {
+    if (!Od || !region_of || !reg_saddle || !reg_top || !lhat || !reg_floods || !reg_fb || !Od2 || !g2) {
         st = ORC_ERR_OOM; goto out;
     }
     for (int64_t v = 0; v < n; ++v) Od[v] = dir > 0 ? O[v] : (int32_t)(n - 1 - O[v]);
@@ -1214,7 +1357,7 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
     st = method == 0 ? regions_flood(G, Od, auth, seed, region_of, reg_saddle, reg_top, &nreg)
                      : regions_jointree(G, Od, auth, region_of, reg_saddle, reg_top, &nreg);
     if (st) goto out;
-    st = local_orders(G, Od, region_of, reg_saddle, nreg, lhat, reg_floods);
+    st = local_orders(G, Od, region_of, reg_saddle, nreg, rule, lhat, reg_floods, reg_fb);
     if (st) goto out;
     st = apply_pass(G, Od, region_of, reg_saddle, reg_top, lhat, Od2, g, g2);
     if (st) goto out;
@@ -1224,7 +1367,7 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
     }
     if (S) {
         int64_t mem = 0, maxr = 0;
-        int32_t mf = 0; int64_t tf = 0;
+        int32_t mf = 0; int64_t tf = 0, nfb = 0;
         int64_t* sz = (int64_t*)calloc((size_t)nreg + 1, sizeof(int64_t));
         if (!sz) { st = ORC_ERR_OOM; goto out; }
         for (int64_t v = 0; v < n; ++v) if (region_of[v] >= 0) { ++mem; ++sz[region_of[v]]; }
@@ -1232,13 +1375,14 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
             if (sz[r] > maxr) maxr = sz[r];
             if (reg_floods[r] > mf) mf = reg_floods[r];
             tf += reg_floods[r];
+            nfb += reg_fb[r];
         }
         free(sz);
         S->regions[side] = nreg; S->region_vertices[side] = mem; S->max_region[side] = maxr;
-        S->max_local_floods[side] = mf; S->total_local_floods[side] = tf;
+        S->max_local_floods[side] = mf; S->total_local_floods[side] = tf; S->fallback_regions[side] = nfb;
     }
 out:
-    free(Od); free(region_of); free(reg_saddle); free(reg_top); free(lhat); free(reg_floods);
+    free(Od); free(region_of); free(reg_saddle); free(reg_top); free(lhat); free(reg_floods); free(reg_fb);
     free(Od2); free(g2);
     return st;
 }
@@ -1247,8 +1391,8 @@ out:
  * maxima pass.  auth_ids lists the authorized extrema (minima and maxima
  * together; an id that is not an extremum of a pass's kind is ignored by
  * that pass; duplicates are allowed). */
-int orc_lts(int ndim, const int64_t* dims, const float* f, const int32_t* auth_ids, int64_t n_auth,
-            int mode, float* g, int32_t* O, orc_stats* S, int method, uint64_t seed) {
+static int lts_rule(int ndim, const int64_t* dims, const float* f, const int32_t* auth_ids, int64_t n_auth,
+                    int mode, float* g, int32_t* O, orc_stats* S, int method, uint64_t seed, int rule) {
     grid_t G;
     int st = grid_init(&G, ndim, dims);
     if (st) return st;
@@ -1263,10 +1407,22 @@ int orc_lts(int ndim, const int64_t* dims, const float* f, const int32_t* auth_i
     if (!auth) return ORC_ERR_OOM;
     for (int64_t i = 0; i < n_auth; ++i) auth[auth_ids[i]] = 1;
     memcpy(g, f, sizeof(float) * G.n);
-    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, method, seed, g, O, S);
-    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, method, seed, g, O, S);
+    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, method, seed, rule, g, O, S);
+    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, method, seed, rule, g, O, S);
     free(auth);
     return st;
+}
+
+int orc_lts(int ndim, const int64_t* dims, const float* f, const int32_t* auth_ids, int64_t n_auth,
+            int mode, float* g, int32_t* O, orc_stats* S, int method, uint64_t seed) {
+    return lts_rule(ndim, dims, f, auth_ids, n_auth, mode, g, O, S, method, seed, ORC_LO_ADOPTED);
+}
+
+/* The whole method under a given step-2 seeding rule (ORC_LO_*), for tests. */
+int orc_lts_rule(int ndim, const int64_t* dims, const float* f, const int32_t* auth_ids, int64_t n_auth,
+                 int mode, float* g, int32_t* O, orc_stats* S, int method, uint64_t seed, int rule) {
+    if (rule < ORC_LO_ADOPTED || rule > ORC_LO_BOUNDARY) return ORC_ERR_ARG;
+    return lts_rule(ndim, dims, f, auth_ids, n_auth, mode, g, O, S, method, seed, rule);
 }
 
 /* One pass on a given (g, O), for stage-wise checks. */
@@ -1282,7 +1438,7 @@ int orc_pass(int ndim, const int64_t* dims, int dir, const int32_t* auth_ids, in
         auth[auth_ids[i]] = 1;
     }
     if (S) { memset(S, 0, sizeof *S); S->n_vertices = G.n; }
-    st = one_pass(&G, dir, auth, method, seed, g, O, S);
+    st = one_pass(&G, dir, auth, method, seed, ORC_LO_ADOPTED, g, O, S);
     free(auth);
     return st;
 }
