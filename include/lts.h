@@ -81,6 +81,11 @@ typedef struct {
                                  /* which runs beside it; persistence-driven calls  */
                                  /* count the selection in classify.                */
     int64_t kernel_launches;     /* CUDA kernels this call launched                 */
+    int64_t fallback_regions[2]; /* regions whose step-2 alternation, seeded from   */
+                                 /* the current authorized minima as the paper     */
+                                 /* says, did not end (a cycle), and which were    */
+                                 /* redone with every vertex of R other than s     */
+                                 /* that has an outside neighbour as a seed         */
 } lts_stats;
 
 /* Creates a context on CUDA device `device` whose workspace fits grids of up

@@ -45,6 +45,7 @@ class LtsStats(ctypes.Structure):
         ("heap_spills", ctypes.c_int64 * 2),
         ("stage_us", ctypes.c_float * 8),
         ("kernel_launches", ctypes.c_int64),
+        ("fallback_regions", ctypes.c_int64 * 2),
     ]
 
     def as_dict(self):
@@ -56,6 +57,7 @@ class LtsStats(ctypes.Structure):
             "total_local_floods": list(self.total_local_floods),
             "heap_spills": list(self.heap_spills),
             "launches": int(self.kernel_launches),
+            "fallback_regions": list(self.fallback_regions),
             "stage_us": {k: round(float(v), 2) for k, v in zip(
                 ["order_field", "classify", "propagate", "regions", "local_order", "reorder", "total"],
                 list(self.stage_us)[:7])},

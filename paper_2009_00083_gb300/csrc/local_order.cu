@@ -8,9 +8,18 @@
 //   its removal leaves R connected.
 //   Then alternate: superlevel propagation from s (largest first; inverse
 //   visiting order = new local order) while some minimum lacks an outside
-//   neighbour, and sublevel propagation from every vertex of R\{s} with an
-//   outside neighbour (smallest first; visiting order = new local order)
-//   while some vertex other than s is a maximum.
+//   neighbour, and sublevel propagation from the current authorized minima,
+//   the minima of the local order with an outside neighbour (smallest first;
+//   visiting order = new local order) while some vertex other than s is a
+//   maximum.
+//   That alternation can cycle for ever.  A region whose alternation has not
+//   ended after 2|R|+2 propagations (or has no authorized minimum to start
+//   from) is redone from the first propagation's order with every vertex of
+//   R\{s} that has an outside neighbour as a seed of each sublevel
+//   propagation.  An order that repeats after a superlevel propagation proves
+//   a cycle and ends the first attempt early (Brent's method: one saved
+//   order, compared after every superlevel propagation and replaced after 1,
+//   2, 4, ... of them); that only saves work, the result is the cap's.
 // Propagations only use edges inside R.
 //
 // Tiers by region size r = |R|:
@@ -31,7 +40,7 @@ namespace lts {
 
 namespace {
 
-constexpr unsigned char kBnd = 1, kVis = 2, kTried = 4;
+constexpr unsigned char kBnd = 1, kVis = 2, kTried = 4, kSeed = 16;
 constexpr int kMedR = 1024;
 constexpr int kHugeR = 4096;
 constexpr int kNoNbr = 0xffff;
@@ -44,11 +53,19 @@ constexpr int kNoNbr = 0xffff;
 // HBM scratch; neighbours recomputed from the grid and the region tags
 template <int NN>
 struct BigStore {
-    int* v; int* l; int* l2; int* hp; unsigned char* f;
+    int* v; int* l; int* l2; int* hp; unsigned char* f; int* p;
     Geom g; const int* owner; const int* loc; int tag; int s; int m;
+    const int* O; int dir;
+    // l0 without the minus-infinity vertex: Od on the members, s on top
+    __device__ int L0(int i) const {
+        if (i == m) return INT_MAX;
+        const int o = __ldg(O + v[i]);
+        return dir > 0 ? o : g.n - 1 - o;
+    }
     __device__ int& V(int i) const { return v[i]; }
     __device__ int& L(int i) const { return l[i]; }
     __device__ int& L2(int i) const { return l2[i]; }
+    __device__ int& P(int i) const { return p[i]; }
     __device__ int hp_get(int i) const { return hp[i]; }
     __device__ void hp_set(int i, int x) const { hp[i] = x; }
     __device__ unsigned char& F(int i) const { return f[i]; }
@@ -127,13 +144,13 @@ __device__ int max_flood(const S& T, int m, int r) {
     return cnt == r ? last : -2;
 }
 
-// sublevel propagation from every vertex of R\{s} with an outside neighbour
+// sublevel propagation from the vertices flagged kSeed
 template <int NN, class S>
 __device__ bool min_flood(const S& T, int m, int r) {
     for (int i = 0; i < r; ++i) T.F(i) &= (unsigned char)~kVis;
     int n = 0, cnt = 0;
     for (int i = 0; i < m; ++i)
-        if (T.F(i) & kBnd) { T.F(i) |= kVis; hpush<false>(T, n, i); }
+        if (T.F(i) & kSeed) { T.F(i) |= kVis; hpush<false>(T, n, i); }
     while (n > 0) {
         const int i = hpop<false>(T, n);
         T.L2(i) = cnt++;
@@ -163,6 +180,27 @@ __device__ bool has_unauth_min(const S& T, int r) {
     return false;
 }
 
+// flags the seeds of a sublevel propagation: the vertices of R\{s} with an
+// outside neighbour that are minima of L (literal) or all of them; returns
+// whether there is one
+template <int NN, class S>
+__device__ bool mark_seeds(const S& T, int m, bool literal) {
+    bool any = false;
+    for (int i = 0; i < m; ++i) {
+        bool sd = (T.F(i) & kBnd) != 0;
+        if (sd && literal) {
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                const int j = T.nbr(i, q);
+                if (j >= 0 && T.L(j) < T.L(i)) sd = false;
+            }
+        }
+        T.F(i) = (unsigned char)(sd ? (T.F(i) | kSeed) : (T.F(i) & ~kSeed));
+        any |= sd;
+    }
+    return any;
+}
+
 template <int NN, class S>
 __device__ bool has_unauth_max(const S& T, int m) {
     for (int i = 0; i < m; ++i) {
@@ -177,15 +215,20 @@ __device__ bool has_unauth_max(const S& T, int m) {
     return false;
 }
 
-// Runs step 2 on a region whose V, L (Od; L(m) = INT_MAX) and F (kBnd)
-// are set.  On success L holds the local order; returns the number of
-// propagations of the alternation, or -1 on failure.
+// Propagation count of a region that was redone with every boundary vertex
+// as a seed (or-ed into the count returned by local_order_run).
+constexpr int kFellBack = 1 << 30;
+
+// Runs step 2 on a region whose V, L (= L0) and F (kBnd) are set.  On success
+// L holds the local order; returns the number of propagations of the run
+// whose result is kept (| kFellBack if the region was redone), or -1.
 template <int NN, class S>
 __device__ int local_order_run(const S& T, int m) {
     const int r = m + 1;
     bool ok = false;
+    int a = -1;
     for (;;) {
-        int a = -1;
+        a = -1;
         for (int i = 0; i < m; ++i)
             if ((T.F(i) & (kBnd | kTried)) == kBnd && (a < 0 || T.L(i) < T.L(a))) a = i;
         if (a < 0) break;
@@ -198,27 +241,48 @@ __device__ int local_order_run(const S& T, int m) {
         T.F(a) |= kTried;
     }
     if (!ok) return -1;
-    for (int i = 0; i < r; ++i) T.L(i) = T.L2(i);
     const int cap = 2 * r + 2;
-    int nfl = 1;
-    for (;;) {
-        if (!has_unauth_min<NN>(T, r)) break;
-        if (!min_flood<NN>(T, m, r)) return -1;
-        for (int i = 0; i < r; ++i) T.L(i) = T.L2(i);
-        ++nfl;
-        if (!has_unauth_max<NN>(T, m)) break;
-        if (max_flood<NN>(T, m, r) < 0) return -1;
-        for (int i = 0; i < r; ++i) T.L(i) = T.L2(i);
-        ++nfl;
-        if (nfl > cap) return -1;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool literal = pass == 0;
+        if (!literal) {                     // rebuild l1 in L2
+            for (int i = 0; i < r; ++i) T.L(i) = T.L0(i);
+            T.L(a) = INT_MIN;
+            if (max_flood<NN>(T, m, r) != a) return -1;
+        }
+        for (int i = 0; i < r; ++i) { T.L(i) = T.L2(i); T.P(i) = T.L2(i); }
+        int nfl = 1, res = 0;               // res: 1 done, -1 does not end, -2 error
+        long long power = 1, lam = 0;
+        for (;;) {
+            if (!has_unauth_min<NN>(T, r)) { res = 1; break; }
+            if (!mark_seeds<NN>(T, m, literal)) { res = -1; break; }
+            if (++nfl > cap) { res = -1; break; }
+            if (!min_flood<NN>(T, m, r)) { res = -2; break; }
+            for (int i = 0; i < r; ++i) T.L(i) = T.L2(i);
+            if (!has_unauth_max<NN>(T, m)) { res = 1; break; }
+            if (++nfl > cap) { res = -1; break; }
+            if (max_flood<NN>(T, m, r) < 0) { res = -2; break; }
+            for (int i = 0; i < r; ++i) T.L(i) = T.L2(i);
+            if (literal) {
+                bool same = true;
+                for (int i = 0; i < r && same; ++i) same = T.P(i) == T.L(i);
+                if (same) { res = -1; break; }
+                if (++lam == power) {
+                    for (int i = 0; i < r; ++i) T.P(i) = T.L(i);
+                    power *= 2;
+                    lam = 0;
+                }
+            }
+        }
+        if (res == 1) return literal ? nfl : (nfl | kFellBack);
+        if (res == -2 || !literal) return -1;
     }
-    return nfl;
+    return -1;
 }
 
 struct LOArgs {
     const int* O; const int* owner; const int* loc; const int* members; const int* reg_start;
     const int* reg_size; const int* reg_saddle; int* lhat;
-    int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
+    int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag; int* lo_P;
     const int* tier_list; DevCounters* ctr;
     int* lo_adj; long long lo_adj_cap;
 };
@@ -295,7 +359,7 @@ __global__ void __launch_bounds__(128, 12) lo_team_kernel(Geom g, LOArgs a, cons
     const int team = (blockIdx.x * blockDim.x + threadIdx.x) / TS;
     const int nteams = gridDim.x * blockDim.x / TS;
     const int cnt = list ? *d_count : a.ctr->n_regions;
-    int mx = 0;
+    int mx = 0, nfb = 0;
     long long tot = 0;
     for (int k = team; k < cnt; k += nteams) {
         const int rid = list ? list[k] : k;
@@ -347,23 +411,36 @@ __global__ void __launch_bounds__(128, 12) lo_team_kernel(Geom g, LOArgs a, cons
             if (T.lane == ap) { L = keepL; tried = true; }
         }
         int nfl = -1;
+        bool fell_back = false;
         if (ok) {
-            L = l2;
-            nfl = 1;
+            const int l1 = l2;
             const int cap = 2 * r + 2;
-            for (;;) {
-                bool mn, mxx;
-                team_extremum(T, L, adj, mn, mxx);
-                if (!__any_sync(T.tm, act && !bnd && mn)) break;
-                if (!team_min_flood(T, act, L, adj, mem && bnd, r, l2)) { nfl = -1; break; }
-                L = l2;
-                ++nfl;
-                team_extremum(T, L, adj, mn, mxx);
-                if (!__any_sync(T.tm, mem && mxx)) break;
-                if (team_max_flood(T, act, L, adj, m, r, l2) < 0) { nfl = -1; break; }
-                L = l2;
-                ++nfl;
-                if (nfl > cap) { nfl = -1; break; }
+            for (int pass = 0; pass < 2 && nfl < 0; ++pass) {
+                const bool literal = pass == 0;
+                L = l1;
+                int saved = l1, fl = 1, res = 0;   // res: 1 done, -1 does not end, -2 error
+                int power = 1, lam = 0;
+                for (;;) {
+                    bool mn, mxx;
+                    team_extremum(T, L, adj, mn, mxx);
+                    if (!__any_sync(T.tm, act && !bnd && mn)) { res = 1; break; }
+                    const bool sd = mem && bnd && (!literal || mn);
+                    if (!__any_sync(T.tm, sd)) { res = -1; break; }
+                    if (++fl > cap) { res = -1; break; }
+                    if (!team_min_flood(T, act, L, adj, sd, r, l2)) { res = -2; break; }
+                    L = l2;
+                    team_extremum(T, L, adj, mn, mxx);
+                    if (!__any_sync(T.tm, mem && mxx)) { res = 1; break; }
+                    if (++fl > cap) { res = -1; break; }
+                    if (team_max_flood(T, act, L, adj, m, r, l2) < 0) { res = -2; break; }
+                    L = l2;
+                    if (literal) {
+                        if (__all_sync(T.tm, !act || L == saved)) { res = -1; break; }
+                        if (++lam == power) { saved = L; power *= 2; lam = 0; }
+                    }
+                }
+                if (res == 1) { nfl = fl; fell_back = !literal; }
+                else if (res == -2) break;
             }
         }
         if (nfl < 0) {
@@ -373,19 +450,21 @@ __global__ void __launch_bounds__(128, 12) lo_team_kernel(Geom g, LOArgs a, cons
         if (mem) a.lhat[st0 + T.tl] = L;
         mx = max(mx, nfl);
         tot += nfl;
+        nfb += fell_back;
     }
     // one count per region: only the team's first lane reports
-    if (T.tl != 0) { mx = 0; tot = 0; }
+    if (T.tl != 0) { mx = 0; tot = 0; nfb = 0; }
     __syncwarp();
     warp_atomic_max(&a.ctr->max_floods, mx);
     warp_atomic_add64(&a.ctr->total_floods, tot);
+    warp_atomic_add(&a.ctr->lo_fallbacks, nfb);
 }
 
 // ---- tier 3: one warp per region of at most kMedR vertices, dense scans ----
 
 template <int NN>
 struct Dense {
-    int* v; int* L; int* L2; unsigned short* adj; unsigned char* f;   // f: kBnd | kVis | kTried | kInq
+    int* v; int* L; int* L2; int* P; unsigned short* adj; unsigned char* f;   // f: kBnd | kVis | kTried | kInq | kSeed
 };
 constexpr unsigned char kInq = 8;
 
@@ -441,8 +520,28 @@ __device__ __forceinline__ void dense_checks(const Dense<NN>& D, int r, int m, i
     umax = __any_sync(0xffffffffu, a_max);
 }
 
+// flags the seeds of a sublevel propagation (see mark_seeds); returns whether there is one
+template <int NN>
+__device__ __forceinline__ bool dense_mark_seeds(const Dense<NN>& D, int m, int lane, bool literal) {
+    bool any = false;
+    for (int i = lane; i < m; i += 32) {
+        bool sd = (D.f[i] & kBnd) != 0;
+        if (sd && literal) {
+            const int l = D.L[i];
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                const unsigned short j = D.adj[i * NN + q];
+                if (j != kNoNbr && D.L[j] < l) sd = false;
+            }
+        }
+        D.f[i] = (unsigned char)(sd ? (D.f[i] | kSeed) : (D.f[i] & ~kSeed));
+        any |= sd;
+    }
+    return __any_sync(0xffffffffu, any);
+}
+
 template <int NN, int RMAX>
-__host__ __device__ constexpr size_t dense_smem_per_warp() { return (size_t)RMAX * (3 * 4 + 2 * NN + 1) + 16; }
+__host__ __device__ constexpr size_t dense_smem_per_warp() { return (size_t)RMAX * (4 * 4 + 2 * NN + 1) + 16; }
 
 // one region per warp, WPB warps per block, regions of at most RMAX vertices
 template <int DIR, int NN, int RMAX, int WPB>
@@ -455,7 +554,8 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
     D.v = reinterpret_cast<int*>(mine);
     D.L = D.v + RMAX;
     D.L2 = D.L + RMAX;
-    D.adj = reinterpret_cast<unsigned short*>(D.L2 + RMAX);
+    D.P = D.L2 + RMAX;
+    D.adj = reinterpret_cast<unsigned short*>(D.P + RMAX);
     D.f = reinterpret_cast<unsigned char*>(D.adj + RMAX * NN);
     const int lane = threadIdx.x & 31;
     const int cnt = *d_count;
@@ -490,6 +590,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
         __syncwarp();
         // the minus-infinity vertex
         bool ok = false;
+        int ai = -1;
         for (;;) {
             int best = INT_MAX, bi = -1;
             for (int i = lane; i < m; i += 32)
@@ -497,7 +598,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
             const int K = __reduce_min_sync(0xffffffffu, best);
             if (K == INT_MAX) break;
             const int src = __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1;
-            const int ai = __shfl_sync(0xffffffffu, bi, src);
+            ai = __shfl_sync(0xffffffffu, bi, src);
             const int keep = D.L[ai];
             __syncwarp();
             if (lane == 0) D.L[ai] = -1;
@@ -510,30 +611,59 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
             __syncwarp();
         }
         int nfl = -1;
+        bool fell_back = false;
         if (ok) {
-            nfl = 1;
             const int cap = 2 * r + 2;
-            for (;;) {
-                for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
+            for (int pass = 0; pass < 2 && nfl < 0; ++pass) {
+                const bool literal = pass == 0;
+                if (!literal) {
+                    // redo from l1: rebuild it in L2 with the accepted candidate at -infinity
+                    for (int i = lane; i < r; i += 32) {
+                        D.L[i] = i == ai ? -1 : (i < m ? od<DIR>(__ldg(a.O + D.v[i]), g.n) : INT_MAX);
+                        D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
+                    }
+                    __syncwarp();
+                    if (dense_flood<true, NN>(D, r, lane) != ai) break;
+                }
+                for (int i = lane; i < r; i += 32) { D.L[i] = D.L2[i]; D.P[i] = D.L2[i]; }
                 __syncwarp();
-                bool umin, umax;
-                dense_checks(D, r, m, lane, umin, umax);
-                if (!umin) break;
-                for (int i = lane; i < r; i += 32)
-                    D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | ((i < m && (D.f[i] & kBnd)) ? kInq : 0));
-                __syncwarp();
-                if (dense_flood<false, NN>(D, r, lane) == -2) { nfl = -1; break; }
-                ++nfl;
-                for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
-                __syncwarp();
-                dense_checks(D, r, m, lane, umin, umax);
-                if (!umax) break;
-                for (int i = lane; i < r; i += 32)
-                    D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
-                __syncwarp();
-                if (dense_flood<true, NN>(D, r, lane) == -2) { nfl = -1; break; }
-                ++nfl;
-                if (nfl > cap) { nfl = -1; break; }
+                int fl = 1, res = 0;          // res: 1 done, -1 does not end, -2 error
+                int power = 1, lam = 0;
+                for (;;) {
+                    bool umin, umax;
+                    dense_checks(D, r, m, lane, umin, umax);
+                    if (!umin) { res = 1; break; }
+                    if (!dense_mark_seeds(D, m, lane, literal)) { res = -1; break; }
+                    if (++fl > cap) { res = -1; break; }
+                    for (int i = lane; i < r; i += 32)
+                        D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | ((i < m && (D.f[i] & kSeed)) ? kInq : 0));
+                    __syncwarp();
+                    if (dense_flood<false, NN>(D, r, lane) == -2) { res = -2; break; }
+                    for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
+                    __syncwarp();
+                    dense_checks(D, r, m, lane, umin, umax);
+                    if (!umax) { res = 1; break; }
+                    if (++fl > cap) { res = -1; break; }
+                    for (int i = lane; i < r; i += 32)
+                        D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
+                    __syncwarp();
+                    if (dense_flood<true, NN>(D, r, lane) == -2) { res = -2; break; }
+                    for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
+                    __syncwarp();
+                    if (literal) {
+                        bool same = true;
+                        for (int i = lane; i < r; i += 32) same &= D.P[i] == D.L[i];
+                        if (__all_sync(0xffffffffu, same)) { res = -1; break; }
+                        if (++lam == power) {
+                            for (int i = lane; i < r; i += 32) D.P[i] = D.L[i];
+                            __syncwarp();
+                            power *= 2;
+                            lam = 0;
+                        }
+                    }
+                }
+                if (res == 1) { nfl = fl; fell_back = !literal; }
+                else if (res == -2) break;
             }
         }
         __syncwarp();
@@ -545,6 +675,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
         if (lane == 0) {
             atomicMax(&a.ctr->max_floods, nfl);
             atomicAdd((unsigned long long*)&a.ctr->total_floods, (unsigned long long)nfl);
+            if (fell_back) atomicAdd(&a.ctr->lo_fallbacks, 1);
         }
         __syncwarp();
     }
@@ -646,7 +777,7 @@ __device__ int wr_flood(const WarpRegion& R, unsigned long long* H, int lane) {
     } else {
         for (int b = 0; b < R.m; b += 32) {
             const int i = b + lane;
-            const bool sd = i < R.m && (R.F[i] & kBnd);
+            const bool sd = i < R.m && (R.F[i] & kSeed);
             if (sd) R.F[i] |= kVis;
             const int key = sd ? R.L[i] : 0;
             unsigned mk = __ballot_sync(0xffffffffu, sd);
@@ -764,7 +895,7 @@ __device__ int wr_flood_keys(const WarpRegion& R, const int* Lk, int* NK, int* o
         }
     } else {
         for (int i = lane; i < R.m; i += 32)
-            if (R.F[i] & kBnd) {
+            if (R.F[i] & kSeed) {
                 const int k = Lk[i];
                 atomicOr(Q.vis + (k >> 5), 1u << (k & 31));
                 kq_push(Q, k);
@@ -811,13 +942,33 @@ __device__ bool wr_has_extremum(const WarpRegion& R, int lane) {
     return __any_sync(0xffffffffu, found);
 }
 
+// flags the seeds of a sublevel propagation (see mark_seeds); returns whether there is one
+template <int NN>
+__device__ bool wr_mark_seeds(const WarpRegion& R, int lane, bool literal) {
+    bool any = false;
+    for (int i = lane; i < R.m; i += 32) {
+        bool sd = (R.F[i] & kBnd) != 0;
+        if (sd && literal) {
+            const int li = R.L[i];
+            for (int q = 0; q < NN && sd; ++q) {
+                const int j = wr_nbr_of<NN>(R, i, q);
+                if (j >= 0 && R.L[j] < li) sd = false;
+            }
+        }
+        R.F[i] = (unsigned char)(sd ? (R.F[i] | kSeed) : (R.F[i] & ~kSeed));
+        any |= sd;
+    }
+    __syncwarp();
+    return __any_sync(0xffffffffu, any);
+}
+
 template <int DIR, int NN>
 __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
     extern __shared__ unsigned long long H[];
     if (failed(&a.ctr->status)) return;
     const int lane = threadIdx.x;
     const int cnt = *d_count;
-    int mx = 0;
+    int mx = 0, nfb = 0;
     long long tot = 0;
     for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int rid = list[k];
@@ -825,6 +976,7 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         const int s = a.reg_saddle[rid];
         const int st0 = a.reg_start[rid];
         const long long off = (long long)st0 + rid;
+        int* P = a.lo_P + off;                      // the order Brent's check compares with
         WarpRegion R{a.lo_v + off, a.lo_L + off, a.lo_L2 + off, a.lo_flag + off, g, a.owner, a.loc, -2 - rid, s, m,
                      m + 1, nullptr};
         // the local adjacency, from a bump pool (recomputed per pop when the pool is spent)
@@ -921,14 +1073,10 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         }
         // the minus-infinity vertex: lowest boundary-adjacent member whose removal keeps R connected
         bool ok = false;
-        for (;;) {
-            int best = INT_MAX, bi = -1;
-            for (int i = lane; i < m; i += 32)
-                if ((R.F[i] & (kBnd | kTried)) == kBnd && R.L[i] < best) { best = R.L[i]; bi = i; }
-            const int K = __reduce_min_sync(0xffffffffu, best);
-            if (K == INT_MAX) break;
-            const int ai = __shfl_sync(0xffffffffu, bi, __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1);
-            __syncwarp();
+        int ai = -1;
+        // the first propagation with candidate ai at -infinity (L2 gets its order);
+        // returns the last vertex (key 0 in key space), -2 / -3 on failure / heap overflow
+        auto first_flood = [&](int ai) -> int {
             if (dense) {
                 // key space: the candidate takes key 0, below every other
                 const int ra = R.V[ai];
@@ -938,42 +1086,79 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
                 }
                 __syncwarp();
                 const int lk = wr_flood_keys<true, NN>(R, R.L2, NK, ordk, Q, lane);
-                if (lk == -2) break;
-                if (lk == 0) { ok = true; break; }
-                if (lane == 0) R.F[ai] |= kTried;
-                __syncwarp();
-                continue;
+                return lk == 0 ? ai : (lk == -2 ? -2 : -1);
             }
             if (lane == 0) R.L[ai] = INT_MIN;
             __syncwarp();
-            const int last = wr_flood<true, NN>(R, H, lane);
+            return wr_flood<true, NN>(R, H, lane);
+        };
+        for (;;) {
+            int best = INT_MAX, bi = -1;
+            for (int i = lane; i < m; i += 32)
+                if ((R.F[i] & (kBnd | kTried)) == kBnd && R.L[i] < best) { best = R.L[i]; bi = i; }
+            const int K = __reduce_min_sync(0xffffffffu, best);
+            if (K == INT_MAX) break;
+            ai = __shfl_sync(0xffffffffu, bi, __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1);
+            __syncwarp();
+            const int last = first_flood(ai);
             if (last == -3) { overflow = true; break; }
             if (last == -2) break;
             if (last == ai) { ok = true; break; }
-            if (lane == 0) { R.L[ai] = K; R.F[ai] |= kTried; }
+            if (lane == 0) { if (!dense) R.L[ai] = K; R.F[ai] |= kTried; }
             __syncwarp();
         }
+        bool fell_back = false;
         if (ok) {
-            nfl = 1;
             const int cap = 2 * R.r + 2;
-            for (;;) {
-                for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
+            for (int pass = 0; pass < 2 && nfl < 0 && !overflow; ++pass) {
+                const bool literal = pass == 0;
+                if (!literal) {
+                    // redo from l1: rebuild it in L2 (V holds vertex ids unless dense)
+                    if (!dense) {
+                        for (int i = lane; i <= m; i += 32) R.L[i] = i < m ? od<DIR>(__ldg(a.O + R.V[i]), g.n) : INT_MAX;
+                        __syncwarp();
+                    }
+                    const int last = first_flood(ai);
+                    if (last == -3) { overflow = true; break; }
+                    if (last != ai) break;
+                }
+                for (int i = lane; i < R.r; i += 32) { R.L[i] = R.L2[i]; P[i] = R.L2[i]; }
                 __syncwarp();
-                if (!wr_has_extremum<true, NN>(R, lane)) break;
-                const int rmin = keyspace ? wr_flood_keys<false, NN>(R, R.L, NK, ordk, Q, lane)
-                                          : wr_flood<false, NN>(R, H, lane);
-                if (rmin == -3) { overflow = true; break; }
-                if (rmin < 0) { nfl = -1; break; }
-                ++nfl;
-                for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
-                __syncwarp();
-                if (!wr_has_extremum<false, NN>(R, lane)) break;
-                const int rmax = keyspace ? wr_flood_keys<true, NN>(R, R.L, NK, ordk, Q, lane)
-                                          : wr_flood<true, NN>(R, H, lane);
-                if (rmax == -3) { overflow = true; break; }
-                if (rmax < 0) { nfl = -1; break; }
-                ++nfl;
-                if (nfl > cap) { nfl = -1; break; }
+                int fl = 1, res = 0;            // res: 1 done, -1 does not end, -2 error, -3 overflow
+                int power = 1, lam = 0;
+                for (;;) {
+                    if (!wr_has_extremum<true, NN>(R, lane)) { res = 1; break; }
+                    if (!wr_mark_seeds<NN>(R, lane, literal)) { res = -1; break; }
+                    if (++fl > cap) { res = -1; break; }
+                    const int rmin = keyspace ? wr_flood_keys<false, NN>(R, R.L, NK, ordk, Q, lane)
+                                              : wr_flood<false, NN>(R, H, lane);
+                    if (rmin == -3) { res = -3; break; }
+                    if (rmin < 0) { res = -2; break; }
+                    for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
+                    __syncwarp();
+                    if (!wr_has_extremum<false, NN>(R, lane)) { res = 1; break; }
+                    if (++fl > cap) { res = -1; break; }
+                    const int rmax = keyspace ? wr_flood_keys<true, NN>(R, R.L, NK, ordk, Q, lane)
+                                              : wr_flood<true, NN>(R, H, lane);
+                    if (rmax == -3) { res = -3; break; }
+                    if (rmax < 0) { res = -2; break; }
+                    for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
+                    __syncwarp();
+                    if (literal) {
+                        bool same = true;
+                        for (int i = lane; i < R.r; i += 32) same &= P[i] == R.L[i];
+                        if (__all_sync(0xffffffffu, same)) { res = -1; break; }
+                        if (++lam == power) {
+                            for (int i = lane; i < R.r; i += 32) P[i] = R.L[i];
+                            __syncwarp();
+                            power *= 2;
+                            lam = 0;
+                        }
+                    }
+                }
+                if (res == 1) { nfl = fl; fell_back = !literal; }
+                else if (res == -3) overflow = true;
+                else if (res == -2) break;
             }
         }
         __syncwarp();
@@ -981,15 +1166,20 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
             // the frontier outgrew the heap: lane 0 redoes the region on the single-thread path
             nfl = -1;
             if (lane == 0) {
-                BigStore<NN> T{a.lo_v + off, a.lo_L + off, a.lo_L2 + off, a.lo_heap + off, a.lo_flag + off,
-                               g, a.owner, a.loc, -2 - rid, s, m};
+                BigStore<NN> T{a.lo_v + off, a.lo_L + off, a.lo_L2 + off, a.lo_heap + off, a.lo_flag + off, P,
+                               g, a.owner, a.loc, -2 - rid, s, m, a.O, DIR};
+                // V holds vertex ids again (the dense ranks are recomputed from scratch)
+                for (int i = 0; i <= m; ++i) T.V(i) = i < m ? a.members[st0 + i] : s;
                 for (int i = 0; i <= m; ++i) {
                     T.F(i) &= kBnd;
-                    T.L(i) = i < m ? od<DIR>(__ldg(a.O + T.V(i)), g.n) : INT_MAX;
+                    T.L(i) = T.L0(i);
                 }
                 nfl = local_order_run<NN>(T, m);
+                fell_back = nfl >= 0 && (nfl & kFellBack);
+                if (nfl >= 0) nfl &= ~kFellBack;
             }
             nfl = __shfl_sync(0xffffffffu, nfl, 0);
+            fell_back = __shfl_sync(0xffffffffu, fell_back, 0);
         }
         if (nfl < 0) {
             if (lane == 0) set_status(&a.ctr->status, LTS_ERR_INTERNAL);
@@ -998,11 +1188,13 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         for (int i = lane; i < m; i += 32) a.lhat[st0 + i] = R.L[i];
         mx = max(mx, nfl);
         tot += nfl;
+        nfb += fell_back;
         __syncwarp();
     }
-    if (lane != 0) { mx = 0; tot = 0; }
+    if (lane != 0) { mx = 0; tot = 0; nfb = 0; }
     warp_atomic_max(&a.ctr->max_floods, mx);
     warp_atomic_add64(&a.ctr->total_floods, tot);
+    warp_atomic_add(&a.ctr->lo_fallbacks, nfb);
 }
 
 template <int DIR, int NN>
@@ -1046,7 +1238,7 @@ void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t
 template <int DIR>
 cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s) {
     LOArgs a{O, w.owner, w.loc, w.members, w.reg_start, w.reg_size, w.reg_saddle, w.lhat,
-             w.lo_v, w.lo_L, w.lo_L2, w.lo_heap, w.lo_flag, w.tier_list, w.ctr, w.lo_adj, w.lo_adj_cap};
+             w.lo_v, w.lo_L, w.lo_L2, w.lo_heap, w.lo_flag, w.lo_P, w.tier_list, w.ctr, w.lo_adj, w.lo_adj_cap};
     if (g.nn == 14) launch_tiers<DIR, 14>(w, g, a, sms, s);
     else launch_tiers<DIR, 6>(w, g, a, sms, s);
     w.launches += 6;

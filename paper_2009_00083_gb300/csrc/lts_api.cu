@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <deque>
 #include <cstring>
+#include <cstdlib>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -111,7 +112,7 @@ size_t bytes_for(const Sizes& z) {
     b += 4 * (size_t)z.spill_cap + 8 * (size_t)z.heap_cap + 4 * (size_t)z.log_cap;
     b += 11 * 4 * (size_t)z.half;                   // region records
     b += 3 * 4 * (size_t)z.n;                       // members, member regions, lhat
-    b += 17 * (size_t)z.lo_cap;                     // local-order scratch
+    b += 21 * (size_t)z.lo_cap;                     // local-order scratch
     b += 16 * (size_t)z.n;                          // local adjacency of the largest regions
     b += sizeof(RankBlk) * (size_t)z.nblk + 2 * 4 * (size_t)z.half;
     b += 8 * (size_t)z.scan_tiles + sizeof(DevCounters) + 2 * sizeof(PassStats);
@@ -166,6 +167,10 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     w.log_cap = z.log_cap; w.spill_cap = z.spill_cap; w.heap_cap = z.heap_cap; w.lo_cap = z.lo_cap;
     w.nblk = (int)z.nblk;
     w.scan_tmp_cap = (int)z.scan_tiles;
+    // tests only: LTS_TEST_MIN_TIER=k (1..5) runs step 2 of small regions in tier k
+    // (the results do not depend on the tier)
+    w.min_tier = 0;
+    if (const char* mt = getenv("LTS_TEST_MIN_TIER")) w.min_tier = std::max(0, std::min(5, atoi(mt)));
     bool ok = true;
     ok = ok && dev_alloc(L, &w.keyA, z.n) && dev_alloc(L, &w.valA, z.n) && dev_alloc(L, &w.keyB, z.n) &&
          dev_alloc(L, &w.valB, z.n);
@@ -191,7 +196,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     ok = ok && dev_alloc(L, &w.members, z.n) && dev_alloc(L, &w.lhat, z.n) && dev_alloc(L, &w.tier_list, 2 * z.half) &&
          dev_alloc(L, &w.member_reg, z.n);
     ok = ok && dev_alloc(L, &w.lo_v, z.lo_cap) && dev_alloc(L, &w.lo_L, z.lo_cap) && dev_alloc(L, &w.lo_L2, z.lo_cap) &&
-         dev_alloc(L, &w.lo_heap, z.lo_cap) && dev_alloc(L, &w.lo_flag, z.lo_cap) &&
+         dev_alloc(L, &w.lo_heap, z.lo_cap) && dev_alloc(L, &w.lo_flag, z.lo_cap) && dev_alloc(L, &w.lo_P, z.lo_cap) &&
          dev_alloc(L, &w.lo_adj, 4 * z.n + 4096);
     w.lo_adj_cap = 4 * z.n + 4096;
     ok = ok && dev_alloc(L, &w.rblk, z.nblk) && dev_alloc(L, &w.sad_att, z.half) && dev_alloc(L, &w.cumA, z.half + 1);
@@ -342,6 +347,7 @@ __global__ void save_pass_kernel(const DevCounters* ctr, const int* reg_start, P
     ps->max_floods = ctr->max_floods;
     ps->total_floods = ctr->total_floods;
     ps->heap_spills = ctr->heap_spills;
+    ps->fallbacks = ctr->lo_fallbacks;
 }
 
 // the request's final status and pass statistics
@@ -467,6 +473,7 @@ void fill_stats(lts_stats& o, long long n, const PassStats* ps, long long launch
         o.max_local_floods[k] = (int32_t)ps[k].max_floods;
         o.total_local_floods[k] = ps[k].total_floods;
         o.heap_spills[k] = ps[k].heap_spills;
+        o.fallback_regions[k] = ps[k].fallbacks;
     }
     o.kernel_launches = launches;
 }

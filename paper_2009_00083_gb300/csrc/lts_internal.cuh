@@ -102,6 +102,7 @@ struct DevCounters {
     int n_big;             // regions for the HBM tier of step 2
     int n_tasks;           // propagation tasks left after the first step
     long long lo_adj_cursor; // local adjacency pool of the largest local-order tier (ints)
+    int lo_fallbacks;      // regions step 2 redid with every boundary vertex as a seed
 };
 
 __device__ __forceinline__ void set_oom(DevCounters* ctr, int pool) {
@@ -111,7 +112,7 @@ __device__ __forceinline__ void set_oom(DevCounters* ctr, int pool) {
 
 // Per-pass statistics accumulated into the host stats.
 struct PassStats {
-    long long removed, regions, region_vertices, max_region, max_floods, total_floods, heap_spills;
+    long long removed, regions, region_vertices, max_region, max_floods, total_floods, heap_spills, fallbacks;
 };
 
 // Rank-space block of 32 ranks (16 bytes, one vector load): members and
@@ -163,7 +164,7 @@ struct Work {
     int* members; int* lhat; int* member_reg;   // CSR members, their local order, their region
     int* tier_list;                      // [0,cap): 16-lane tier; then quarters of cap: 32-lane, dense <=128, dense <=1024, HBM
     // local-order scratch (slots: members + one saddle per region)
-    int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag;
+    int* lo_v; int* lo_L; int* lo_L2; int* lo_heap; unsigned char* lo_flag; int* lo_P;
     int* lo_adj; long long lo_adj_cap;   // local adjacency of the largest regions (bump pool)
     long long lo_cap;
     // the local-order tiers run side by side: three more streams, forked from
@@ -181,6 +182,7 @@ struct Work {
     DevCounters* ctr;
     PassStats* pstats;                   // [0] minima pass, [1] maxima pass
     DevCounters* h_ctr;                  // pinned host copy (followed by two PassStats)
+    int min_tier;                        // tests only: step-2 regions go to at least this tier (0: by size)
     int lanes;                           // propagation lanes (threads)
     int class_cap;                       // capacity of the class and region arrays
     long long launches;                  // kernels launched by the current call

@@ -109,8 +109,12 @@ __global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int
 // vertex (it has neighbours outside R), the propagation from s visits it
 // last, and no vertex lacks an outside neighbour, so lhat(m) = 0 after one
 // propagation.
+// min_tier > 0 (tests only) moves regions up to tier min_tier (0: 16 lanes,
+// 1: 32 lanes, 2: dense <= 128, 3: dense <= med_max, 4: dense <= huge_max,
+// 5: HBM) while its list has room, so that every tier runs on small regions.
 __global__ void tiers_kernel(const int* __restrict__ reg_size, const int* __restrict__ reg_start, int* lhat,
-                             int* tier_list, int cap, int q, int med_max, int huge_max, DevCounters* ctr) {
+                             int* tier_list, int cap, int q, int med_max, int huge_max, int min_tier, int nverts,
+                             DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nreg = ctr->n_regions;
     int trivial = 0;
@@ -118,15 +122,37 @@ __global__ void tiers_kernel(const int* __restrict__ reg_size, const int* __rest
         const int r = (int)(b + threadIdx.x);
         const int sz = r < nreg ? reg_size[r] + 1 : 0;
         if (sz == 2) { lhat[reg_start[r]] = 0; ++trivial; }
-        const bool t16 = sz > 2 && sz <= 16;
+        int tier = sz <= 2 ? -1 : sz <= 16 ? 0 : sz <= 32 ? 1 : sz <= 128 ? 2 : sz <= med_max ? 3 : sz <= huge_max ? 4 : 5;
+        if (tier >= 0 && tier < min_tier) {
+            // room in the forced tier's list (quarters of cap; the last one split in halves)
+            int* cnt = min_tier == 1 ? &ctr->n_t32 : min_tier == 2 ? &ctr->n_med : min_tier == 3 ? &ctr->n_large
+                     : min_tier == 4 ? &ctr->n_huge : &ctr->n_big;
+            // leave room for the regions that belong there by size (at most nverts / their least size)
+            const int least = min_tier == 1 ? 16 : min_tier == 2 ? 32 : min_tier == 3 ? 128
+                            : min_tier == 4 ? med_max : huge_max;
+            const int room = (min_tier >= 4 ? q / 2 : q) - nverts / least;
+            if (*(volatile int*)cnt < room) {
+                const int pos = atomicAdd(cnt, 1);
+                if (pos < room) {
+                    int* rest = tier_list + cap;
+                    const int base = min_tier == 1 ? 0 : min_tier == 2 ? q : min_tier == 3 ? 2 * q
+                                   : min_tier == 4 ? 3 * q : 3 * q + q / 2;
+                    rest[base + pos] = r;
+                    tier = -2;                        // placed
+                } else {
+                    atomicSub(cnt, 1);
+                }
+            }
+        }
+        const bool t16 = tier == 0;
         const int p16 = warp_reserve(&ctr->n_t16, t16);
         if (t16) tier_list[p16] = r;
         int* rest = tier_list + cap;
-        const bool t32 = sz > 16 && sz <= 32;
-        const bool med = sz > 32 && sz <= 128;
-        const bool lrg = sz > 128 && sz <= med_max;
-        const bool huge = sz > med_max && sz <= huge_max;
-        const bool big = sz > huge_max;
+        const bool t32 = tier == 1;
+        const bool med = tier == 2;
+        const bool lrg = tier == 3;
+        const bool huge = tier == 4;
+        const bool big = tier == 5;
         const int p32 = warp_reserve(&ctr->n_t32, t32);
         const int pm = warp_reserve(&ctr->n_med, med);
         const int pl = warp_reserve(&ctr->n_large, lrg);
@@ -204,7 +230,7 @@ cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaS
     siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.sib_head, w.sib_next,
                                     w.class2reg, w.reg_place, w.reg_att, w.rblk, w.ctr);
     tiers_kernel<<<B, T, 0, s>>>(w.reg_size, w.reg_start, w.lhat, w.tier_list, w.class_cap, w.class_cap / 4,
-                                 local_order_med_max(), local_order_huge_max(), w.ctr);
+                                 local_order_med_max(), local_order_huge_max(), w.min_tier, g.n, w.ctr);
     w.launches += 6;
     return cudaGetLastError();
 }

@@ -109,6 +109,7 @@ def test_gaussian_configs(lts, config):
     assert st["regions"] == [st_ref["regions_min"], st_ref["regions_max"]]
     assert st["region_vertices"] == [st_ref["region_vertices_min"], st_ref["region_vertices_max"]]
     assert st["max_local_floods"] == [st_ref["max_local_floods_min"], st_ref["max_local_floods_max"]]
+    assert st["fallback_regions"] == [st_ref["fallback_regions_min"], st_ref["fallback_regions_max"]]
 
 
 @pytest.mark.parametrize("side", [64, 128])
