@@ -40,20 +40,32 @@ METRIC = "LTS Mvertices/s (bit-exact vs oracle), batched vs plain per-field; ser
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# Algorithmic bytes per vertex of each stage of one call in mode both
-# (every array touched once at its minimal width):
+# Algorithmic bytes of each stage of one call in mode both (every array
+# touched once at its minimal width), per vertex of the grid for the
+# streaming stages and per region vertex (a vertex moved by a pass, summed
+# over the two passes) for the output-sensitive ones:
 #   order field: read f (4) + copy to g (4) + a 32-bit LSD sort with 11-bit
 #     digits: 3 passes x (read 8 + write 8) + rank write (4) + keep (4)
 #   classify:    read the order field once per pass (2 x 4)
 #   reorder:     read + write the order field per pass (2 x 8)
-BYTES_PER_VERTEX = {"order_field": 4 + 4 + 48 + 8, "classify": 8, "reorder": 16}
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# order-field kernels per vertex, from an ncu capture of the 256^3 case of the
-# same recipe, scaled by the vertex count (the 512^3 call is too large to
-# capture with all metrics); only the order-field stage has a capture.  The
-# recipe's fields have few distinct values, so the capture is of the two-pass
-# sort on compressed keys; the algorithmic count above stays the general one.
-TRAFFIC_PER_VERTEX = {"order_field": 41.7}   # the two-pass sort on compressed keys (few distinct values)
+#   propagate:   per region vertex and pass: its order, its owner and its
+#     queue mark read, the claim written, the log entry written (~24)
+#   regions:     per region vertex: the log entry read, member id, its region
+#     and its local index written (16)
+#   local order: per region vertex: read member, adjacency tags and order,
+#     write the local order (~24)
+STAGE_BYTES = {"order_field": (64, "vertex"), "classify": (8, "vertex"), "reorder": (16, "vertex"),
+               "propagate": (24, "region vertex"), "regions": (16, "region vertex"),
+               "local_order": (24, "region vertex")}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a stage's
+# kernels per unit, from an ncu capture of the 256^3 case of the same recipe
+# scaled by the units (the 512^3 call is too large to capture with all
+# metrics), and the kernels it covers; None where no capture of the current
+# kernels exists.
+#   order field: the two-pass sort on compressed keys (the recipe's fields have
+#     few distinct values; the algorithmic count above stays the general one)
+#   propagate: first_step_kernel + propagate_kernel, both passes
+STAGE_TRAFFIC = {"order_field": 41.7, "propagate": 799.0}
 PATH_BYTES_PER_VERTEX = 100   # sort + classify + flatten, both passes
 
 
@@ -152,10 +164,39 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(sample_side=160):
-    """The oracle, as it stands, single-threaded on the host: same recipe on a
-    bounded sample (a sample_side^3 field), authorized list precomputed, mode
-    both, wall clock of the whole method (order field included)."""
+def host_cpu():
+    """The host's CPU model and logical core count."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+
+    return {"cpu_model": model or platform.processor() or platform.machine(), "host_cores": os.cpu_count()}
+
+
+def cpu_baseline(sample_side=224):
+    """The oracle, as it stands, single-threaded on the host: the headline
+    recipe (box noise, 10% persistence) on a bounded sample (a sample_side^3
+    field, about 20 s of CPU work), authorized list precomputed, mode both,
+    wall clock of the whole method (order field included), best of 1.  The
+    rate is per vertex; the oracle's cost per vertex grows slowly with size
+    (its sorts are n log n), so the 512^3 rate would be a little lower."""
     import oracle
 
     f = W.make_config_field(2, shape=(sample_side,) * 3)
@@ -163,9 +204,11 @@ def cpu_baseline(sample_side=160):
     t = time.perf_counter()
     oracle.lts(f, ids, mode="both")
     dt = time.perf_counter() - t
-    return {"value": round(f.size / dt / 1e6, 3), "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
-            "sample": f"box-noise recipe at {sample_side}^3 ({f.size} vertices), mode both, "
-                      f"{dt:.1f} s single-threaded"}
+    out = {"value": round(f.size / dt / 1e6, 3), "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
+           "sample": f"box-noise recipe at {sample_side}^3 ({f.size} vertices), mode both, "
+                     f"{dt:.1f} s single-threaded, best of 1"}
+    out.update(host_cpu())
+    return out
 
 
 def run_reference(args):
@@ -191,8 +234,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
         "config": {"workload": args.workload, "reference_sample": f"{side}^3"},
-        "cpu_baseline": {"value": round(value, 3), "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": dict({"value": round(value, 3), "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
+                              "sample": sample}, **host_cpu()),
         "e2e": {"value": round(value, 3), "unit": "Mvertices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -440,12 +483,12 @@ def sweep_leg(lts, torch, dev, side=256, points=(0, 10, 20, 30, 40, 50, 60, 70, 
                 e1.record(ctx.stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
-            rows.append({"removed_pct": p, "ms": round(statistics.median(times), 3), "removed": st["removed"],
-                         "regions": st["regions"], "max_region": st["max_region"],
-                         "region_vertices": st["region_vertices"]})
+            rows.append([p, round(statistics.median(times), 3), sum(st["removed"]), sum(st["regions"]),
+                         max(st["max_region"]), sum(st["region_vertices"])])
     finally:
         ctx.close()
     return {"workload": f"white noise {side}^3 (uniform [0,1) float32), a random share of the extrema removed",
+            "columns": ["removed_pct", "ms", "removed", "regions", "max_region", "region_vertices"],
             "points": rows}
 
 
@@ -537,10 +580,25 @@ def main():
             dist.destroy_process_group()
         return
     peak, kind = peaks()
-    # dominant stage by device time, and its algorithmic bytes
-    dom = max(BYTES_PER_VERTEX, key=lambda k: stage_us.get(k, 0.0))
-    dom_us = stage_us[dom]
-    achieved = BYTES_PER_VERTEX[dom] * n / (dom_us * 1e-6) / 1e9
+    # every stage against its algorithmic bytes; the roofline is the stage with the most device time
+    rv = sum(st["region_vertices"])
+    stages = {}
+    for k, (bpu, unit) in STAGE_BYTES.items():
+        us = stage_us.get(k, 0.0)
+        units = rv if unit == "region vertex" else n
+        gbs = bpu * units / (us * 1e-6) / 1e9 if us > 0 else 0.0
+        tr = STAGE_TRAFFIC.get(k)
+        stages[k] = {"us": round(us, 1), "bytes_per_unit": bpu, "unit": unit, "units": int(units),
+                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                     "traffic_bytes": int(tr * units) if tr is not None else None}
+    dom = max(stages, key=lambda k: stages[k]["us"])
+    dstage = stages[dom]
+    kernels = {"order_field": "order field (histogram/copy with distinct-key count, onesweep digit passes: two on "
+                              "compressed keys for this quantized field, four otherwise; inverse)",
+               "propagate": "propagation engine (first_step_kernel + persistent propagate_kernel, both passes)",
+               "local_order": "local-order tiers (team, dense, key-space warp kernels, both passes)",
+               "regions": "region extraction (flatten, roots, members count/fill, siblings, tiers, both passes)",
+               "classify": "classify_kernel (both passes)", "reorder": "reorder and flatten (both passes)"}
     path_achieved = PATH_BYTES_PER_VERTEX * n / (ms * 1e-3) / 1e9
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     batch = None if args.no_batch or world > 1 else batch_leg(lts, torch, dev)
@@ -555,23 +613,21 @@ def main():
                    "authorized": int(ids.size), "mode": "both", "l2": "inputs (512 MB) larger than L2",
                    "parallelism": f"replicas x{world}"},
         "parity_vs_oracle": bool(parity),
-        "roofline": {"bound": "hbm", "kernel": dom + (" (histogram/copy with distinct-key count, onesweep digit "
-                                                      "passes: two on compressed keys for this quantized field, "
-                                                      "four otherwise; inverse)"
-                                                      if dom == "order_field" else ""),
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4),
-                     "traffic": (int(TRAFFIC_PER_VERTEX[dom] * n) if dom in TRAFFIC_PER_VERTEX else None),
-                     "peak_kind": kind, "bytes_per_vertex": BYTES_PER_VERTEX[dom]},
-        "path_roofline": {"bytes_per_vertex": PATH_BYTES_PER_VERTEX, "achieved": round(path_achieved, 1),
-                          "peak": peak, "unit": "GB/s", "frac": round(path_achieved / peak, 4)},
-        "stage_us": {k: round(v, 1) for k, v in stage_us.items()},
-        "stats": {k: st[k] for k in ("removed", "regions", "region_vertices", "max_region",
-                                     "max_local_floods", "heap_spills")},
-        "cpu_baseline": cpu,
-        "e2e": e2e,
         "batch": batch,
         "serve": serve,
+        "roofline": {"bound": "hbm", "kernel": dom + ": " + kernels[dom],
+                     "achieved": dstage["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": dstage["frac"], "traffic": dstage["traffic_bytes"], "peak_kind": kind,
+                     "bytes_per_unit": dstage["bytes_per_unit"], "units": dstage["units"],
+                     "unit_kind": dstage["unit"], "us_per_call": dstage["us"],
+                     "timing": "CUDA events on the context's stream around the stage, per call"},
+        "path_roofline": {"bytes_per_vertex": PATH_BYTES_PER_VERTEX, "achieved": round(path_achieved, 1),
+                          "peak": peak, "unit": "GB/s", "frac": round(path_achieved / peak, 4)},
+        "stages": stages,
+        "stats": {k: st[k] for k in ("removed", "regions", "region_vertices", "max_region",
+                                     "max_local_floods", "heap_spills", "fallback_regions")},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
         "persistence_driven": pers,
         "output_sensitivity": sweep,
         "clocks": clk.summary(),

@@ -212,14 +212,18 @@ void lts_destroy(lts_ctx* ctx);
  * cudaMalloc would fail), or one on a latency-bound path where cudaMalloc and
  * cudaFree (which waits for the whole device) are not acceptable.
  *
- * It computes the order field of Sec. 4.1 alone, i.e. O(v) = the rank of
- * vertex v when the vertices are sorted by (f(v), v), with -0.0 == +0.0;
- * the result equals d_out_order of lts_simplify with every vertex
- * authorized.  It runs the same sort kernels as lts_simplify, but its scratch
- * is a static device array inside the library, sized for at most
- * LTS_ORDER_STATIC_MAX_VERTICES vertices (16.5 MiB), which CUDA allocates
- * once per device when the library's module loads there.  The call makes
- * no cudaMalloc/cudaFree and needs no context.
+ * It computes the order field alone, i.e. O(v) = the rank of vertex v when
+ * the vertices are sorted by (f(v), v), with -0.0 == +0.0; the result equals
+ * d_out_order of lts_simplify with every vertex authorized.  It runs the same
+ * sort kernels as lts_simplify, but its scratch is a static device array
+ * inside the library, sized for at most LTS_ORDER_STATIC_MAX_VERTICES
+ * vertices (16.5 MiB).  CUDA allocates that array once per device when the
+ * library's module is loaded there, and under CUDA's default lazy module
+ * loading that happens at the first use of the module on the device (the
+ * first call of this entry point or of any lts_* call there), not when the
+ * library is opened: a caller that hands the device's free memory to its own
+ * pool must make one call on each device before doing so.  The call makes no
+ * cudaMalloc/cudaFree and needs no context.
  *
  *   device       CUDA device to run on; made current for the call, and the
  *                previously current device is restored before returning
@@ -232,7 +236,8 @@ void lts_destroy(lts_ctx* ctx);
  *
  * Set-up: the first call on each device looks up the scratch's address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins on the device.
+ * before any stream capture begins on the device, and before the device's
+ * free memory is handed to a pool (see above).
  * The call enqueues its kernels on cuda_stream and waits for them (one small
  * read of the status word), so on return d_order is final.
  * Calls on one device share the scratch: calls that overlap in time (from

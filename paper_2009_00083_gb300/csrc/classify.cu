@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kCT) classify_kernel(Geom g, const int* __rest
 template <int DIR>
 cudaError_t classify(Work& w, const Geom& g, const int* O, cudaStream_t s) {
     const long long nblk = (long long)((g.X + kOut - 1) / kOut) * ((g.Y + kWarps - 1) / kWarps) * ((g.Z + kZC - 1) / kZC);
-    const int blocks = (int)std::min<long long>(nblk, 152LL * 8 * 4);
+    const int blocks = (int)std::min<long long>(nblk, (long long)w.sms * 8 * 4);
     classify_kernel<DIR><<<blocks, kCT, 0, s>>>(g, O, w.authbits, w.U, w.parent, w.wait_v, w.spill_n, w.sib_head,
                                                 w.class_cap, w.ctr);
     w.launches += 1;

@@ -167,6 +167,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     w.log_cap = z.log_cap; w.spill_cap = z.spill_cap; w.heap_cap = z.heap_cap; w.lo_cap = z.lo_cap;
     w.nblk = (int)z.nblk;
     w.scan_tmp_cap = (int)z.scan_tiles;
+    w.sms = sms;
     // tests only: LTS_TEST_MIN_TIER=k (1..5) runs step 2 of small regions in tier k
     // (the results do not depend on the tier)
     w.min_tier = 0;

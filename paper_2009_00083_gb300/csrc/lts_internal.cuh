@@ -183,6 +183,7 @@ struct Work {
     PassStats* pstats;                   // [0] minima pass, [1] maxima pass
     DevCounters* h_ctr;                  // pinned host copy (followed by two PassStats)
     int min_tier;                        // tests only: step-2 regions go to at least this tier (0: by size)
+    int sms;                             // multiprocessors of the workspace's device
     int lanes;                           // propagation lanes (threads)
     int class_cap;                       // capacity of the class and region arrays
     long long launches;                  // kernels launched by the current call

@@ -523,7 +523,7 @@ cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int
     cudaMemsetAsync(w.dk_info, 0, 4 * sizeof(unsigned), s);
     {
         long long nch = (n + 15) / 16;
-        int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, 152LL * 8);
+        int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, (long long)w.sms * 8);
         hist_copy_kernel<<<blocks, kThreads, 0, s>>>(f, gout, n, w.sort_hist, st, w.dk_keys, w.dk_cnts, w.dk_info);
     }
     dense_keys_kernel<<<1, 1024, 0, s>>>(w.dk_keys, w.dk_cnts, w.dk_rank, w.dk_info, w.sort_hist, st);
@@ -562,7 +562,7 @@ cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int
                                                             24, w.sort_offsets + 768, w.sort_status,
                                                             w.tile_counter + 3, ep[3], st, dkk, dkr, dki,
                                                             kRoleFourPass);
-    inverse_kernel<<<152 * 8, 256, 0, s>>>(w.keyB, w.valB, O, n);
+    inverse_kernel<<<w.sms * 8, 256, 0, s>>>(w.keyB, w.valB, O, n);
     return cudaGetLastError();
 }
 
@@ -688,10 +688,13 @@ extern "C" lts_status lts_order_field_static(int device, const lts_grid* gr, con
     const int ni = (int)n;
     const int tiles = (int)((n + kTile - 1) / kTile);
 
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0)
+        return st_fail(err, err_len, LTS_ERR_CUDA, "cannot read the device's multiprocessor count");
     cudaMemsetAsync(base, 0, kStZero, s);
     {
         const long long nch = (n + 15) / 16;
-        const int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, 152LL * 8);
+        const int blocks = (int)std::min<long long>((nch + kThreads - 1) / kThreads, (long long)sms * 8);
         hist_copy_kernel<<<blocks, kThreads, 0, s>>>(d_field, reinterpret_cast<float*>(keyB), ni, hist, st, nullptr,
                                                      nullptr, nullptr);
     }
@@ -711,7 +714,7 @@ extern "C" lts_status lts_order_field_static(int device, const lts_grid* gr, con
     onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, keyA, valA, keyB, valB, bins, ni, 24,
                                                             goff + 768, look, ticket + 3, 4u, st, nullptr, nullptr,
                                                             nullptr, kRoleAlways);
-    inverse_kernel<<<152 * 8, 256, 0, s>>>(keyB, valB, d_order, ni);
+    inverse_kernel<<<sms * 8, 256, 0, s>>>(keyB, valB, d_order, ni);
     cudaError_t e = cudaGetLastError();
     int h_status = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, st, sizeof(int), cudaMemcpyDeviceToHost, s);
