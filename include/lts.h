@@ -116,6 +116,10 @@ size_t lts_workspace_bytes(const lts_grid* g);
  * The call enqueues its kernels and then waits for them (one small read of
  * the status word), so on return the outputs are final and the status holds
  * any device-side error (NaN, no authorized extremum, timeout, pool overflow).
+ * When the propagations' queues outgrow a workspace pool (regions covering a
+ * large share of the grid), the call doubles that pool (the larger pool is
+ * kept for later calls) and runs again, up to 3 times; LTS_ERR_OOM remains
+ * when that is not enough or the device has no memory left.
  * Authorized ids outside [0, N) give LTS_ERR_ARG (detected on the device). */
 lts_status lts_simplify(lts_ctx* ctx, const lts_grid* g, const float* d_field,
                         const int32_t* d_authorized, int64_t n_authorized, lts_mode mode,

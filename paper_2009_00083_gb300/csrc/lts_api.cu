@@ -40,6 +40,7 @@ namespace {
 constexpr int kMaxLanes = 16;      // the context's own workspace and up to 15 more
 constexpr int kBatchLanes = 4;     // workspaces a batch spreads over
 constexpr int kRing = 1024;        // serving requests in flight per context
+constexpr int kPoolRetries = 3;    // times a call may enlarge an exhausted flood pool and run again
 
 // A workspace with the stream its work is enqueued on.
 struct Lane {
@@ -116,12 +117,21 @@ size_t bytes_for(const Sizes& z) {
     b += 16 * (size_t)z.n;                          // local adjacency of the largest regions
     b += sizeof(RankBlk) * (size_t)z.nblk + 2 * 4 * (size_t)z.half;
     b += 8 * (size_t)z.scan_tiles + sizeof(DevCounters) + 2 * sizeof(PassStats);
+    b += 256 * 8;                                   // test-only look-back words
     return b;
+}
+
+// tests only: while LTS_TEST_FAIL_ALLOC is set, every device allocation of the
+// library fails as if the device had no memory left
+bool test_alloc_fails() {
+    const char* v = getenv("LTS_TEST_FAIL_ALLOC");
+    return v && v[0] && v[0] != '0';
 }
 
 template <typename T>
 bool dev_alloc(Lane& L, T** p, size_t count) {
     if (L.nallocs >= (int)(sizeof L.allocs / sizeof L.allocs[0])) return false;
+    if (test_alloc_fails()) return false;
     void* q = nullptr;
     if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return false;
     L.allocs[L.nallocs++] = q;
@@ -172,6 +182,8 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     // (the results do not depend on the tier)
     w.min_tier = 0;
     if (const char* mt = getenv("LTS_TEST_MIN_TIER")) w.min_tier = std::max(0, std::min(5, atoi(mt)));
+    // tests only: look-back words that nothing sets (see LTS_TEST_STALL_SORT in order_field.cu)
+    unsigned long long* stall_words = nullptr;
     bool ok = true;
     ok = ok && dev_alloc(L, &w.keyA, z.n) && dev_alloc(L, &w.valA, z.n) && dev_alloc(L, &w.keyB, z.n) &&
          dev_alloc(L, &w.valB, z.n);
@@ -202,6 +214,8 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     w.lo_adj_cap = 4 * z.n + 4096;
     ok = ok && dev_alloc(L, &w.rblk, z.nblk) && dev_alloc(L, &w.sad_att, z.half) && dev_alloc(L, &w.cumA, z.half + 1);
     ok = ok && dev_alloc(L, &w.scan_tmp, z.scan_tiles) && dev_alloc(L, &w.ctr, 1) && dev_alloc(L, &w.pstats, 2);
+    ok = ok && dev_alloc(L, &stall_words, 256);
+    w.test_stall = stall_words;
     if (ok && cudaMallocHost((void**)&w.h_ctr, sizeof(DevCounters) + 2 * sizeof(PassStats)) != cudaSuccess) ok = false;
     if (!ok) {
         cudaGetLastError();
@@ -237,6 +251,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)z.n, s);
     cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), s);
     cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, s);
+    if (stall_words) cudaMemsetAsync(stall_words, 0, 256 * sizeof(unsigned long long), s);
     w.pass_tag = 0;
     cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), s);
     w.epoch = 0;
@@ -349,6 +364,10 @@ __global__ void save_pass_kernel(const DevCounters* ctr, const int* reg_start, P
     ps->total_floods = ctr->total_floods;
     ps->heap_spills = ctr->heap_spills;
     ps->fallbacks = ctr->lo_fallbacks;
+#ifdef LTS_DEBUG_POOLS
+    printf("pools: heap %lld spill %lld log %d regions %d status %d oom %d\n", ctr->heap_cursor, ctr->spill_cursor,
+           ctr->log_cursor, ctr->n_regions, ctr->status, ctr->oom_pool);
+#endif
 }
 
 // the request's final status and pass statistics
@@ -627,6 +646,43 @@ const char* lts_last_error(const lts_ctx* c) { return c ? c->err.c_str() : "null
 
 namespace {
 
+// Replaces one tracked allocation of the lane by a larger one (contents are not kept).
+template <typename T>
+bool regrow(Lane& L, T** p, size_t count) {
+    void* q = nullptr;
+    if (test_alloc_fails()) return false;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    for (int i = 0; i < L.nallocs; ++i)
+        if (L.allocs[i] == static_cast<void*>(*p)) {
+            cudaFree(L.allocs[i]);
+            L.allocs[i] = q;
+            *p = static_cast<T*>(q);
+            return true;
+        }
+    cudaFree(q);
+    return false;
+}
+
+// Doubles the flood overflow-heap pool (pool 1) or the queue spill pool
+// (pool 2, whose offsets are 32-bit) of a workspace.
+bool grow_pool(Lane& L, int pool) {
+    Work& w = L.w;
+    if (cudaStreamSynchronize(L.stream) != cudaSuccess) return false;
+    if (pool == 1) {
+        const long long cap = 2 * w.heap_cap;
+        if (!regrow(L, &w.heap_pool, (size_t)cap)) return false;
+        w.heap_cap = cap;
+        return true;
+    }
+    const long long cap = std::min<long long>(2 * w.spill_cap, (1LL << 31) - 1);
+    if (cap <= w.spill_cap || !regrow(L, &w.spill_pool, (size_t)cap)) return false;
+    w.spill_cap = cap;
+    return true;
+}
+
 lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const float* d_field, const Selection& sel, lts_mode mode,
                         float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats) {
     Lane& L = c->lane[0];
@@ -640,14 +696,28 @@ lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const float* d_field, co
         L.dirty = false;
     }
     const Geom g = geom_of(gr, n);
-    if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, nullptr, 0)) != cudaSuccess)
-        return cuda_fail(c, L, e, "launch");
     Work& w = L.w;
-    cudaMemcpyAsync(w.h_ctr, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
     PassStats* hps = reinterpret_cast<PassStats*>(w.h_ctr + 1);
-    cudaMemcpyAsync(hps, w.pstats, 2 * sizeof(PassStats), cudaMemcpyDeviceToHost, L.stream);
-    if ((e = cudaStreamSynchronize(L.stream)) != cudaSuccess) return cuda_fail(c, L, e, "synchronize");
-    const int status = w.h_ctr->status;
+    int status = 0;
+    for (int attempt = 0;; ++attempt) {
+        if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, nullptr, 0)) !=
+            cudaSuccess)
+            return cuda_fail(c, L, e, "launch");
+        cudaMemcpyAsync(w.h_ctr, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
+        cudaMemcpyAsync(hps, w.pstats, 2 * sizeof(PassStats), cudaMemcpyDeviceToHost, L.stream);
+        if ((e = cudaStreamSynchronize(L.stream)) != cudaSuccess) return cuda_fail(c, L, e, "synchronize");
+        status = w.h_ctr->status;
+        // A flood pool ran out (the propagations' queues outgrew it: regions of a
+        // large share of the grid): enlarge that pool and run the call again.  The
+        // failed run left the workspace clean (fail_clean_kernel) and did not
+        // touch the input.
+        const int pool = w.h_ctr->oom_pool;
+        if (status == LTS_ERR_OOM && (pool == 1 || pool == 2) && attempt < kPoolRetries) {
+            if (!grow_pool(L, pool)) break;
+            continue;
+        }
+        break;
+    }
     if (opt_stats) {
         fill_stats(*opt_stats, n, hps, w.launches);
         fill_stage_times(*opt_stats, L);
@@ -725,7 +795,7 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
         c->batch_dev = nullptr;
         c->batch_host = nullptr;
         c->batch_cap = 0;
-        if (cudaMalloc((void**)&c->batch_dev, nf * sizeof(ReqResult)) != cudaSuccess ||
+        if (test_alloc_fails() || cudaMalloc((void**)&c->batch_dev, nf * sizeof(ReqResult)) != cudaSuccess ||
             cudaMallocHost((void**)&c->batch_host, nf * sizeof(ReqResult)) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, LTS_ERR_OOM, "cannot allocate batch results");

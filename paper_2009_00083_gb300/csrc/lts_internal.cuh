@@ -76,6 +76,8 @@ __device__ __forceinline__ bool failed(const int* st) { return *(volatile const 
 
 // Bounded spin budget for every device-side wait on another block.
 constexpr long long kSpinLimit = 1LL << 26;
+// The budget of the test-only wait that nothing ends (LTS_TEST_STALL_SORT).
+constexpr long long kTestSpinLimit = 1LL << 14;
 
 // Scalars produced and consumed on the device, read back once per call.
 struct DevCounters {
@@ -183,6 +185,7 @@ struct Work {
     PassStats* pstats;                   // [0] minima pass, [1] maxima pass
     DevCounters* h_ctr;                  // pinned host copy (followed by two PassStats)
     int min_tier;                        // tests only: step-2 regions go to at least this tier (0: by size)
+    const unsigned long long* test_stall; // tests only: look-back words nothing sets, or null
     int sms;                             // multiprocessors of the workspace's device
     int lanes;                           // propagation lanes (threads)
     int class_cap;                       // capacity of the class and region arrays

@@ -26,6 +26,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cstdlib>
+
 #include "lts_internal.cuh"
 
 namespace lts {
@@ -308,7 +310,8 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     const float* __restrict__ f, const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
     unsigned* __restrict__ kout, unsigned* __restrict__ vout, unsigned* bin_cursor, int n, int shift,
     const unsigned* __restrict__ goff, unsigned long long* status, unsigned* tile_ctr, unsigned epoch, int* st,
-    const unsigned* __restrict__ dk_keys, const unsigned* __restrict__ dk_rank, const unsigned* dk_info, int role) {
+    const unsigned* __restrict__ dk_keys, const unsigned* __restrict__ dk_rank, const unsigned* dk_info, int role,
+    const unsigned long long* stall = nullptr) {
     __shared__ unsigned s_tile;
     __shared__ unsigned wh[kWarps][256];
     __shared__ unsigned s_gstart[256];
@@ -384,11 +387,14 @@ __global__ void __launch_bounds__(kThreads, 4) onesweep_kernel(
     if (tile > 0) {
         long long t = (long long)tile - 1;
         long long spins = 0;
+        // tests only: with `stall`, tile 1 waits on words that nothing sets, with a short limit
+        const bool stalled = stall != nullptr && tile == 1;
+        const long long limit = stalled ? kTestSpinLimit : kSpinLimit;
         while (t >= 0) {
-            unsigned long long w = vs[t * 256 + d];
+            unsigned long long w = stalled ? *(volatile const unsigned long long*)(stall + d) : vs[t * 256 + d];
             const unsigned e = (unsigned)(w >> 34), fl = (unsigned)(w >> 32) & 3u;
             if (e != epoch || fl == 0u) {
-                if (++spins > kSpinLimit) { set_status(st, LTS_ERR_TIMEOUT); break; }
+                if (++spins > limit) { set_status(st, LTS_ERR_TIMEOUT); break; }
                 continue;
             }
             excl += (unsigned)w;
@@ -543,11 +549,17 @@ cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int
     const unsigned* dkk = w.dk_keys;
     const unsigned* dkr = w.dk_rank;
     const unsigned* dki = w.dk_info;
+    // tests only: while LTS_TEST_STALL_SORT is set, tile 1 of the first digit
+    // pass waits on look-back words that nothing sets, so that its bounded wait
+    // expires (LTS_ERR_TIMEOUT) without any fault
+    const char* stall_env = getenv("LTS_TEST_STALL_SORT");
+    const unsigned long long* stall =
+        (stall_env && stall_env[0] && stall_env[0] != '0') ? w.test_stall : nullptr;
     // digit 0 (both sorts); digit 1: middle pass of the four-pass sort, last
     // pass of the two-pass sort (both write the binned pairs to B); digits 2, 3
     onesweep_kernel<true, false><<<tiles, kThreads, 0, s>>>(f, nullptr, nullptr, w.keyA, w.valA, nullptr, n, 0,
                                                             w.sort_offsets, w.sort_status, w.tile_counter + 0, ep[0],
-                                                            st, dkk, dkr, dki, kRoleAlways);
+                                                            st, dkk, dkr, dki, kRoleAlways, stall);
     onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, w.keyA, w.valA, w.keyB, w.valB, nullptr, n, 8,
                                                              w.sort_offsets + 256, w.sort_status, w.tile_counter + 1,
                                                              ep[1], st, dkk, dkr, dki, kRoleFourPass);

@@ -10,6 +10,7 @@ order field (mode both: minima pass, then maxima pass) with its statistics.
     python tests/golden/make_golden.py mixed_batch_256    # the mixed batch, 256 fields
     python tests/golden/make_golden.py serve_pool_16      # served requests, the first 16
     python tests/golden/make_golden.py pers boxnoise3d_512   # persistence-driven (Sec. 4.5)
+    python tests/golden/make_golden.py sweep 256          # the output-sensitivity sweep (Fig. 6)
 
 The persistence-driven records ({name}_pers.json) hold, for eps = thr * range
 of the field (range = max - min in double precision), the hashes of the
@@ -131,12 +132,37 @@ def main_pers(name):
     print(json.dumps(rec, indent=1))
 
 
+SWEEP_POINTS = (0, 50, 90, 99, 100)
+
+
+def main_sweep(side=256):
+    """The output-sensitivity sweep (Fig. 6): uniform white noise on side^3,
+    a random share p of the vertices left out of an otherwise complete
+    authorized list (workloads.sweep_authorized); the oracle's output hashes
+    and statistics per share (mode both)."""
+    t0 = time.time()
+    f = W.uniform_noise_field((side,) * 3, W.seed_of(5))
+    lists = W.sweep_authorized(f, SWEEP_POINTS, W.seed_of(5, 1))
+    pts = []
+    for p, ids in zip(SWEEP_POINTS, lists):
+        g, O, st = oracle.lts(f, ids, mode="both", return_stats=True)
+        pts.append({"removed_pct": p, "n_authorized": int(ids.size), "g_sha256": W.sha256_of(g),
+                    "order_sha256": W.sha256_of(O), "stats": st})
+    rec = {"workload": f"sweep_{side}", "shape": [side] * 3, "field_sha256": W.sha256_of(f), "points": pts,
+           "oracle_seconds": round(time.time() - t0, 1)}
+    with open(os.path.join(HERE, f"sweep_{side}.json"), "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(f"sweep_{side}", rec["oracle_seconds"], "s")
+
+
 from tests.golden.store import load_authorized, load_record, load_set_authorized  # noqa: E402,F401
 
 
 if __name__ == "__main__":
     if sys.argv[1] == "pers":
         main_pers(sys.argv[2])
+    elif sys.argv[1] == "sweep":
+        main_sweep(int(sys.argv[2]) if len(sys.argv) > 2 else 256)
     elif sys.argv[1] in SETS:
         main_set(sys.argv[1])
     else:
