@@ -17,6 +17,7 @@ Public functions (numpy in, numpy out):
     local_order_trace(...)            Sec. 4.2 step 2 on one vertex set, with every intermediate order
     apply(...)                        Sec. 4.2 steps 3-4 (Eq. 6)
     lts(f, auth_ids, mode)            the whole method
+    order_field_f64(f), lts_f64(f, auth_ids, mode)   the same on a float64 field
     persistent_by_elder(g, O, dir, eps) Sec. 3.3 as Sec. 4.5 selects (Elder rule, one kind)
     pers_select(f, O, dir, eps)       Sec. 4.5 (propagations from every extremum, stopped at eps)
     pers_lts(f, eps, mode)            Sec. 4.5 (Elder-rule selection per pass, then the pass)
@@ -106,6 +107,8 @@ def _get():
         lib.orc_local_orders_rule.argtypes = [ctypes.c_int, P, P, P, P, i64, ctypes.c_int, P, P, P]
         lib.orc_local_order_trace.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
                                               P, P, P, P, ctypes.c_int32, P]
+        lib.orc_order_field_f64.argtypes = [ctypes.c_int, P, P, P]
+        lib.orc_lts_f64.argtypes = [ctypes.c_int, P, P, P, i64, ctypes.c_int, P, P, P]
         lib.orc_lts_rule.argtypes = [ctypes.c_int, P, P, P, i64, ctypes.c_int, P, P, P, ctypes.c_int,
                                      ctypes.c_uint64, ctypes.c_int]
         lib.orc_apply.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P]
@@ -291,6 +294,31 @@ def lts(f, auth_ids, mode="both", method=0, seed=0, return_stats=False, rule="ad
     code = _get().orc_lts_rule(nd, _p(dims), _p(f), _p(ids) if ids.size else None, ids.size, _MODES[mode],
                                _p(g), _p(O), ctypes.byref(st), method, seed, _RULES[rule])
     _check(code, "lts")
+    if return_stats:
+        return g, O, st.as_dict()
+    return g, O
+
+
+def order_field_f64(f):
+    """Sec. 4.1 on a float64 field: rank of every vertex under (value, vertex id)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    nd, dims = _dims(f.shape)
+    O = np.empty(f.shape, dtype=np.int32)
+    _check(_get().orc_order_field_f64(nd, _p(dims), _p(f), _p(O)), "order_field_f64")
+    return O
+
+
+def lts_f64(f, auth_ids, mode="both", return_stats=False):
+    """The whole method on a float64 field: (g float64, O)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    nd, dims = _dims(f.shape)
+    ids = np.ascontiguousarray(np.asarray(auth_ids, dtype=np.int32).reshape(-1))
+    g = np.empty(f.shape, dtype=np.float64)
+    O = np.empty(f.shape, dtype=np.int32)
+    st = Stats()
+    code = _get().orc_lts_f64(nd, _p(dims), _p(f), _p(ids) if ids.size else None, ids.size, _MODES[mode],
+                              _p(g), _p(O), ctypes.byref(st))
+    _check(code, "lts_f64")
     if return_stats:
         return g, O, st.as_dict()
     return g, O

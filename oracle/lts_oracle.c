@@ -11,6 +11,7 @@
  *   - domain, star/link, lower/upper link, critical point index ....... Sec. 3.1
  *   - persistence pairs by the Elder rule (input selector) ............ Sec. 3.3
  *   - order field (sort by value, ties by memory position) ............ Sec. 4.1
+ *     (float32 fields, and float64 fields through orc_lts_f64)
  *   - superlevel set propagation from one maximum (step 1) ............ Sec. 4.2
  *   - hill chains: stop / merge at saddles, queue melding, union-find . Sec. 4.3
  *   - arrival counter of unvisited higher neighbours .................. Sec. 4.4
@@ -256,6 +257,32 @@ int orc_order_field(int ndim, const int64_t* dims, const float* f, int32_t* O) {
     for (int64_t v = 0; v < G.n; ++v) idx[v] = (int32_t)v;
     s_sort_f = f;
     qsort(idx, (size_t)G.n, sizeof(int32_t), cmp_value_then_id);
+    for (int64_t i = 0; i < G.n; ++i) O[idx[i]] = (int32_t)i;
+    free(idx);
+    return ORC_OK;
+}
+
+/* The same for a float64 field. */
+static const double* s_sort_d;
+static int cmp_dvalue_then_id(const void* pa, const void* pb) {
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    double fa = s_sort_d[a], fb = s_sort_d[b];
+    if (fa < fb) return -1;        /* IEEE compare: -0.0 == +0.0 */
+    if (fa > fb) return 1;
+    return (a > b) - (a < b);
+}
+
+int orc_order_field_f64(int ndim, const int64_t* dims, const double* f, int32_t* O) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    for (int64_t v = 0; v < G.n; ++v)
+        if (isnan(f[v])) return ORC_ERR_NAN;
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * G.n);
+    if (!idx) return ORC_ERR_OOM;
+    for (int64_t v = 0; v < G.n; ++v) idx[v] = (int32_t)v;
+    s_sort_d = f;
+    qsort(idx, (size_t)G.n, sizeof(int32_t), cmp_dvalue_then_id);
     for (int64_t i = 0; i < G.n; ++i) O[idx[i]] = (int32_t)i;
     free(idx);
     return ORC_OK;
@@ -1245,9 +1272,11 @@ static int cmp_pair_order(const void* pa, const void* pb) {
     return 0;
 }
 
+/* Values of step 4 (zeta = 0): members take their saddle's value, in
+ * float32 (g_in/g_out) or float64 (g_in64/g_out64, when not NULL). */
 static int apply_pass(const grid_t* G, const int32_t* Od, const int32_t* region_of,
                       const int32_t* reg_saddle, const int32_t* reg_top, const int32_t* lhat,
-                      int32_t* Od_out, const float* g_in, float* g_out) {
+                      int32_t* Od_out, const float* g_in, float* g_out, const double* g_in64, double* g_out64) {
     int64_t n = G->n;
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * n);
     if (!idx) return ORC_ERR_OOM;
@@ -1258,7 +1287,8 @@ static int apply_pass(const grid_t* G, const int32_t* Od, const int32_t* region_
     free(idx);
     for (int64_t v = 0; v < n; ++v) {
         int32_t r = region_of[v];
-        g_out[v] = (r < 0) ? g_in[v] : g_in[reg_saddle[r]];
+        if (g_out64) g_out64[v] = (r < 0) ? g_in64[v] : g_in64[reg_saddle[r]];
+        else g_out[v] = (r < 0) ? g_in[v] : g_in[reg_saddle[r]];
     }
     return ORC_OK;
 }
@@ -1324,14 +1354,14 @@ int orc_apply(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* r
     grid_t G;
     int st = grid_init(&G, ndim, dims);
     if (st) return st;
-    return apply_pass(&G, Od, region_of, reg_saddle, reg_top, lhat, Od_out, g_in, g_out);
+    return apply_pass(&G, Od, region_of, reg_saddle, reg_top, lhat, Od_out, g_in, g_out, NULL, NULL);
 }
 
 /* One pass on (g, O).  dir = +1: maxima pass; dir = -1: minima pass, run as a
  * maxima pass on the mirrored order N-1-O and mirrored back (Sec. 4:
  * minima are processed symmetrically). */
 static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, uint64_t seed, int rule,
-                    float* g, int32_t* O, orc_stats* S) {
+                    float* g, double* g64, int32_t* O, orc_stats* S) {
     int64_t n = G->n;
     int st = ORC_OK;
     int32_t* Od = (int32_t*)malloc(sizeof(int32_t) * n);
@@ -1342,10 +1372,11 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
     int32_t* reg_floods = (int32_t*)malloc(sizeof(int32_t) * n);
     int32_t* reg_fb = (int32_t*)malloc(sizeof(int32_t) * n);
     int32_t* Od2 = (int32_t*)malloc(sizeof(int32_t) * n);
-    float* g2 = (float*)malloc(sizeof(float) * n);
+    float* g2 = g64 ? NULL : (float*)malloc(sizeof(float) * n);
+    double* g2d = g64 ? (double*)malloc(sizeof(double) * n) : NULL;
     int64_t nreg = 0;
     int side = dir > 0 ? 1 : 0;
-    if (!Od || !region_of || !reg_saddle || !reg_top || !lhat || !reg_floods || !reg_fb || !Od2 || !g2) {
+    if (!Od || !region_of || !reg_saddle || !reg_top || !lhat || !reg_floods || !reg_fb || !Od2 || (!g2 && !g2d)) {
         st = ORC_ERR_OOM; goto out;
     }
     for (int64_t v = 0; v < n; ++v) Od[v] = dir > 0 ? O[v] : (int32_t)(n - 1 - O[v]);
@@ -1359,11 +1390,12 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
     if (st) goto out;
     st = local_orders(G, Od, region_of, reg_saddle, nreg, rule, lhat, reg_floods, reg_fb);
     if (st) goto out;
-    st = apply_pass(G, Od, region_of, reg_saddle, reg_top, lhat, Od2, g, g2);
+    st = apply_pass(G, Od, region_of, reg_saddle, reg_top, lhat, Od2, g, g2, g64, g2d);
     if (st) goto out;
     for (int64_t v = 0; v < n; ++v) {
         O[v] = dir > 0 ? Od2[v] : (int32_t)(n - 1 - Od2[v]);
-        g[v] = g2[v];
+        if (g64) g64[v] = g2d[v];
+        else g[v] = g2[v];
     }
     if (S) {
         int64_t mem = 0, maxr = 0;
@@ -1383,7 +1415,7 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
     }
 out:
     free(Od); free(region_of); free(reg_saddle); free(reg_top); free(lhat); free(reg_floods); free(reg_fb);
-    free(Od2); free(g2);
+    free(Od2); free(g2); free(g2d);
     return st;
 }
 
@@ -1407,8 +1439,8 @@ static int lts_rule(int ndim, const int64_t* dims, const float* f, const int32_t
     if (!auth) return ORC_ERR_OOM;
     for (int64_t i = 0; i < n_auth; ++i) auth[auth_ids[i]] = 1;
     memcpy(g, f, sizeof(float) * G.n);
-    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, method, seed, rule, g, O, S);
-    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, method, seed, rule, g, O, S);
+    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, method, seed, rule, g, NULL, O, S);
+    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, method, seed, rule, g, NULL, O, S);
     free(auth);
     return st;
 }
@@ -1416,6 +1448,32 @@ static int lts_rule(int ndim, const int64_t* dims, const float* f, const int32_t
 int orc_lts(int ndim, const int64_t* dims, const float* f, const int32_t* auth_ids, int64_t n_auth,
             int mode, float* g, int32_t* O, orc_stats* S, int method, uint64_t seed) {
     return lts_rule(ndim, dims, f, auth_ids, n_auth, mode, g, O, S, method, seed, ORC_LO_ADOPTED);
+}
+
+/* The whole method on a float64 field: the order field sorts the float64
+ * values (ties by vertex id, -0.0 == +0.0, NaN an error) and members take
+ * their saddle's float64 value; everything else works on the order field and
+ * is the same as for float32. */
+int orc_lts_f64(int ndim, const int64_t* dims, const double* f, const int32_t* auth_ids, int64_t n_auth,
+                int mode, double* g, int32_t* O, orc_stats* S) {
+    grid_t G;
+    int st = grid_init(&G, ndim, dims);
+    if (st) return st;
+    if (mode < ORC_MODE_MIN || mode > ORC_MODE_BOTH) return ORC_ERR_ARG;
+    if (n_auth < 0 || (n_auth > 0 && !auth_ids)) return ORC_ERR_ARG;
+    for (int64_t i = 0; i < n_auth; ++i)
+        if (auth_ids[i] < 0 || auth_ids[i] >= G.n) return ORC_ERR_ARG;
+    if (S) { memset(S, 0, sizeof *S); S->n_vertices = G.n; }
+    st = orc_order_field_f64(ndim, dims, f, O);
+    if (st) return st;
+    uint8_t* auth = (uint8_t*)calloc((size_t)G.n, 1);
+    if (!auth) return ORC_ERR_OOM;
+    for (int64_t i = 0; i < n_auth; ++i) auth[auth_ids[i]] = 1;
+    memcpy(g, f, sizeof(double) * G.n);
+    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, 0, 0, ORC_LO_ADOPTED, NULL, g, O, S);
+    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, 0, 0, ORC_LO_ADOPTED, NULL, g, O, S);
+    free(auth);
+    return st;
 }
 
 /* The whole method under a given step-2 seeding rule (ORC_LO_*), for tests. */
@@ -1438,7 +1496,7 @@ int orc_pass(int ndim, const int64_t* dims, int dir, const int32_t* auth_ids, in
         auth[auth_ids[i]] = 1;
     }
     if (S) { memset(S, 0, sizeof *S); S->n_vertices = G.n; }
-    st = one_pass(&G, dir, auth, method, seed, ORC_LO_ADOPTED, g, O, S);
+    st = one_pass(&G, dir, auth, method, seed, ORC_LO_ADOPTED, g, NULL, O, S);
     free(auth);
     return st;
 }

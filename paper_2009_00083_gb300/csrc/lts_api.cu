@@ -364,10 +364,6 @@ __global__ void save_pass_kernel(const DevCounters* ctr, const int* reg_start, P
     ps->total_floods = ctr->total_floods;
     ps->heap_spills = ctr->heap_spills;
     ps->fallbacks = ctr->lo_fallbacks;
-#ifdef LTS_DEBUG_POOLS
-    printf("pools: heap %lld spill %lld log %d regions %d status %d oom %d\n", ctr->heap_cursor, ctr->spill_cursor,
-           ctr->log_cursor, ctr->n_regions, ctr->status, ctr->oom_pool);
-#endif
 }
 
 // the request's final status and pass statistics
