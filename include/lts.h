@@ -125,6 +125,19 @@ lts_status lts_simplify(lts_ctx* ctx, const lts_grid* g, const float* d_field,
                         const int32_t* d_authorized, int64_t n_authorized, lts_mode mode,
                         float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats);
 
+/* The same as lts_simplify for a float64 field (Sec. 4.1 on float64 values):
+ *   d_field        device float64[N], the input f (not modified)
+ *   d_out_field    device float64[N]: g, every moved vertex takes its saddle's
+ *                  float64 value bit for bit
+ * The order field sorts the float64 values (ties by vertex id, -0.0 equal to
+ * +0.0, a NaN is LTS_ERR_NAN) with a 64-bit radix sort; every later step
+ * works on the order field and is the float32 path's.  The outputs must not
+ * overlap the input or each other (8 bytes per vertex for the fields).
+ * Waiting, pool growth and errors as in lts_simplify. */
+lts_status lts_simplify_f64(lts_ctx* ctx, const lts_grid* g, const double* d_field,
+                            const int32_t* d_authorized, int64_t n_authorized, lts_mode mode,
+                            double* d_out_field, int32_t* d_out_order, lts_stats* opt_stats);
+
 /* Persistence-driven simplification (Sec. 4.5): removes every extremum whose
  * persistence is at most epsilon, with no list of authorized extrema.
  * Each pass (minima, then maxima, as `mode` says) first starts a propagation

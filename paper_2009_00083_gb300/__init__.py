@@ -15,7 +15,8 @@ import os
 __all__ = [
     "LtsGrid", "LtsStats", "LtsError", "Context", "lts_create", "lts_simplify", "lts_destroy",
     "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "lts_simplify_batch", "lts_submit",
-    "lts_poll", "lts_simplify_persistence", "lts_serve_config", "library_path", "load", "simplify", "simplify_persistence",
+    "lts_poll", "lts_simplify_persistence", "lts_simplify_f64", "lts_serve_config", "library_path", "load", "simplify",
+    "simplify_persistence",
     "MODE_MIN", "MODE_MAX", "MODE_BOTH", "ORDER_STATIC_MAX_VERTICES",
 ]
 
@@ -89,6 +90,9 @@ def load():
         lib.lts_simplify.argtypes = [P, ctypes.POINTER(LtsGrid), P, P, ctypes.c_int64, ctypes.c_int, P, P,
                                      ctypes.POINTER(LtsStats)]
         lib.lts_simplify.restype = ctypes.c_int
+        lib.lts_simplify_f64.argtypes = [P, ctypes.POINTER(LtsGrid), P, P, ctypes.c_int64, ctypes.c_int, P, P,
+                                         ctypes.POINTER(LtsStats)]
+        lib.lts_simplify_f64.restype = ctypes.c_int
         lib.lts_simplify_persistence.argtypes = [P, ctypes.POINTER(LtsGrid), P, ctypes.c_double, ctypes.c_int, P, P,
                                                  ctypes.POINTER(LtsStats)]
         lib.lts_simplify_persistence.restype = ctypes.c_int
@@ -148,6 +152,13 @@ def lts_simplify(ctx, grid: LtsGrid, d_field: int, d_authorized: int, n_authoriz
     return load().lts_simplify(ctx, ctypes.byref(grid), ctypes.c_void_p(d_field), ctypes.c_void_p(d_authorized),
                                int(n_authorized), _MODES[mode], ctypes.c_void_p(d_out_field),
                                ctypes.c_void_p(d_out_order), ctypes.byref(stats) if stats is not None else None)
+
+
+def lts_simplify_f64(ctx, grid: LtsGrid, d_field: int, d_authorized: int, n_authorized: int, mode,
+                     d_out_field: int, d_out_order: int, stats: LtsStats | None = None) -> int:
+    return load().lts_simplify_f64(ctx, ctypes.byref(grid), ctypes.c_void_p(d_field), ctypes.c_void_p(d_authorized),
+                                   int(n_authorized), _MODES[mode], ctypes.c_void_p(d_out_field),
+                                   ctypes.c_void_p(d_out_order), ctypes.byref(stats) if stats is not None else None)
 
 
 def lts_simplify_persistence(ctx, grid: LtsGrid, d_field: int, epsilon: float, mode, d_out_field: int,
@@ -232,12 +243,13 @@ class Context:
             pass
 
     def simplify(self, field, authorized, mode="both", out_field=None, out_order=None, with_stats=True):
-        """field: CUDA float32 tensor (Y, X) or (Z, Y, X); authorized: CUDA int32
-        tensor of vertex ids.  Returns (g, order, stats dict or None)."""
+        """field: CUDA float32 or float64 tensor (Y, X) or (Z, Y, X);
+        authorized: CUDA int32 tensor of vertex ids.  Returns (g, order, stats
+        dict or None); g has the field's dtype."""
         import torch
 
-        if field.dtype != torch.float32 or not field.is_cuda or not field.is_contiguous():
-            raise ValueError("field must be a contiguous CUDA float32 tensor")
+        if field.dtype not in (torch.float32, torch.float64) or not field.is_cuda or not field.is_contiguous():
+            raise ValueError("field must be a contiguous CUDA float32 or float64 tensor")
         if authorized.dtype != torch.int32 or not authorized.is_cuda:
             raise ValueError("authorized must be a CUDA int32 tensor")
         authorized = authorized.contiguous()
@@ -245,8 +257,9 @@ class Context:
         g = out_field if out_field is not None else torch.empty_like(field)
         o = out_order if out_order is not None else torch.empty(field.shape, dtype=torch.int32, device=field.device)
         st = LtsStats() if with_stats else None
-        code = lts_simplify(self._ctx, grid, field.data_ptr(), authorized.data_ptr() if authorized.numel() else 0,
-                            authorized.numel(), mode, g.data_ptr(), o.data_ptr(), st)
+        call = lts_simplify_f64 if field.dtype == torch.float64 else lts_simplify
+        code = call(self._ctx, grid, field.data_ptr(), authorized.data_ptr() if authorized.numel() else 0,
+                    authorized.numel(), mode, g.data_ptr(), o.data_ptr(), st)
         if code != 0:
             raise LtsError(code, lts_last_error(self._ctx))
         return g, o, (st.as_dict() if st is not None else None)

@@ -103,7 +103,7 @@ Sizes sizes_for(long long n, int sms) {
 size_t bytes_for(const Sizes& z) {
     size_t b = 0;
     b += 4 * 4 * (size_t)z.n;                       // sort key/value double buffers
-    b += (size_t)z.tiles * 256 * 8 + 4096 * 3;      // look-back words, histograms
+    b += (size_t)z.tiles * 256 * 8 + 8192 * 2 + 32; // look-back words, histograms, digit offsets
     b += 3 * 4 * 8192 + 48;                         // distinct-key table
     b += ((size_t)z.n + 31) / 32 * 4;               // authorized bitmap
     b += 2 * 4 * (size_t)z.n + 8 * (size_t)z.n;     // owner, loc, qmark
@@ -187,8 +187,8 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     bool ok = true;
     ok = ok && dev_alloc(L, &w.keyA, z.n) && dev_alloc(L, &w.valA, z.n) && dev_alloc(L, &w.keyB, z.n) &&
          dev_alloc(L, &w.valB, z.n);
-    ok = ok && dev_alloc(L, &w.sort_status, (size_t)z.tiles * 256) && dev_alloc(L, &w.sort_hist, 1024) &&
-         dev_alloc(L, &w.sort_offsets, 1024) && dev_alloc(L, &w.tile_counter, 8) &&
+    ok = ok && dev_alloc(L, &w.sort_status, (size_t)z.tiles * 256) && dev_alloc(L, &w.sort_hist, 2048) &&
+         dev_alloc(L, &w.sort_offsets, 2048) && dev_alloc(L, &w.tile_counter, 8) &&
          dev_alloc(L, &w.dk_keys, 8192) && dev_alloc(L, &w.dk_cnts, 8192) && dev_alloc(L, &w.dk_rank, 8192) &&
          dev_alloc(L, &w.dk_info, 4) &&
          dev_alloc(L, &w.bin_cursor, 1024);
@@ -328,18 +328,18 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb) {
 }
 
 // Checks one field's arguments; n receives its vertex count.
-lts_status check_field(lts_ctx* c, const lts_grid* gr, long long nmax, const float* d_field,
-                       const int32_t* d_authorized, int64_t n_authorized, lts_mode mode, const float* d_out_field,
-                       const int32_t* d_out_order, long long* n, const std::string& what) {
+lts_status check_field(lts_ctx* c, const lts_grid* gr, long long nmax, const void* d_field,
+                       const int32_t* d_authorized, int64_t n_authorized, lts_mode mode, const void* d_out_field,
+                       const int32_t* d_out_order, long long* n, const std::string& what, int vbytes = 4) {
     if (!grid_ok(gr, n)) return fail(c, LTS_ERR_ARG, what + "invalid grid");
     if (*n > nmax) return fail(c, LTS_ERR_ARG, what + "grid larger than the context's max_vertices");
     if (mode < LTS_MODE_MIN || mode > LTS_MODE_BOTH) return fail(c, LTS_ERR_ARG, what + "invalid mode");
     if (!d_field || !d_out_field || !d_out_order) return fail(c, LTS_ERR_ARG, what + "null data pointer");
     if (n_authorized < 0 || (n_authorized > 0 && !d_authorized))
         return fail(c, LTS_ERR_ARG, what + "invalid authorized list");
-    const size_t nb = (size_t)*n * 4;
-    if (overlap(d_field, nb, d_out_field, nb) || overlap(d_field, nb, d_out_order, nb) ||
-        overlap(d_out_field, nb, d_out_order, nb))
+    const size_t nv = (size_t)*n * vbytes, no = (size_t)*n * 4;
+    if (overlap(d_field, nv, d_out_field, nv) || overlap(d_field, nv, d_out_order, no) ||
+        overlap(d_out_field, nv, d_out_order, no))
         return fail(c, LTS_ERR_ARG, what + "outputs overlap the input or each other");
     return LTS_OK;
 }
@@ -404,8 +404,9 @@ struct Selection {
 // With a persistence selection each pass first runs the propagations from
 // every extremum of its kind (counted in the classification stage), which
 // set the authorized bitmap, and then the pass proper.
-cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const Selection& sel, lts_mode mode,
-                             float* gout, int* O, int sms, ReqResult* res, unsigned long long ticket) {
+cudaError_t enqueue_simplify(Lane& L, const Geom& g, const void* d_field, const Selection& sel, lts_mode mode,
+                             void* gout, int* O, int sms, ReqResult* res, unsigned long long ticket,
+                             bool f64 = false) {
     cudaStream_t s = L.stream;
     Work& w = L.w;
     w.nblk_cur = (g.n + 31) / 32;
@@ -414,7 +415,8 @@ cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const
     w.launches = 0;
     cudaEventRecord(L.ev[0], s);
     if (!sel.by_persistence) build_authbits(w, g, sel.ids, sel.n_ids, s);
-    order_field(w, g, d_field, gout, O, s);
+    if (f64) order_field_f64(w, g, static_cast<const double*>(d_field), static_cast<double*>(gout), O, s);
+    else order_field(w, g, static_cast<const float*>(d_field), static_cast<float*>(gout), O, s);
     cudaEventRecord(L.ev[1], s);
     int evi = 2;
     for (int side = 0; side < 2; ++side) {
@@ -428,10 +430,10 @@ cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const
             cudaMemsetAsync(w.authbits, 0, sizeof(unsigned) * (((size_t)g.n + 31) / 32), s);
             if (side == 0) {
                 classify<-1>(w, g, O, s);
-                select_persistent<-1>(w, g, O, gout, sel.eps, sms, s);
+                select_persistent<-1>(w, g, O, static_cast<const float*>(gout), sel.eps, sms, s);
             } else {
                 classify<1>(w, g, O, s);
-                select_persistent<1>(w, g, O, gout, sel.eps, sms, s);
+                select_persistent<1>(w, g, O, static_cast<const float*>(gout), sel.eps, sms, s);
             }
             pass_reset(w, s);
         }
@@ -457,14 +459,14 @@ cudaError_t enqueue_simplify(Lane& L, const Geom& g, const float* d_field, const
             extract_regions<-1>(w, g, O, sms, s);   cudaEventRecord(L.ev[evi++], s);
             prefix_fork();
             local_orders<-1>(w, g, O, sms, s);      prefix_join(); cudaEventRecord(L.ev[evi++], s);
-            reorder_flatten<-1>(w, g, O, gout, sms, s); cudaEventRecord(L.ev[evi++], s);
+            reorder_flatten<-1>(w, g, O, gout, f64, sms, s); cudaEventRecord(L.ev[evi++], s);
         } else {
             classify<1>(w, g, O, s);                cudaEventRecord(L.ev[evi++], s);
             propagate<1>(w, g, O, sms, s);          cudaEventRecord(L.ev[evi++], s);
             extract_regions<1>(w, g, O, sms, s);    cudaEventRecord(L.ev[evi++], s);
             prefix_fork();
             local_orders<1>(w, g, O, sms, s);       prefix_join(); cudaEventRecord(L.ev[evi++], s);
-            reorder_flatten<1>(w, g, O, gout, sms, s); cudaEventRecord(L.ev[evi++], s);
+            reorder_flatten<1>(w, g, O, gout, f64, sms, s); cudaEventRecord(L.ev[evi++], s);
         }
         save_pass_kernel<<<1, 1, 0, s>>>(w.ctr, w.reg_start, w.pstats + side);
         w.launches += 1;
@@ -679,11 +681,12 @@ bool grow_pool(Lane& L, int pool) {
     return true;
 }
 
-lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const float* d_field, const Selection& sel, lts_mode mode,
-                        float* d_out_field, int32_t* d_out_order, lts_stats* opt_stats) {
+lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const void* d_field, const Selection& sel, lts_mode mode,
+                        void* d_out_field, int32_t* d_out_order, lts_stats* opt_stats, bool f64 = false) {
     Lane& L = c->lane[0];
     long long n;
-    lts_status st = check_field(c, gr, L.nmax, d_field, sel.ids, sel.n_ids, mode, d_out_field, d_out_order, &n, "");
+    lts_status st = check_field(c, gr, L.nmax, d_field, sel.ids, sel.n_ids, mode, d_out_field, d_out_order, &n, "",
+                                f64 ? 8 : 4);
     if (st != LTS_OK) return st;
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
     cudaError_t e;
@@ -696,7 +699,7 @@ lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const float* d_field, co
     PassStats* hps = reinterpret_cast<PassStats*>(w.h_ctr + 1);
     int status = 0;
     for (int attempt = 0;; ++attempt) {
-        if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, nullptr, 0)) !=
+        if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, nullptr, 0, f64)) !=
             cudaSuccess)
             return cuda_fail(c, L, e, "launch");
         cudaMemcpyAsync(w.h_ctr, w.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, L.stream);
@@ -733,6 +736,15 @@ lts_status lts_simplify(lts_ctx* c, const lts_grid* gr, const float* d_field, co
     c->err.clear();
     const Selection sel{d_authorized, n_authorized, false, 0.0};
     return simplify_one(c, gr, d_field, sel, mode, d_out_field, d_out_order, opt_stats);
+}
+
+lts_status lts_simplify_f64(lts_ctx* c, const lts_grid* gr, const double* d_field, const int32_t* d_authorized,
+                            int64_t n_authorized, lts_mode mode, double* d_out_field, int32_t* d_out_order,
+                            lts_stats* opt_stats) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    const Selection sel{d_authorized, n_authorized, false, 0.0};
+    return simplify_one(c, gr, d_field, sel, mode, d_out_field, d_out_order, opt_stats, true);
 }
 
 lts_status lts_simplify_persistence(lts_ctx* c, const lts_grid* gr, const float* d_field, double epsilon,

@@ -136,8 +136,8 @@ struct Work {
     // order field (radix sort)
     unsigned int* keyA; unsigned int* valA; unsigned int* keyB; unsigned int* valB;
     unsigned long long* sort_status;     // tiles x 256 look-back words
-    unsigned int* sort_hist;             // 4 x 256
-    unsigned int* sort_offsets;          // 4 x 256
+    unsigned int* sort_hist;             // 8 x 256 (digits of a 64-bit key; 4 for float32 fields)
+    unsigned int* sort_offsets;          // 8 x 256
     unsigned int* tile_counter;          // 4
     unsigned int* bin_cursor;            // id bins of the last radix pass
     unsigned int* dk_keys; unsigned int* dk_cnts; unsigned int* dk_rank;   // distinct keys (hash table)
@@ -194,6 +194,7 @@ struct Work {
 
 // ---- launch helpers (defined in the .cu files) ----
 cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int* O, cudaStream_t s);
+cudaError_t order_field_f64(Work& w, const Geom& g, const double* f, double* gout, int* O, cudaStream_t s);
 cudaError_t build_authbits(Work& w, const Geom& g, const int* ids, long long nids, cudaStream_t s);
 template <int DIR>
 cudaError_t classify(Work& w, const Geom& g, const int* O, cudaStream_t s);
@@ -208,7 +209,7 @@ template <int DIR>
 cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
 cudaError_t reorder_prefix(Work& w, const Geom& g, int sms, cudaStream_t s);
 template <int DIR>
-cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms, cudaStream_t s);
+cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, void* gout, bool f64, int sms, cudaStream_t s);
 cudaError_t pass_reset(Work& w, cudaStream_t s);
 int local_order_tiny_max();
 int local_order_med_max();

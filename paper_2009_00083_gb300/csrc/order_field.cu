@@ -25,6 +25,7 @@
 // other path are launched too and return at once.
 #include <cstdio>
 #include <mutex>
+#include <utility>
 
 #include <cstdlib>
 
@@ -276,6 +277,52 @@ __global__ void __launch_bounds__(1024) dense_keys_kernel(const unsigned* __rest
     __syncthreads();
     for (int i = threadIdx.x; i < 512; i += blockDim.x) hist[i] = (&s_h[0][0])[i];
     if (threadIdx.x == 0) dk_info[kDkMode] = 1;
+}
+
+// float64 fields: IEEE order as unsigned 64-bit order; -0.0 is folded onto +0.0.
+__device__ __forceinline__ unsigned long long order_key64(double x, int* st) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    if ((u & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) set_status(st, LTS_ERR_NAN);
+    if (u == 0x8000000000000000ull) u = 0ull;
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// float64 fields: copies f to g, writes (low word of the key, id) as the
+// first sort's pairs and the high word of the key by id, and counts the
+// eight byte digits of the key (low word: digits 0-3, high word: 4-7).
+__global__ void __launch_bounds__(kThreads) hist64_kernel(const double* __restrict__ f, double* __restrict__ gout,
+                                                          int n, unsigned* __restrict__ keys, unsigned* __restrict__ vals,
+                                                          unsigned* __restrict__ hi, unsigned* __restrict__ hist,
+                                                          int* st) {
+    __shared__ unsigned sh[8][256];
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double x = __ldcs(f + i);
+        __stcs(gout + i, x);
+        const unsigned long long k = order_key64(x, st);
+        const unsigned lo = (unsigned)k, h = (unsigned)(k >> 32);
+        __stcs(keys + i, lo);
+        __stcs(vals + i, (unsigned)i);
+        __stcs(hi + i, h);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            atomicAdd(&sh[d][(lo >> (8 * d)) & 255u], 1u);
+            atomicAdd(&sh[4 + d][(h >> (8 * d)) & 255u], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) {
+        const unsigned v = (&sh[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// keys[i] = hi[vals[i]]: the high words in the order of the sort by low words.
+__global__ void gather_hi_kernel(const unsigned* __restrict__ vals, const unsigned* __restrict__ hi,
+                                 unsigned* __restrict__ keys, int n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        keys[i] = __ldg(hi + __ldcs(vals + i));
 }
 
 // Exclusive prefix of each digit's histogram: global start of every bucket.
@@ -575,6 +622,64 @@ cudaError_t order_field(Work& w, const Geom& g, const float* f, float* gout, int
                                                             w.tile_counter + 3, ep[3], st, dkk, dkr, dki,
                                                             kRoleFourPass);
     inverse_kernel<<<w.sms * 8, 256, 0, s>>>(w.keyB, w.valB, O, n);
+    return cudaGetLastError();
+}
+
+// The order field of a float64 field: an LSD radix sort of the 64-bit order
+// keys with the vertex ids, as two stable 32-bit sorts (four 8-bit digit
+// passes each): first by the low words, then, after the high words are
+// gathered in that order, by the high words; ties keep the id order.  The
+// last pass bins (id, rank) pairs like the float32 sort.  The high words are
+// kept in the member-region array, unused until the passes.
+cudaError_t order_field_f64(Work& w, const Geom& g, const double* f, double* gout, int* O, cudaStream_t s) {
+    const int n = g.n;
+    const int tiles = (n + kTile - 1) / kTile;
+    int* st = &w.ctr->status;
+    unsigned* hi = reinterpret_cast<unsigned*>(w.member_reg);
+    cudaMemsetAsync(w.sort_hist, 0, 2048 * sizeof(unsigned), s);
+    cudaMemsetAsync(w.tile_counter, 0, 8 * sizeof(unsigned), s);
+    {
+        const int blocks = (int)std::min<long long>(((long long)n + kThreads - 1) / kThreads, (long long)w.sms * 8);
+        hist64_kernel<<<blocks, kThreads, 0, s>>>(f, gout, n, w.keyA, w.valA, hi, w.sort_hist, st);
+    }
+    digit_offsets_kernel<<<8, 256, 0, s>>>(w.sort_hist, w.sort_offsets);
+    const int nbins = (int)(((unsigned)n + (1u << kBinShift) - 1) >> kBinShift);
+    bin_init_kernel<<<(nbins + 255) / 256, 256, 0, s>>>(w.bin_cursor, nbins);
+    w.launches += 3;
+    unsigned ep[8];
+    for (int p = 0; p < 8; ++p) {
+        ep[p] = ++w.epoch;
+        if (w.epoch >= (1u << 30) - 8) {   // epoch wrap: clear the look-back words
+            cudaMemsetAsync(w.sort_status, 0, (size_t)w.max_tiles * 256 * sizeof(unsigned long long), s);
+            w.epoch = 1;
+            ep[p] = 1;
+        }
+    }
+    unsigned* ka = w.keyA; unsigned* va = w.valA; unsigned* kb = w.keyB; unsigned* vb = w.valB;
+    for (int p = 0; p < 8; ++p) {
+        if (p == 4) {
+            // the low words are sorted (pairs in A): sort on the high words next
+            gather_hi_kernel<<<w.sms * 8, 256, 0, s>>>(va, hi, ka, n);
+            w.launches += 1;
+        }
+        const int shift = 8 * (p & 3);
+        if (p < 7)
+            onesweep_kernel<false, false><<<tiles, kThreads, 0, s>>>(nullptr, ka, va, kb, vb, nullptr, n, shift,
+                                                                     w.sort_offsets + 256 * p, w.sort_status,
+                                                                     w.tile_counter + p, ep[p], st, nullptr, nullptr,
+                                                                     nullptr, kRoleAlways);
+        else
+            onesweep_kernel<false, true><<<tiles, kThreads, 0, s>>>(nullptr, ka, va, kb, vb, w.bin_cursor, n, shift,
+                                                                    w.sort_offsets + 256 * p, w.sort_status,
+                                                                    w.tile_counter + p, ep[p], st, nullptr, nullptr,
+                                                                    nullptr, kRoleAlways);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    w.launches += 8;
+    // after eight passes the binned (id, rank) pairs are in A again (ka, va)
+    inverse_kernel<<<w.sms * 8, 256, 0, s>>>(ka, va, O, n);
+    w.launches += 1;
     return cudaGetLastError();
 }
 

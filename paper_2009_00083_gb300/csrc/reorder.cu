@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(kT) stream_kernel(int n, int* O, const RankBlk
 
 // one thread per member (CSR position); the first threads also reset the
 // saddles' claims
-template <int DIR>
-__global__ void members_place_kernel(int n, int* O, float* gout, int* owner, const int* __restrict__ members,
+template <int DIR, typename T>
+__global__ void members_place_kernel(int n, int* O, T* gout, int* owner, const int* __restrict__ members,
                                      const int* __restrict__ member_reg, const int* __restrict__ lhat,
                                      const int* __restrict__ reg_saddle, const int* __restrict__ reg_sod,
                                      const int* __restrict__ reg_place, const int* __restrict__ reg_start,
@@ -181,17 +181,24 @@ cudaError_t reorder_prefix(Work& w, const Geom& g, int sms, cudaStream_t s) {
 }
 
 template <int DIR>
-cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, float* gout, int sms, cudaStream_t s) {
+cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, void* gout, bool f64, int sms, cudaStream_t s) {
     stream_kernel<DIR><<<sms * 8, kT, 0, s>>>(g.n, O, w.rblk, w.cumA, w.ctr);
-    members_place_kernel<DIR><<<sms * 8, 256, 0, s>>>(g.n, O, gout, w.owner, w.members, w.member_reg, w.lhat,
-                                                      w.reg_saddle, w.reg_sod, w.reg_place, w.reg_start, w.rblk,
-                                                      w.cumA, w.ctr);
+    if (f64)
+        members_place_kernel<DIR, double><<<sms * 8, 256, 0, s>>>(g.n, O, static_cast<double*>(gout), w.owner,
+                                                                  w.members, w.member_reg, w.lhat, w.reg_saddle,
+                                                                  w.reg_sod, w.reg_place, w.reg_start, w.rblk,
+                                                                  w.cumA, w.ctr);
+    else
+        members_place_kernel<DIR, float><<<sms * 8, 256, 0, s>>>(g.n, O, static_cast<float*>(gout), w.owner,
+                                                                 w.members, w.member_reg, w.lhat, w.reg_saddle,
+                                                                 w.reg_sod, w.reg_place, w.reg_start, w.rblk,
+                                                                 w.cumA, w.ctr);
     saddles_reset_kernel<<<sms * 4, 256, 0, s>>>(w.owner, w.cnt, w.reg_saddle, w.ctr);
     w.launches += 3;
     return cudaGetLastError();
 }
 
-template cudaError_t reorder_flatten<1>(Work&, const Geom&, int*, float*, int, cudaStream_t);
-template cudaError_t reorder_flatten<-1>(Work&, const Geom&, int*, float*, int, cudaStream_t);
+template cudaError_t reorder_flatten<1>(Work&, const Geom&, int*, void*, bool, int, cudaStream_t);
+template cudaError_t reorder_flatten<-1>(Work&, const Geom&, int*, void*, bool, int, cudaStream_t);
 
 }  // namespace lts

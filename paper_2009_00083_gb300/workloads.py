@@ -46,8 +46,9 @@ def _coords(n):
     return np.arange(n, dtype=np.float64) / float(n - 1)
 
 
-def gaussian_field(shape, K, noise, seed, sigma=(0.05, 0.15), amp=(0.5, 1.0)):
-    """sum_k a_k exp(-|p - c_k|^2 / (2 sigma_k^2)) + U[-noise, noise], float64 -> float32.
+def gaussian_field(shape, K, noise, seed, sigma=(0.05, 0.15), amp=(0.5, 1.0), dtype=np.float32):
+    """sum_k a_k exp(-|p - c_k|^2 / (2 sigma_k^2)) + U[-noise, noise], computed in
+    float64 and returned as `dtype` (float32 unless asked for float64).
 
     Draw order: centres (K x d), sigma (K), |a| (K), signs (K), noise (N, x fastest).
     Coordinates are idx / (dim - 1), so the extent is the unit square or cube."""
@@ -71,7 +72,7 @@ def gaussian_field(shape, K, noise, seed, sigma=(0.05, 0.15), amp=(0.5, 1.0)):
             term = parts[2][:, None, None] * parts[1][None, :, None] * parts[0][None, None, :]
         f += sign[k] * mag[k] * term
     f += eps.reshape(shape)
-    return f.astype(np.float32)
+    return f.astype(dtype)
 
 
 def _box_sum_axis(a, axis, r):
