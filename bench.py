@@ -257,30 +257,70 @@ def whole_job_mvps(n, world, ms):
     return world * n / (ms / 1e3) / 1e6
 
 
-def _load_set(name, make_field, specs):
-    """Fields of a stored multi-field workload (hash-checked) and their authorized lists."""
+def _load_set(name, make_field, specs, keep=None):
+    """Fields of a stored multi-field workload (hash-checked) and their
+    authorized lists; with `keep`, only those field indices (in that order)."""
     from tests.golden import store as mg
 
     rec = mg.load_record(name)
     auth = mg.load_set_authorized(name)
+    idx = list(range(len(specs))) if keep is None else list(keep)
     fields = []
-    for spec, fr in zip(specs, rec["fields"]):
-        f = make_field(spec)
-        if W.sha256_of(f) != fr["field_sha256"]:
+    for i in idx:
+        f = make_field(specs[i])
+        if W.sha256_of(f) != rec["fields"][i]["field_sha256"]:
             raise RuntimeError(f"{name}: generated field does not match the stored hash")
         fields.append(f)
-    return rec, fields, auth
+    return ({"fields": [rec["fields"][i] for i in idx]}, fields, [auth[i] for i in idx])
 
 
-def batch_leg(lts, torch, dev, reps=3):
+class _Ranks:
+    """This process's rank in a multi-GPU run (dist None: one rank)."""
+
+    def __init__(self, dist, rank, world, dev):
+        self.dist, self.rank, self.world, self.dev = dist, rank, world, dev
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def reduce(self, x, op):
+        """max / min / sum over the ranks of a float."""
+        if self.dist is None:
+            return x
+        import torch
+
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.dev)
+        self.dist.all_reduce(t, op={"max": self.dist.ReduceOp.MAX, "min": self.dist.ReduceOp.MIN,
+                                    "sum": self.dist.ReduceOp.SUM}[op])
+        return float(t.item())
+
+    def gather(self, obj):
+        if self.dist is None:
+            return [obj]
+        out = [None] * self.world
+        self.dist.all_gather_object(out, obj)
+        return out
+
+
+def batch_leg(lts, torch, dev, reps=3, ranks=None):
     """The 256-field batch (2D squares of side 64..1024 and 3D cubes of side
     32..160, 125.6 Mvertices): one plain lts_simplify per field against one
     lts_simplify_batch call; inputs resident on the device; wall clock around
-    synchronized calls, median of `reps` after one warm-up."""
-    rec, fs, auth = _load_set("mixed_batch_256", W.batch_field, W.batch_specs(256))
+    synchronized calls, median of `reps` after one warm-up.  With several
+    ranks the fields are sharded by field (sharding.shard_fields: largest
+    first to the least loaded rank), each rank runs its share, and the time
+    is the slowest rank's (no collective on the data path)."""
+    from paper_2009_00083_gb300 import sharding
+
+    ranks = ranks or _Ranks(None, 0, 1, dev)
+    specs = W.batch_specs(256)
+    sizes = [int(np.prod(sp["shape"])) for sp in specs]
+    mine = sharding.shard_fields(sizes, ranks.world)[ranks.rank]
+    rec, fs, auth = _load_set("mixed_batch_256", W.batch_field, specs, keep=mine)
     fields = [torch.from_numpy(f).to(dev) for f in fs]
     ids = [torch.from_numpy(a).to(dev) for a in auth]
-    total = sum(f.numel() for f in fields)
+    total = sum(sizes)
     ctx = lts.Context(max(f.numel() for f in fields), device=dev.index)
     outs = [(torch.empty_like(f), torch.empty(f.shape, dtype=torch.int32, device=dev)) for f in fields]
     grids = [lts.grid_of_shape(tuple(f.shape)) for f in fields]
@@ -298,32 +338,38 @@ def batch_leg(lts, torch, dev, reps=3):
 
     def timed(fn):
         torch.cuda.synchronize(dev)
+        ranks.barrier()
         t = time.perf_counter()
         fn()
         torch.cuda.synchronize(dev)
-        n_reps = reps if time.perf_counter() - t < 3.0 else 1     # keep the leg bounded
+        first = ranks.reduce(time.perf_counter() - t, "max")
+        n_reps = reps if first < 3.0 else 1     # keep the leg bounded
         ts = []
         for _ in range(n_reps):
             torch.cuda.synchronize(dev)
+            ranks.barrier()
             t = time.perf_counter()
             fn()
             torch.cuda.synchronize(dev)
-            ts.append(time.perf_counter() - t)
+            ts.append(ranks.reduce(time.perf_counter() - t, "max"))
         return statistics.median(ts)
 
     tp = timed(plain)
     tb = timed(batched)
     parity = all(W.sha256_of(o.cpu().numpy()) == fr["order_sha256"] and W.sha256_of(g.cpu().numpy()) == fr["g_sha256"]
                  for (g, o), fr in zip(outs, rec["fields"]))
+    parity = ranks.reduce(1.0 if parity else 0.0, "min") == 1.0
     ctx.close()
     return {"workload": "mixed_batch_256: 128 2D squares (side 64..1024) + 128 3D cubes (side 32..160)",
-            "fields": len(fields), "vertices": total, "plain_mvps": round(total / tp / 1e6, 1),
+            "fields": len(specs), "vertices": total, "plain_mvps": round(total / tp / 1e6, 1),
             "batched_mvps": round(total / tb / 1e6, 1), "plain_ms": round(tp * 1e3, 2),
             "batched_ms": round(tb * 1e3, 2), "parity_vs_oracle": bool(parity),
-            "timing": "wall clock around synchronized calls, median of up to 3 after a warm-up, inputs on the device"}
+            "ranks": ranks.world, "sharding": "by field, largest first to the least loaded rank",
+            "timing": "wall clock around synchronized calls (slowest rank), median of up to 3 after a warm-up, "
+                      "inputs on the device"}
 
 
-def _serve_run(lts, torch, dev, ctx, fields, ids, grids, arrivals, max_inflight, max_submit_s):
+def _serve_run(lts, torch, dev, ctx, fields, ids, grids, arrivals, max_inflight, max_submit_s, pool_idx=None):
     """Submits request i at arrivals[i] (seconds; None: as soon as fewer than
     max_inflight are in flight), polls every request, returns (latency
     seconds per submitted request, submitted count, errors, overloaded,
@@ -343,7 +389,7 @@ def _serve_run(lts, torch, dev, ctx, fields, ids, grids, arrivals, max_inflight,
             overloaded = True
         while (i < nreq and not overloaded and len(pending) < max_inflight
                and (not open_loop or arrivals[i] <= now)):
-            k = i % len(fields)
+            k = pool_idx[i] if pool_idx is not None else i % len(fields)
             g, o = torch.empty_like(fields[k]), torch.empty(fields[k].shape, dtype=torch.int32, device=dev)
             code, t = lts.lts_submit(ctx._ctx, grids[k], fields[k].data_ptr(), ids[k].data_ptr(), ids[k].numel(),
                                      "both", g.data_ptr(), o.data_ptr())
@@ -365,7 +411,7 @@ def _serve_run(lts, torch, dev, ctx, fields, ids, grids, arrivals, max_inflight,
 
 
 def serve_leg(lts, torch, dev, nreq=2000, warm=100, rate=200.0, max_inflight=64, max_submit_s=30.0,
-              closed_requests=320):
+              closed_requests=320, ranks=None):
     """Served requests from a pool of the first 16 requests of the served
     workload (3D cubes of side 32..256, cycled), inputs resident on the device,
     through lts_submit / lts_poll on up to 15 serving workspaces side by side.
@@ -375,7 +421,13 @@ def serve_leg(lts, torch, dev, nreq=2000, warm=100, rate=200.0, max_inflight=64,
     - scheduled arrival, the first `warm` excluded).  If the device cannot
     keep up (`max_inflight` requests in flight) or submission takes longer
     than `max_submit_s`, submission stops and the run is marked overloaded.
-    (3) When (2) is overloaded, the same at 80% of the measured capacity."""
+    (3) When (2) is overloaded, the same at 80% of the measured capacity.
+    With several ranks, request i goes to rank i mod world (sharding by
+    request: no collective on the data path); capacities add up, and the
+    latencies of every rank are pooled for the percentiles."""
+    from paper_2009_00083_gb300 import sharding
+
+    ranks = ranks or _Ranks(None, 0, 1, dev)
     specs = W.serve_specs(16)
     rec, fs, auth = _load_set("serve_pool_16", W.serve_field, specs)
     fields = [torch.from_numpy(f).to(dev) for f in fs]
@@ -389,18 +441,30 @@ def serve_leg(lts, torch, dev, nreq=2000, warm=100, rate=200.0, max_inflight=64,
             ctx.simplify(f, a, "both", with_stats=False)
         _serve_run(lts, torch, dev, ctx, fields, ids, grids, [None] * 32, max_inflight, 1e9)
         torch.cuda.synchronize(dev)
-        lat, done, err_c, _, wall = _serve_run(lts, torch, dev, ctx, fields, ids, grids, [None] * closed_requests,
+        ranks.barrier()
+        n_closed = max(1, closed_requests // ranks.world)
+        lat, done, err_c, _, wall = _serve_run(lts, torch, dev, ctx, fields, ids, grids, [None] * n_closed,
                                                max_inflight, 1e9)
-        cap_rps = done / wall
-        cap = {"requests": done, "in_flight": max_inflight, "seconds": round(wall, 3),
-               "requests_per_s": round(cap_rps, 2),
-               "mvps": round(sum(sizes[j % len(sizes)] for j in range(done)) / wall / 1e6, 3), "errors": int(err_c)}
+        cap_rps = ranks.reduce(done / wall, "sum")
+        cap_mvps = ranks.reduce(sum(sizes[j % len(sizes)] for j in range(done)) / wall / 1e6, "sum")
+        cap = {"requests": int(ranks.reduce(done, "sum")), "in_flight": max_inflight,
+               "seconds": round(ranks.reduce(wall, "max"), 3), "requests_per_s": round(cap_rps, 2),
+               "mvps": round(cap_mvps, 3), "errors": int(ranks.reduce(err_c, "sum"))}
 
         def open_run(r, count):
             arr = W.serve_arrivals(count, r)
-            lat, sub, errs, over, _ = _serve_run(lts, torch, dev, ctx, fields, ids, grids, list(arr), max_inflight,
-                                                 max_submit_s)
-            served = lat[warm:] * 1e3 if sub > warm else lat * 1e3
+            mine = sharding.route_requests(count, ranks.world)[ranks.rank]
+            ranks.barrier()
+            lat, sub, errs, over, _ = _serve_run(lts, torch, dev, ctx, fields, ids, grids, [arr[i] for i in mine],
+                                                 max_inflight, max_submit_s, pool_idx=[i % len(fields) for i in mine])
+            parts = ranks.gather((mine[:sub], list(lat), int(sub), int(errs), bool(over)))
+            all_lat = np.full(count, np.nan)
+            for idx, ls, _, _, _ in parts:
+                all_lat[np.asarray(idx, dtype=np.int64)] = ls
+            sub = sum(p[2] for p in parts)
+            errs = sum(p[3] for p in parts)
+            over = any(p[4] for p in parts)
+            served = all_lat[warm:] * 1e3
             served = served[~np.isnan(served)]
             pct = (lambda q: round(float(np.percentile(served, q)), 3)) if served.size else (lambda q: None)
             return {"rate_hz": round(r, 2), "requests": count, "submitted": int(sub), "warmup_excluded": warm,
@@ -417,6 +481,7 @@ def serve_leg(lts, torch, dev, nreq=2000, warm=100, rate=200.0, max_inflight=64,
     return {"workload": "serve_3d: 3D cubes of side 32..256 (pool of 16 cycled), inputs on the device",
             "admission": "up to 15 serving workspaces of 256^3 side by side, HBM budget 120 GiB",
             "mean_vertices": int(np.mean([sizes[j % len(sizes)] for j in range(nreq)])),
+            "ranks": ranks.world, "routing": "request i to rank i mod world",
             "capacity": cap, "poisson": main_run, "poisson_at_80pct_capacity": sustained}
 
 
@@ -579,6 +644,10 @@ def main():
                "h2d_bytes_per_step": int(f.nbytes + ids.nbytes), "d2h_bytes_per_step": int(2 * f.nbytes),
                "ms_per_step": round(ms_e2e, 3)}
 
+    # the batch and served workloads shard by field over every rank
+    ranks = _Ranks(dist, rank, world, dev)
+    batch = None if args.no_batch else batch_leg(lts, torch, dev, ranks=ranks)
+    serve = None if args.no_serve else serve_leg(lts, torch, dev, ranks=ranks)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -605,8 +674,6 @@ def main():
                "classify": "classify_kernel (both passes)", "reorder": "reorder and flatten (both passes)"}
     path_achieved = PATH_BYTES_PER_VERTEX * n / (ms * 1e-3) / 1e9
     cpu = None if args.no_cpu_baseline else cpu_baseline()
-    batch = None if args.no_batch or world > 1 else batch_leg(lts, torch, dev)
-    serve = None if args.no_serve or world > 1 else serve_leg(lts, torch, dev)
     pers = None if args.no_pers or world > 1 else pers_leg(lts, torch, ctx, fd, f, args.workload)
     sweep = None if args.no_sweep or world > 1 else sweep_leg(lts, torch, dev)
     out = {
