@@ -40,7 +40,10 @@ _lib = None
 
 OK, ERR_ARG, ERR_NAN, ERR_NO_AUTHORIZED, ERR_OOM, ERR_INTERNAL, ERR_CYCLE = 0, 1, 2, 3, 4, 7, 8
 MODE_MIN, MODE_MAX, MODE_BOTH = 1, 2, 3
-_MODES = {"min": MODE_MIN, "max": MODE_MAX, "both": MODE_BOTH}
+MODE_RESTORE = 4
+_MODES = {"min": MODE_MIN, "max": MODE_MAX, "both": MODE_BOTH,
+          "min+restore": MODE_MIN | MODE_RESTORE, "max+restore": MODE_MAX | MODE_RESTORE,
+          "both+restore": MODE_BOTH | MODE_RESTORE}
 # step-2 seeding rules: the adopted one (the paper's alternation, all-boundary
 # seeds only for a region where it does not end), the paper's alternation
 # alone (ERR_CYCLE where it does not end), all-boundary seeds alone
@@ -64,6 +67,7 @@ class Stats(ctypes.Structure):
         ("pad", ctypes.c_int32),
         ("total_local_floods", ctypes.c_int64 * 2),
         ("fallback_regions", ctypes.c_int64 * 2),
+        ("restored", ctypes.c_int64 * 2),
     ]
 
     def as_dict(self):
@@ -80,6 +84,7 @@ class Stats(ctypes.Structure):
             "total_local_floods_max": self.total_local_floods[1],
             "fallback_regions_min": self.fallback_regions[0],
             "fallback_regions_max": self.fallback_regions[1],
+            "restored_min": self.restored[0], "restored_max": self.restored[1],
         }
 
 

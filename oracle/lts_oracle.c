@@ -49,6 +49,10 @@
  *   - the numerical perturbation uses zeta = 0: every region vertex takes the
  *     saddle's value bit for bit;
  *   - one minima pass, then one maxima pass;
+ *   - the optional restoration of swallowed authorized extrema (Sec. 4.2
+ *     step 3, mode flag ORC_MODE_RESTORE): each one moves below the other
+ *     vertices of its region's block, in increasing order, unless that would
+ *     leave one of its neighbours without a higher neighbour (a new maximum);
  *   - persistence-driven selection (Sec. 4.5): eps is absolute; the tracked
  *     difference is f(m) - f(v) (minima pass: f(v) - f(m)) for the class's
  *     highest extremum m and the vertex v about to be taken, in double
@@ -72,6 +76,7 @@
 #define ORC_MODE_MIN 1
 #define ORC_MODE_MAX 2
 #define ORC_MODE_BOTH 3
+#define ORC_MODE_RESTORE 4   /* or-ed into the mode: restore swallowed authorized extrema */
 
 typedef struct {
     int64_t n_vertices;
@@ -83,6 +88,7 @@ typedef struct {
     int32_t pad;
     int64_t total_local_floods[2];
     int64_t fallback_regions[2]; /* regions step 2 redid with all-boundary seeds            */
+    int64_t restored[2];         /* swallowed authorized extrema restored (mode RESTORE)     */
 } orc_stats;
 
 /* ------------------------------------------------------------------------ */
@@ -1244,6 +1250,106 @@ out:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Optional post-process of step 3 (Sec. 4.2): restoring authorized extrema   */
+/* of the other kind that a region swallowed.  In the maxima pass a region R  */
+/* can contain authorized minima of the pass's input order; all their         */
+/* neighbours lie in R (they are higher than the minimum, hence above s and   */
+/* connected to it), and the local order of step 2 makes none of them a       */
+/* minimum.  The paper restores such a minimum by making it smaller than all  */
+/* its neighbours.  Read here as: the swallowed authorized minima of R are    */
+/* taken in increasing order; each one moves below every vertex of the block  */
+/* of R (below the ones already restored: they are never adjacent), unless a  */
+/* neighbour u of it would then have no higher neighbour left (u would become */
+/* a maximum, an unauthorized extremum, breaking Eq. 1); such a minimum stays */
+/* swallowed.  Vertices outside R next to a vertex of R other than s are      */
+/* below the block of R, so only s and the vertices of R can be higher.       */
+/* lhat is renumbered: the restored vertices first, the others in their order.*/
+/* Returns the number of restored vertices (added to *restored).              */
+/* ------------------------------------------------------------------------ */
+static int restore_swallowed(const grid_t* G, const int32_t* Od, const uint8_t* auth, const int32_t* region_of,
+                             const int32_t* reg_saddle, int64_t nreg, int32_t* lhat, int64_t* restored) {
+    int64_t n = G->n;
+    int st = ORC_OK;
+    int64_t* key = (int64_t*)malloc(sizeof(int64_t) * n);
+    int32_t* cand = NULL;
+    int32_t* newr = NULL;
+    int64_t* start = (int64_t*)calloc((size_t)nreg + 1, sizeof(int64_t));
+    int32_t* members = (int32_t*)malloc(sizeof(int32_t) * (n + 1));
+    if (!key || !start || !members) { st = ORC_ERR_OOM; goto out; }
+    for (int64_t v = 0; v < n; ++v) if (region_of[v] >= 0) start[region_of[v] + 1]++;
+    for (int64_t r = 0; r < nreg; ++r) start[r + 1] += start[r];
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nreg + 1));
+        if (!fill) { st = ORC_ERR_OOM; goto out; }
+        memcpy(fill, start, sizeof(int64_t) * ((size_t)nreg + 1));
+        for (int64_t v = 0; v < n; ++v) if (region_of[v] >= 0) members[fill[region_of[v]]++] = (int32_t)v;
+        free(fill);
+    }
+    cand = (int32_t*)malloc(sizeof(int32_t) * (n + 1));
+    newr = (int32_t*)malloc(sizeof(int32_t) * (n + 1));
+    if (!cand || !newr) { st = ORC_ERR_OOM; goto out; }
+    for (int64_t r = 0; r < nreg; ++r) {
+        int32_t m = (int32_t)(start[r + 1] - start[r]);
+        const int32_t* mem = members + start[r];
+        int32_t s = reg_saddle[r];
+        /* the swallowed authorized minima of R, in increasing order */
+        int32_t k = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            int32_t w = mem[i];
+            if (!auth[w]) continue;
+            int32_t nb[14];
+            int kn = nbrs(G, w, nb), ismin = 1;
+            for (int j = 0; j < kn; ++j) if (Od[nb[j]] < Od[w]) { ismin = 0; break; }
+            if (ismin) cand[k++] = w;
+        }
+        if (k == 0) continue;
+        for (int32_t i = 1; i < k; ++i) {             /* insertion sort by Od */
+            int32_t w = cand[i], j = i - 1;
+            while (j >= 0 && Od[cand[j]] > Od[w]) { cand[j + 1] = cand[j]; --j; }
+            cand[j + 1] = w;
+        }
+        for (int32_t i = 0; i < m; ++i) key[mem[i]] = lhat[mem[i]];
+        int32_t done = 0;
+        for (int32_t c = 0; c < k; ++c) {
+            int32_t w = cand[c];
+            int32_t nbw[14];
+            int kw = nbrs(G, w, nbw), ok = 1;
+            for (int j = 0; j < kw && ok; ++j) {
+                int32_t u = nbw[j];
+                int32_t nbu[14];
+                int ku = nbrs(G, u, nbu), higher = 0;
+                for (int t = 0; t < ku && !higher; ++t) {
+                    int32_t x = nbu[t];
+                    if (x == w) continue;
+                    if (x == s) higher = 1;
+                    else if (region_of[x] == r && key[x] > key[u]) higher = 1;
+                }
+                if (!higher) ok = 0;
+            }
+            if (ok) key[w] = INT64_MIN + done++;     /* below the block, above the earlier restored ones */
+        }
+        if (done == 0) continue;
+        /* renumber: restored first (in the order they were restored), then the
+         * others in their order (lhat minus the restored ones below them) */
+        for (int32_t i = 0; i < m; ++i) {
+            int32_t v = mem[i];
+            if (key[v] < 0) continue;
+            int32_t below = 0;
+            for (int32_t c = 0; c < k; ++c) if (key[cand[c]] < 0 && lhat[cand[c]] < lhat[v]) ++below;
+            newr[i] = done + lhat[v] - below;
+        }
+        for (int32_t i = 0; i < m; ++i) {
+            int32_t v = mem[i];
+            lhat[v] = key[v] < 0 ? (int32_t)(key[v] - INT64_MIN) : newr[i];
+        }
+        *restored += done;
+    }
+out:
+    free(key); free(cand); free(newr); free(start); free(members);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Step 3 (Sec. 4.2, Eq. 6): new global order.  Sort key                     */
 /*   non-member u (saddles included): (Od(u), 1, 0, 0)                        */
 /*   member v of region R:            (Od(s_R), 0, Od(top_R), lhat(v))        */
@@ -1361,7 +1467,7 @@ int orc_apply(int ndim, const int64_t* dims, const int32_t* Od, const int32_t* r
  * maxima pass on the mirrored order N-1-O and mirrored back (Sec. 4:
  * minima are processed symmetrically). */
 static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, uint64_t seed, int rule,
-                    float* g, double* g64, int32_t* O, orc_stats* S) {
+                    int restore, float* g, double* g64, int32_t* O, orc_stats* S) {
     int64_t n = G->n;
     int st = ORC_OK;
     int32_t* Od = (int32_t*)malloc(sizeof(int32_t) * n);
@@ -1390,6 +1496,12 @@ static int one_pass(const grid_t* G, int dir, const uint8_t* auth, int method, u
     if (st) goto out;
     st = local_orders(G, Od, region_of, reg_saddle, nreg, rule, lhat, reg_floods, reg_fb);
     if (st) goto out;
+    if (restore) {
+        int64_t nres = 0;
+        st = restore_swallowed(G, Od, auth, region_of, reg_saddle, nreg, lhat, &nres);
+        if (st) goto out;
+        if (S) S->restored[side] = nres;
+    }
     st = apply_pass(G, Od, region_of, reg_saddle, reg_top, lhat, Od2, g, g2, g64, g2d);
     if (st) goto out;
     for (int64_t v = 0; v < n; ++v) {
@@ -1428,7 +1540,7 @@ static int lts_rule(int ndim, const int64_t* dims, const float* f, const int32_t
     grid_t G;
     int st = grid_init(&G, ndim, dims);
     if (st) return st;
-    if (mode < ORC_MODE_MIN || mode > ORC_MODE_BOTH) return ORC_ERR_ARG;
+    if ((mode & ~ORC_MODE_RESTORE) < ORC_MODE_MIN || (mode & ~ORC_MODE_RESTORE) > ORC_MODE_BOTH) return ORC_ERR_ARG;
     if (n_auth < 0 || (n_auth > 0 && !auth_ids)) return ORC_ERR_ARG;
     for (int64_t i = 0; i < n_auth; ++i)
         if (auth_ids[i] < 0 || auth_ids[i] >= G.n) return ORC_ERR_ARG;
@@ -1439,8 +1551,9 @@ static int lts_rule(int ndim, const int64_t* dims, const float* f, const int32_t
     if (!auth) return ORC_ERR_OOM;
     for (int64_t i = 0; i < n_auth; ++i) auth[auth_ids[i]] = 1;
     memcpy(g, f, sizeof(float) * G.n);
-    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, method, seed, rule, g, NULL, O, S);
-    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, method, seed, rule, g, NULL, O, S);
+    const int restore = (mode & ORC_MODE_RESTORE) != 0;
+    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, method, seed, rule, restore, g, NULL, O, S);
+    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, method, seed, rule, restore, g, NULL, O, S);
     free(auth);
     return st;
 }
@@ -1459,7 +1572,7 @@ int orc_lts_f64(int ndim, const int64_t* dims, const double* f, const int32_t* a
     grid_t G;
     int st = grid_init(&G, ndim, dims);
     if (st) return st;
-    if (mode < ORC_MODE_MIN || mode > ORC_MODE_BOTH) return ORC_ERR_ARG;
+    if ((mode & ~ORC_MODE_RESTORE) < ORC_MODE_MIN || (mode & ~ORC_MODE_RESTORE) > ORC_MODE_BOTH) return ORC_ERR_ARG;
     if (n_auth < 0 || (n_auth > 0 && !auth_ids)) return ORC_ERR_ARG;
     for (int64_t i = 0; i < n_auth; ++i)
         if (auth_ids[i] < 0 || auth_ids[i] >= G.n) return ORC_ERR_ARG;
@@ -1470,8 +1583,9 @@ int orc_lts_f64(int ndim, const int64_t* dims, const double* f, const int32_t* a
     if (!auth) return ORC_ERR_OOM;
     for (int64_t i = 0; i < n_auth; ++i) auth[auth_ids[i]] = 1;
     memcpy(g, f, sizeof(double) * G.n);
-    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, 0, 0, ORC_LO_ADOPTED, NULL, g, O, S);
-    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, 0, 0, ORC_LO_ADOPTED, NULL, g, O, S);
+    const int restore = (mode & ORC_MODE_RESTORE) != 0;
+    if (mode & ORC_MODE_MIN) st = one_pass(&G, -1, auth, 0, 0, ORC_LO_ADOPTED, restore, NULL, g, O, S);
+    if (!st && (mode & ORC_MODE_MAX)) st = one_pass(&G, +1, auth, 0, 0, ORC_LO_ADOPTED, restore, NULL, g, O, S);
     free(auth);
     return st;
 }
@@ -1496,7 +1610,7 @@ int orc_pass(int ndim, const int64_t* dims, int dir, const int32_t* auth_ids, in
         auth[auth_ids[i]] = 1;
     }
     if (S) { memset(S, 0, sizeof *S); S->n_vertices = G.n; }
-    st = one_pass(&G, dir, auth, method, seed, ORC_LO_ADOPTED, g, NULL, O, S);
+    st = one_pass(&G, dir, auth, method, seed, ORC_LO_ADOPTED, 0, g, NULL, O, S);
     free(auth);
     return st;
 }
