@@ -56,7 +56,17 @@ typedef enum {
 typedef enum {
     LTS_MODE_MIN = 1,           /* minima pass only                 */
     LTS_MODE_MAX = 2,           /* maxima pass only                 */
-    LTS_MODE_BOTH = 3           /* minima pass, then maxima pass    */
+    LTS_MODE_BOTH = 3,          /* minima pass, then maxima pass    */
+    /* Flag or-ed into one of the above: the optional post-process of Sec. 4.2
+     * step 3 that restores authorized extrema of the other kind swallowed by
+     * a region (an authorized minimum inside a region of the maxima pass, an
+     * authorized maximum inside one of the minima pass).  Each one, in
+     * increasing order of the pass, is moved below every other vertex of its
+     * region's block (above the region's block in the minima pass), unless a
+     * neighbour of it would then have no higher (lower) neighbour, i.e. would
+     * become a new, unauthorized extremum; then it stays swallowed.  Values
+     * are not changed (members already take the saddle's value). */
+    LTS_MODE_RESTORE = 4
 } lts_mode;
 
 typedef struct {
@@ -86,6 +96,8 @@ typedef struct {
                                  /* says, did not end (a cycle), and which were    */
                                  /* redone with every vertex of R other than s     */
                                  /* that has an outside neighbour as a seed         */
+    int64_t restored[2];         /* swallowed authorized extrema restored           */
+                                 /* (LTS_MODE_RESTORE)                              */
 } lts_stats;
 
 /* Creates a context on CUDA device `device` whose workspace fits grids of up

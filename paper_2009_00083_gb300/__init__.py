@@ -25,7 +25,10 @@ library_path = os.path.join(_HERE, "liblts.so")
 
 MODE_MIN, MODE_MAX, MODE_BOTH = 1, 2, 3
 ORDER_STATIC_MAX_VERTICES = 1 << 20   # LTS_ORDER_STATIC_MAX_VERTICES
-_MODES = {"min": MODE_MIN, "max": MODE_MAX, "both": MODE_BOTH, 1: 1, 2: 2, 3: 3}
+MODE_RESTORE = 4   # LTS_MODE_RESTORE, or-ed into a mode
+_MODES = {"min": MODE_MIN, "max": MODE_MAX, "both": MODE_BOTH, 1: 1, 2: 2, 3: 3,
+          "min+restore": MODE_MIN | MODE_RESTORE, "max+restore": MODE_MAX | MODE_RESTORE,
+          "both+restore": MODE_BOTH | MODE_RESTORE, 5: 5, 6: 6, 7: 7}
 STATUS = {0: "LTS_OK", 1: "LTS_ERR_ARG", 2: "LTS_ERR_NAN", 3: "LTS_ERR_NO_AUTHORIZED", 4: "LTS_ERR_OOM",
           5: "LTS_ERR_CUDA", 6: "LTS_ERR_TIMEOUT", 7: "LTS_ERR_INTERNAL"}
 
@@ -47,6 +50,7 @@ class LtsStats(ctypes.Structure):
         ("stage_us", ctypes.c_float * 8),
         ("kernel_launches", ctypes.c_int64),
         ("fallback_regions", ctypes.c_int64 * 2),
+        ("restored", ctypes.c_int64 * 2),
     ]
 
     def as_dict(self):
@@ -59,6 +63,7 @@ class LtsStats(ctypes.Structure):
             "heap_spills": list(self.heap_spills),
             "launches": int(self.kernel_launches),
             "fallback_regions": list(self.fallback_regions),
+            "restored": list(self.restored),
             "stage_us": {k: round(float(v), 2) for k, v in zip(
                 ["order_field", "classify", "propagate", "regions", "local_order", "reorder", "total"],
                 list(self.stage_us)[:7])},

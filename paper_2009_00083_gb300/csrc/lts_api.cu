@@ -205,7 +205,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
          dev_alloc(L, &w.reg_saddle, z.half) && dev_alloc(L, &w.reg_size, z.half) &&
          dev_alloc(L, &w.reg_start, z.half + 1) && dev_alloc(L, &w.reg_top, z.half) &&
          dev_alloc(L, &w.reg_sod, z.half) && dev_alloc(L, &w.reg_place, z.half) && dev_alloc(L, &w.reg_head, z.half) &&
-         dev_alloc(L, &w.reg_att, z.half) && dev_alloc(L, &w.reg_floods, z.half);
+         dev_alloc(L, &w.reg_att, z.half) && dev_alloc(L, &w.reg_swallowed, z.half);
     ok = ok && dev_alloc(L, &w.members, z.n) && dev_alloc(L, &w.lhat, z.n) && dev_alloc(L, &w.tier_list, 2 * z.half) &&
          dev_alloc(L, &w.member_reg, z.n);
     ok = ok && dev_alloc(L, &w.lo_v, z.lo_cap) && dev_alloc(L, &w.lo_L, z.lo_cap) && dev_alloc(L, &w.lo_L2, z.lo_cap) &&
@@ -333,7 +333,8 @@ lts_status check_field(lts_ctx* c, const lts_grid* gr, long long nmax, const voi
                        const int32_t* d_out_order, long long* n, const std::string& what, int vbytes = 4) {
     if (!grid_ok(gr, n)) return fail(c, LTS_ERR_ARG, what + "invalid grid");
     if (*n > nmax) return fail(c, LTS_ERR_ARG, what + "grid larger than the context's max_vertices");
-    if (mode < LTS_MODE_MIN || mode > LTS_MODE_BOTH) return fail(c, LTS_ERR_ARG, what + "invalid mode");
+    if ((mode & ~LTS_MODE_RESTORE) < LTS_MODE_MIN || (mode & ~LTS_MODE_RESTORE) > LTS_MODE_BOTH)
+        return fail(c, LTS_ERR_ARG, what + "invalid mode");
     if (!d_field || !d_out_field || !d_out_order) return fail(c, LTS_ERR_ARG, what + "null data pointer");
     if (n_authorized < 0 || (n_authorized > 0 && !d_authorized))
         return fail(c, LTS_ERR_ARG, what + "invalid authorized list");
@@ -364,6 +365,7 @@ __global__ void save_pass_kernel(const DevCounters* ctr, const int* reg_start, P
     ps->total_floods = ctr->total_floods;
     ps->heap_spills = ctr->heap_spills;
     ps->fallbacks = ctr->lo_fallbacks;
+    ps->restored = ctr->n_restored;
 }
 
 // the request's final status and pass statistics
@@ -458,14 +460,18 @@ cudaError_t enqueue_simplify(Lane& L, const Geom& g, const void* d_field, const 
             propagate<-1>(w, g, O, sms, s);         cudaEventRecord(L.ev[evi++], s);
             extract_regions<-1>(w, g, O, sms, s);   cudaEventRecord(L.ev[evi++], s);
             prefix_fork();
-            local_orders<-1>(w, g, O, sms, s);      prefix_join(); cudaEventRecord(L.ev[evi++], s);
+            local_orders<-1>(w, g, O, sms, s);      prefix_join();
+            if (mode & LTS_MODE_RESTORE) restore_swallowed<-1>(w, g, O, sms, s);
+            cudaEventRecord(L.ev[evi++], s);
             reorder_flatten<-1>(w, g, O, gout, f64, sms, s); cudaEventRecord(L.ev[evi++], s);
         } else {
             classify<1>(w, g, O, s);                cudaEventRecord(L.ev[evi++], s);
             propagate<1>(w, g, O, sms, s);          cudaEventRecord(L.ev[evi++], s);
             extract_regions<1>(w, g, O, sms, s);    cudaEventRecord(L.ev[evi++], s);
             prefix_fork();
-            local_orders<1>(w, g, O, sms, s);       prefix_join(); cudaEventRecord(L.ev[evi++], s);
+            local_orders<1>(w, g, O, sms, s);       prefix_join();
+            if (mode & LTS_MODE_RESTORE) restore_swallowed<1>(w, g, O, sms, s);
+            cudaEventRecord(L.ev[evi++], s);
             reorder_flatten<1>(w, g, O, gout, f64, sms, s); cudaEventRecord(L.ev[evi++], s);
         }
         save_pass_kernel<<<1, 1, 0, s>>>(w.ctr, w.reg_start, w.pstats + side);
@@ -492,6 +498,7 @@ void fill_stats(lts_stats& o, long long n, const PassStats* ps, long long launch
         o.total_local_floods[k] = ps[k].total_floods;
         o.heap_spills[k] = ps[k].heap_spills;
         o.fallback_regions[k] = ps[k].fallbacks;
+        o.restored[k] = ps[k].restored;
     }
     o.kernel_launches = launches;
 }

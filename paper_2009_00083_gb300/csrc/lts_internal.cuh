@@ -105,6 +105,8 @@ struct DevCounters {
     int n_tasks;           // propagation tasks left after the first step
     long long lo_adj_cursor; // local adjacency pool of the largest local-order tier (ints)
     int lo_fallbacks;      // regions step 2 redid with every boundary vertex as a seed
+    int n_rs_regions;      // regions with swallowed authorized extrema (restoration)
+    long long n_restored;  // swallowed authorized extrema restored
 };
 
 __device__ __forceinline__ void set_oom(DevCounters* ctr, int pool) {
@@ -114,7 +116,7 @@ __device__ __forceinline__ void set_oom(DevCounters* ctr, int pool) {
 
 // Per-pass statistics accumulated into the host stats.
 struct PassStats {
-    long long removed, regions, region_vertices, max_region, max_floods, total_floods, heap_spills, fallbacks;
+    long long removed, regions, region_vertices, max_region, max_floods, total_floods, heap_spills, fallbacks, restored;
 };
 
 // Rank-space block of 32 ranks (16 bytes, one vector load): members and
@@ -162,7 +164,8 @@ struct Work {
     int* vlog; long long log_cap;
     // regions
     int* class2reg; int* reg_class; int* reg_saddle; int* reg_size; int* reg_start;
-    int* reg_top; int* reg_sod; int* reg_place; int* reg_head; int* reg_att; int* reg_floods;
+    int* reg_top; int* reg_sod; int* reg_place; int* reg_head; int* reg_att;
+    int* reg_swallowed;                  // per region: swallowed authorized extrema (restoration)
     int* members; int* lhat; int* member_reg;   // CSR members, their local order, their region
     int* tier_list;                      // [0,cap): 16-lane tier; then quarters of cap: 32-lane, dense <=128, dense <=1024, HBM
     // local-order scratch (slots: members + one saddle per region)
@@ -207,6 +210,8 @@ template <int DIR>
 cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
 template <int DIR>
 cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
+template <int DIR>
+cudaError_t restore_swallowed(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
 cudaError_t reorder_prefix(Work& w, const Geom& g, int sms, cudaStream_t s);
 template <int DIR>
 cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, void* gout, bool f64, int sms, cudaStream_t s);
