@@ -150,6 +150,25 @@ lts_status lts_simplify_f64(lts_ctx* ctx, const lts_grid* g, const double* d_fie
                             const int32_t* d_authorized, int64_t n_authorized, lts_mode mode,
                             double* d_out_field, int32_t* d_out_order, lts_stats* opt_stats);
 
+/* Critical points of an order field (Sec. 3.1), e.g. to check the output of
+ * lts_simplify against Eq. 1: for every vertex, the number of connected
+ * components of its lower link and of its upper link in the Freudenthal
+ * triangulation.  Interior vertices are classified with a table of their
+ * lower-neighbour pattern (2^6 or 2^14 entries, built per context); vertices
+ * on the grid boundary count components over their present neighbours.
+ *   d_order    device int32[N]: an injective order (e.g. d_out_order)
+ *   d_lower    device int8[N] or NULL: lower link components per vertex
+ *   d_upper    device int8[N] or NULL: upper link components per vertex
+ *   counts     host int64[6]: minima (no lower link), maxima (no upper link),
+ *              regular vertices (both connected), saddles (the rest), and the
+ *              sums over the vertices of (lower components - 1) and of
+ *              (upper components - 1) where positive (join and split
+ *              saddle multiplicities)
+ * Synchronous on the context's stream.  Errors: LTS_ERR_ARG (grid, sizes,
+ * NULL or overlapping pointers), LTS_ERR_CUDA. */
+lts_status lts_classify(lts_ctx* ctx, const lts_grid* g, const int32_t* d_order, int8_t* d_lower, int8_t* d_upper,
+                        int64_t* counts);
+
 /* Persistence-driven simplification (Sec. 4.5): removes every extremum whose
  * persistence is at most epsilon, with no list of authorized extrema.
  * Each pass (minima, then maxima, as `mode` says) first starts a propagation

@@ -15,7 +15,8 @@ import os
 __all__ = [
     "LtsGrid", "LtsStats", "LtsError", "Context", "lts_create", "lts_simplify", "lts_destroy",
     "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "lts_simplify_batch", "lts_submit",
-    "lts_poll", "lts_simplify_persistence", "lts_simplify_f64", "lts_serve_config", "library_path", "load", "simplify",
+    "lts_poll", "lts_simplify_persistence", "lts_simplify_f64", "lts_classify", "lts_serve_config", "library_path",
+    "load", "simplify",
     "simplify_persistence",
     "MODE_MIN", "MODE_MAX", "MODE_BOTH", "ORDER_STATIC_MAX_VERTICES",
 ]
@@ -95,6 +96,8 @@ def load():
         lib.lts_simplify.argtypes = [P, ctypes.POINTER(LtsGrid), P, P, ctypes.c_int64, ctypes.c_int, P, P,
                                      ctypes.POINTER(LtsStats)]
         lib.lts_simplify.restype = ctypes.c_int
+        lib.lts_classify.argtypes = [P, ctypes.POINTER(LtsGrid), P, P, P, ctypes.POINTER(ctypes.c_int64)]
+        lib.lts_classify.restype = ctypes.c_int
         lib.lts_simplify_f64.argtypes = [P, ctypes.POINTER(LtsGrid), P, P, ctypes.c_int64, ctypes.c_int, P, P,
                                          ctypes.POINTER(LtsStats)]
         lib.lts_simplify_f64.restype = ctypes.c_int
@@ -157,6 +160,15 @@ def lts_simplify(ctx, grid: LtsGrid, d_field: int, d_authorized: int, n_authoriz
     return load().lts_simplify(ctx, ctypes.byref(grid), ctypes.c_void_p(d_field), ctypes.c_void_p(d_authorized),
                                int(n_authorized), _MODES[mode], ctypes.c_void_p(d_out_field),
                                ctypes.c_void_p(d_out_order), ctypes.byref(stats) if stats is not None else None)
+
+
+def lts_classify(ctx, grid: LtsGrid, d_order: int, d_lower: int = 0, d_upper: int = 0):
+    """Returns (status, counts): minima, maxima, regular, saddles, join and
+    split saddle multiplicities."""
+    counts = (ctypes.c_int64 * 6)()
+    code = load().lts_classify(ctx, ctypes.byref(grid), ctypes.c_void_p(d_order), ctypes.c_void_p(d_lower or None),
+                               ctypes.c_void_p(d_upper or None), counts)
+    return int(code), list(counts)
 
 
 def lts_simplify_f64(ctx, grid: LtsGrid, d_field: int, d_authorized: int, n_authorized: int, mode,

@@ -118,6 +118,7 @@ size_t bytes_for(const Sizes& z) {
     b += sizeof(RankBlk) * (size_t)z.nblk + 2 * 4 * (size_t)z.half;
     b += 8 * (size_t)z.scan_tiles + sizeof(DevCounters) + 2 * sizeof(PassStats);
     b += 256 * 8;                                   // test-only look-back words
+    b += 64 + (1 << 14) + 6 * 8;                    // link tables, critical point counts
     return b;
 }
 
@@ -215,6 +216,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     ok = ok && dev_alloc(L, &w.rblk, z.nblk) && dev_alloc(L, &w.sad_att, z.half) && dev_alloc(L, &w.cumA, z.half + 1);
     ok = ok && dev_alloc(L, &w.scan_tmp, z.scan_tiles) && dev_alloc(L, &w.ctr, 1) && dev_alloc(L, &w.pstats, 2);
     ok = ok && dev_alloc(L, &stall_words, 256);
+    ok = ok && dev_alloc(L, &w.link6, 64) && dev_alloc(L, &w.link14, 1 << 14) && dev_alloc(L, &w.crit_counts, 6);
     w.test_stall = stall_words;
     if (ok && cudaMallocHost((void**)&w.h_ctr, sizeof(DevCounters) + 2 * sizeof(PassStats)) != cudaSuccess) ok = false;
     if (!ok) {
@@ -252,6 +254,7 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), s);
     cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, s);
     if (stall_words) cudaMemsetAsync(stall_words, 0, 256 * sizeof(unsigned long long), s);
+    build_link_tables(w.link6, w.link14, s);
     w.pass_tag = 0;
     cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), s);
     w.epoch = 0;
@@ -752,6 +755,32 @@ lts_status lts_simplify_f64(lts_ctx* c, const lts_grid* gr, const double* d_fiel
     c->err.clear();
     const Selection sel{d_authorized, n_authorized, false, 0.0};
     return simplify_one(c, gr, d_field, sel, mode, d_out_field, d_out_order, opt_stats, true);
+}
+
+lts_status lts_classify(lts_ctx* c, const lts_grid* gr, const int32_t* d_order, int8_t* d_lower, int8_t* d_upper,
+                        int64_t* counts) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    Lane& L = c->lane[0];
+    long long n;
+    if (!grid_ok(gr, &n)) return fail(c, LTS_ERR_ARG, "invalid grid");
+    if (n > L.nmax) return fail(c, LTS_ERR_ARG, "grid larger than the context's max_vertices");
+    if (!d_order || !counts) return fail(c, LTS_ERR_ARG, "null pointer");
+    if ((d_lower && overlap(d_lower, (size_t)n, d_order, (size_t)n * 4)) ||
+        (d_upper && overlap(d_upper, (size_t)n, d_order, (size_t)n * 4)) ||
+        (d_lower && d_upper && overlap(d_lower, (size_t)n, d_upper, (size_t)n)))
+        return fail(c, LTS_ERR_ARG, "outputs overlap the order field or each other");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
+    Work& w = L.w;
+    const Geom g = geom_of(gr, n);
+    cudaError_t e = critical_points(w, g, d_order, reinterpret_cast<signed char*>(d_lower),
+                                    reinterpret_cast<signed char*>(d_upper), w.crit_counts, L.stream);
+    unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, w.crit_counts, sizeof h, cudaMemcpyDeviceToHost, L.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+    if (e != cudaSuccess) return cuda_fail(c, L, e, "classify");
+    for (int i = 0; i < 6; ++i) counts[i] = (int64_t)h[i];
+    return LTS_OK;
 }
 
 lts_status lts_simplify_persistence(lts_ctx* c, const lts_grid* gr, const float* d_field, double epsilon,

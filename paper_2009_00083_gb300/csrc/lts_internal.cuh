@@ -190,6 +190,8 @@ struct Work {
     int min_tier;                        // tests only: step-2 regions go to at least this tier (0: by size)
     const unsigned long long* test_stall; // tests only: look-back words nothing sets, or null
     int sms;                             // multiprocessors of the workspace's device
+    unsigned char* link6; unsigned char* link14;   // link component tables of interior vertices (2D, 3D)
+    unsigned long long* crit_counts;     // critical point counts of lts_classify
     int lanes;                           // propagation lanes (threads)
     int class_cap;                       // capacity of the class and region arrays
     long long launches;                  // kernels launched by the current call
@@ -213,6 +215,9 @@ cudaError_t local_orders(Work& w, const Geom& g, const int* O, int sms, cudaStre
 template <int DIR>
 cudaError_t restore_swallowed(Work& w, const Geom& g, const int* O, int sms, cudaStream_t s);
 cudaError_t reorder_prefix(Work& w, const Geom& g, int sms, cudaStream_t s);
+cudaError_t build_link_tables(unsigned char* t6, unsigned char* t14, cudaStream_t s);
+cudaError_t critical_points(Work& w, const Geom& g, const int* O, signed char* lower, signed char* upper,
+                            unsigned long long* d_counts, cudaStream_t s);
 template <int DIR>
 cudaError_t reorder_flatten(Work& w, const Geom& g, int* O, void* gout, bool f64, int sms, cudaStream_t s);
 cudaError_t pass_reset(Work& w, cudaStream_t s);
