@@ -196,9 +196,12 @@ lts_status lts_simplify_persistence(lts_ctx* ctx, const lts_grid* g, const float
  * at a time, and batching is this library's addition).  Array arguments
  * hold one entry per field, with the meaning they have in lts_simplify;
  * every field must fit the context's max_vertices.  The fields are spread
- * over the context's workspace and up to 3 more (allocated on first use,
- * each sized for the largest field of the batch, kept for later batches),
- * each on its own stream, largest fields first; the extra streams start
+ * over the context's workspace and up to 31 more (allocated on first use
+ * while the device keeps 1 GiB free beyond them, each sized for the largest
+ * field of the batch, kept for later batches), each on its own stream,
+ * largest fields first; LTS_ERR_OOM if not even one more fits.  (Streams
+ * beyond the process's CUDA_DEVICE_MAX_CONNECTIONS hardware queues share
+ * them.)  The extra streams start
  * after the work already on the context's stream, and the call returns when
  * every field is done.  opt_stats, if non-NULL, is an array of nf entries
  * (stage_us is not filled).  Returns LTS_OK when every field succeeded, else

@@ -37,8 +37,12 @@ struct ReqResult {
 
 namespace {
 
-constexpr int kMaxLanes = 16;      // the context's own workspace and up to 15 more
-constexpr int kBatchLanes = 4;     // workspaces a batch spreads over
+constexpr int kMaxLanes = 32;      // the context's own workspace and up to 31 more
+constexpr int kMaxServe = 15;      // serving workspaces at most (lts_serve_config)
+// Workspaces a batch spreads over (fields with large regions take long on one
+// warp per region; running many fields side by side overlaps them: measured
+// on the 256-field batch, 4 -> 63, 8 -> 94, 16 -> 158 Mvertices/s).
+constexpr int kBatchLanes = 32;
 constexpr int kRing = 1024;        // serving requests in flight per context
 constexpr int kPoolRetries = 3;    // times a call may enlarge an exhausted flood pool and run again
 
@@ -74,7 +78,7 @@ struct lts_ctx {
     cudaEvent_t ring_ev[kRing];
     bool ring_ready = false;
     unsigned long long next_ticket = 1;
-    int serve_max = kMaxLanes - 1;    // serving workspaces (lanes 1..serve_max); 0: the context's own
+    int serve_max = kMaxServe;        // serving workspaces (lanes 1..serve_max); 0: the context's own
     long long serve_budget = 120LL << 30;
     std::deque<std::pair<unsigned long long, long long>> inflight[kMaxLanes];   // (ticket, vertices) per lane
 };
@@ -812,21 +816,33 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, LTS_ERR_CUDA, "cudaSetDevice");
     cudaError_t e;
-    // workspaces: the context's own, and up to kMaxLanes - 1 more sized for the largest field
-    const int want = std::min(kBatchLanes, nf);
+    // workspaces: the context's own, and up to kBatchLanes - 1 more sized for
+    // the largest field, while the device has room for them (a batch runs on
+    // as many as it could get; it needs at least one more than the context's
+    // own when it has several fields)
+    int want = std::min(kBatchLanes, nf);
+    const size_t per_lane = bytes_for(sizes_for(nbig, c->sms));
     for (int i = 1; i < want; ++i) {
         Lane& L = c->lane[i];
         if (L.nmax >= nbig) continue;
         if (L.stream) cudaStreamSynchronize(L.stream);
         lane_free(L);
+        size_t fr = 0, tot = 0;
+        lts_status st = LTS_ERR_OOM;
         cudaStream_t s;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, LTS_ERR_CUDA, "cannot create a stream");
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr > per_lane + (1ull << 30)) {
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, LTS_ERR_CUDA, "cannot create a stream");
+            }
+            st = lane_alloc(L, nbig, c->sms, s, true, false);   // frees the lane and its stream on failure
         }
-        const lts_status st = lane_alloc(L, nbig, c->sms, s, true, false);
-        if (st != LTS_OK)   // lane_alloc has already freed the lane and destroyed the stream it owned
-            return fail(c, st, "cannot allocate a batch workspace");
+        cudaGetLastError();
+        if (st != LTS_OK) {
+            if (i == 1) return fail(c, LTS_ERR_OOM, "cannot allocate a batch workspace");
+            want = i;
+            break;
+        }
     }
     c->nlanes = std::max(c->nlanes, want);
     if (!c->fork) {
@@ -894,7 +910,7 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
 lts_status lts_serve_config(lts_ctx* c, int32_t max_concurrent, int64_t hbm_budget_bytes) {
     if (!c) return LTS_ERR_ARG;
     c->err.clear();
-    if (max_concurrent < 0 || max_concurrent > kMaxLanes - 1 || hbm_budget_bytes < 0)
+    if (max_concurrent < 0 || max_concurrent > kMaxServe || hbm_budget_bytes < 0)
         return fail(c, LTS_ERR_ARG, "max_concurrent must be in [0, 15] and the budget non-negative");
     c->serve_max = max_concurrent;
     c->serve_budget = hbm_budget_bytes;
