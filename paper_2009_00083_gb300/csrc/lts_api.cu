@@ -54,7 +54,7 @@ struct Lane {
     bool own_stream = false;
     cudaEvent_t ev[16];
     bool events = false;
-    void* allocs[64];
+    void* allocs[96];
     int nallocs = 0;
     bool dirty = false;            // a CUDA error left the workspace in an unknown state
 };
@@ -115,6 +115,7 @@ size_t bytes_for(const Sizes& z) {
     b += 32 * (size_t)z.half;                       // task records, heap records
     b += 4 * (size_t)z.n;                           // saddle arrival counters
     b += 4 * (size_t)z.spill_cap + 8 * (size_t)z.heap_cap + 4 * (size_t)z.log_cap;
+    b += 16 * (size_t)z.log_cap + 4 * (size_t)z.half;   // log classes, per-entry region data, class regions
     b += 11 * 4 * (size_t)z.half;                   // region records
     b += 3 * 4 * (size_t)z.n;                       // members, member regions, lhat
     b += 21 * (size_t)z.lo_cap;                     // local-order scratch
@@ -205,7 +206,9 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
          dev_alloc(L, &w.sib_head, z.half) && dev_alloc(L, &w.sib_next, z.half) &&
          dev_alloc(L, &w.spill_base, z.half) && dev_alloc(L, &w.spill_n, z.half) && dev_alloc(L, &w.heaprec, z.half);
     ok = ok && dev_alloc(L, &w.spill_pool, z.spill_cap) && dev_alloc(L, &w.heap_pool, z.heap_cap) &&
-         dev_alloc(L, &w.vlog, z.log_cap);
+         dev_alloc(L, &w.vlog, z.log_cap) && dev_alloc(L, &w.vlog_cls, z.log_cap) &&
+         dev_alloc(L, &w.ent_rid, z.log_cap) && dev_alloc(L, &w.ent_loc, z.log_cap) &&
+         dev_alloc(L, &w.ent_od, z.log_cap) && dev_alloc(L, &w.cls2rid, z.half);
     ok = ok && dev_alloc(L, &w.class2reg, z.half) && dev_alloc(L, &w.reg_class, z.half) &&
          dev_alloc(L, &w.reg_saddle, z.half) && dev_alloc(L, &w.reg_size, z.half) &&
          dev_alloc(L, &w.reg_start, z.half + 1) && dev_alloc(L, &w.reg_top, z.half) &&

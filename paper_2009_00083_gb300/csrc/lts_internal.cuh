@@ -162,6 +162,9 @@ struct Work {
     int* spill_pool; long long spill_cap;
     unsigned long long* heap_pool; long long heap_cap;
     int* vlog; long long log_cap;
+    int* vlog_cls;                       // per log entry: the class that claimed the vertex
+    int* ent_rid; int* ent_loc; int* ent_od;   // per log entry: region, local index, Od (regions stage)
+    int* cls2rid;                        // per class: region of its root, -1 if none
     // regions
     int* class2reg; int* reg_class; int* reg_saddle; int* reg_size; int* reg_start;
     int* reg_top; int* reg_sod; int* reg_place; int* reg_head; int* reg_att;

@@ -91,6 +91,7 @@ struct PropArgs {
     unsigned long long* heap_pool;
     long long heap_cap;
     int* vlog;
+    int* vlog_cls;               // the class that claimed each logged vertex (at the time of the claim)
     long long log_cap;
     const int4* tasks;           // (class, u, Od(u), seed; -1 after a meeting at u)
     DevCounters* ctr;
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
             m = __ldg(a.U + c);
             a.owner[m] = c;
             a.vlog[c] = m;
+            a.vlog_cls[c] = c;
             int x, y, z;
             coords_of(g, m, x, y, z);
 #pragma unroll
@@ -381,6 +383,7 @@ __global__ void __launch_bounds__(256) first_step_kernel(Geom g, const int* __re
             a.wait_v[c] = u;
             const int prev = atomicCAS(a.owner + u, -1, c);
             a.vlog[nU + c] = prev == -1 ? u : -1;
+            a.vlog_cls[nU + c] = c;
             int x, y, z;
             coords_of(g, u, x, y, z);
             int h = 0;
@@ -580,7 +583,10 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                         decision = -1;
                     }
                 }
-                if (decision == 1) a.vlog[log_pos++] = v;
+                if (decision == 1) {
+                    a.vlog_cls[log_pos] = c;
+                    a.vlog[log_pos++] = v;
+                }
             } else {
                 decision = (prev == c || (merged && find_root(a.parent, prev) == c)) ? 0 : 2;
             }
@@ -777,7 +783,7 @@ cudaError_t launch_propagate(Work& w, const Geom& g, const int* O, const float* 
     a.parent = w.parent; a.wait_v = w.wait_v; a.cnt = w.cnt;
     a.spill_base = w.spill_base; a.spill_n = w.spill_n; a.heaprec = w.heaprec;
     a.spill_pool = w.spill_pool; a.spill_cap = w.spill_cap; a.heap_pool = w.heap_pool; a.heap_cap = w.heap_cap;
-    a.vlog = w.vlog; a.log_cap = w.log_cap; a.tasks = w.tasks; a.ctr = w.ctr;
+    a.vlog = w.vlog; a.vlog_cls = w.vlog_cls; a.log_cap = w.log_cap; a.tasks = w.tasks; a.ctr = w.ctr;
     a.F = F; a.eps = eps; a.ctop = w.ctop; a.authbits = w.authbits;
     const int pb = sms * 8;
     const int blocks = w.lanes / kThreads;

@@ -63,43 +63,60 @@ __global__ void roots_kernel(Geom g, const int* __restrict__ O, const int* __res
     }
 }
 
+// every class: the region of its root (the forest is flat), -1 if none
+__global__ void cls_rid_kernel(const int* __restrict__ parent, const int* __restrict__ class2reg, int* cls2rid,
+                               const DevCounters* ctr) {
+    if (failed(&ctr->status)) return;
+    const int nU = ctr->n_unauth;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nU; c += gridDim.x * blockDim.x)
+        cls2rid[c] = class2reg[parent[c]];
+}
+
+// One thread per log entry (a claimed vertex u with the class that claimed
+// it): the region of u, its local index (counted), the region's highest
+// member, and u's region tag and local index.  The entry's region, local
+// index and Od are kept for members_fill_kernel, which then reads nothing at
+// random.  A region's final saddle is not a member (entry region -1).
 template <int DIR>
 __global__ void members_count_kernel(Geom g, const int* __restrict__ O, const int* __restrict__ vlog,
-                                     const int* __restrict__ parent, int* owner, int* loc,
-                                     const int* __restrict__ class2reg, const int* __restrict__ reg_saddle,
-                                     int* reg_size, int* reg_top, DevCounters* ctr) {
+                                     const int* __restrict__ vlog_cls, const int* __restrict__ cls2rid, int* owner,
+                                     int* loc, const int* __restrict__ reg_saddle, int* reg_size, int* reg_top,
+                                     int* ent_rid, int* ent_loc, int* ent_od, DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nlog = ctr->log_cursor;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlog; i += gridDim.x * blockDim.x) {
         const int u = vlog[i];
-        if (u < 0) continue;
-        const int ow = owner[u];
-        const int rid = class2reg[parent[ow]];
-        if (rid < 0) { set_status(&ctr->status, LTS_ERR_INTERNAL); continue; }
-        if (reg_saddle[rid] == u) continue;                // a final saddle, not a member
-        loc[u] = atomicAdd(reg_size + rid, 1);
-        atomicMax(reg_top + rid, od<DIR>(O[u], g.n));
-        owner[u] = -2 - rid;                                // region tag
+        int rid = -1;
+        if (u >= 0) {
+            rid = __ldg(cls2rid + vlog_cls[i]);
+            if (rid < 0) set_status(&ctr->status, LTS_ERR_INTERNAL);
+            else if (__ldg(reg_saddle + rid) == u) rid = -1;    // a final saddle, not a member
+        }
+        ent_rid[i] = rid;
+        if (rid < 0) continue;
+        const int l = atomicAdd(reg_size + rid, 1);
+        const int o = od<DIR>(__ldg(O + u), g.n);
+        atomicMax(reg_top + rid, o);
+        loc[u] = l;
+        owner[u] = -2 - rid;                                    // region tag
+        ent_loc[i] = l;
+        ent_od[i] = o;
     }
 }
 
-template <int DIR>
-__global__ void members_fill_kernel(Geom g, const int* __restrict__ O, const int* __restrict__ vlog,
-                                    const int* __restrict__ owner, const int* __restrict__ loc,
+__global__ void members_fill_kernel(const int* __restrict__ vlog, const int* __restrict__ ent_rid,
+                                    const int* __restrict__ ent_loc, const int* __restrict__ ent_od,
                                     const int* __restrict__ reg_start, int* members, int* member_reg, RankBlk* rblk,
                                     DevCounters* ctr) {
     if (failed(&ctr->status)) return;
     const int nlog = ctr->log_cursor;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nlog; i += gridDim.x * blockDim.x) {
-        const int u = vlog[i];
-        if (u < 0) continue;
-        const int t = owner[u];
-        if (t > -2) continue;
-        const int rid = -2 - t;
-        const int p = reg_start[rid] + loc[u];
-        members[p] = u;
+        const int rid = ent_rid[i];
+        if (rid < 0) continue;
+        const int p = __ldg(reg_start + rid) + ent_loc[i];
+        members[p] = vlog[i];
         member_reg[p] = rid;
-        const int j = od<DIR>(O[u], g.n);
+        const int j = ent_od[i];
         atomicOr(&rblk[j >> kRankShift].mmask, 1u << (j & 31));
     }
 }
@@ -222,16 +239,17 @@ cudaError_t extract_regions(Work& w, const Geom& g, const int* O, int sms, cudaS
     flatten_kernel<<<B, T, 0, s>>>(w.parent, w.ctr);
     roots_kernel<DIR><<<B, T, 0, s>>>(g, O, w.parent, w.wait_v, w.owner, w.sib_head, w.sib_next, w.class2reg, w.reg_class, w.reg_saddle,
                                       w.reg_size, w.reg_top, w.reg_sod, w.reg_head, w.ctr);
-    members_count_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.parent, w.owner, w.loc, w.class2reg, w.reg_saddle,
-                                              w.reg_size, w.reg_top, w.ctr);
+    cls_rid_kernel<<<B, T, 0, s>>>(w.parent, w.class2reg, w.cls2rid, w.ctr);
+    members_count_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.vlog_cls, w.cls2rid, w.owner, w.loc, w.reg_saddle,
+                                              w.reg_size, w.reg_top, w.ent_rid, w.ent_loc, w.ent_od, w.ctr);
     scan_excl_i32(w, w.reg_size, w.reg_start, &w.ctr->n_regions, g.n / 2 + 1, s);
-    members_fill_kernel<DIR><<<B, T, 0, s>>>(g, O, w.vlog, w.owner, w.loc, w.reg_start, w.members, w.member_reg,
-                                             w.rblk, w.ctr);
+    members_fill_kernel<<<B, T, 0, s>>>(w.vlog, w.ent_rid, w.ent_loc, w.ent_od, w.reg_start, w.members,
+                                        w.member_reg, w.rblk, w.ctr);
     siblings_kernel<<<B, T, 0, s>>>(w.reg_class, w.reg_head, w.reg_sod, w.reg_size, w.reg_top, w.sib_head, w.sib_next,
                                     w.class2reg, w.reg_place, w.reg_att, w.rblk, w.ctr);
     tiers_kernel<<<B, T, 0, s>>>(w.reg_size, w.reg_start, w.lhat, w.tier_list, w.class_cap, w.class_cap / 4,
                                  local_order_med_max(), local_order_huge_max(), w.min_tier, g.n, w.ctr);
-    w.launches += 6;
+    w.launches += 7;
     return cudaGetLastError();
 }
 
