@@ -110,7 +110,7 @@ size_t bytes_for(const Sizes& z) {
     b += (size_t)z.tiles * 256 * 8 + 8192 * 2 + 32; // look-back words, histograms, digit offsets
     b += 3 * 4 * 8192 + 48;                         // distinct-key table
     b += ((size_t)z.n + 31) / 32 * 4;               // authorized bitmap
-    b += 2 * 4 * (size_t)z.n + 8 * (size_t)z.n;     // owner, loc, qmark
+    b += 3 * 4 * (size_t)z.n;                       // owner, loc, qmark
     b += 10 * 4 * (size_t)z.half;                   // U and class records
     b += 32 * (size_t)z.half;                       // task records, heap records
     b += 4 * (size_t)z.n;                           // saddle arrival counters
@@ -259,10 +259,9 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     cudaMemsetAsync(w.owner, 0xff, sizeof(int) * (size_t)z.n, s);
     cudaMemsetAsync(w.cnt, 0, sizeof(int) * (size_t)z.n, s);
     cudaMemsetAsync(w.sort_status, 0, (size_t)z.tiles * 256 * sizeof(unsigned long long), s);
-    cudaMemsetAsync(w.qmark, 0, sizeof(unsigned long long) * (size_t)z.n, s);
+    cudaMemsetAsync(w.qmark, 0xff, sizeof(int) * (size_t)z.n, s);
     if (stall_words) cudaMemsetAsync(stall_words, 0, 256 * sizeof(unsigned long long), s);
     build_link_tables(w.link6, w.link14, s);
-    w.pass_tag = 0;
     cudaMemsetAsync(w.ctr, 0, sizeof(DevCounters), s);
     w.epoch = 0;
     if (cudaStreamSynchronize(s) != cudaSuccess) {

@@ -149,8 +149,7 @@ struct Work {
     unsigned int* authbits;              // ceil(n/32)
     // propagation
     int* owner;                          // per vertex: class, region tag, or -1
-    unsigned long long* qmark;           // per vertex: last (pass tag, class) that queued it
-    unsigned int pass_tag;
+    int* qmark;                          // per vertex: the last class that queued it (-1 after a clear)
     int* loc;                            // per vertex: local index within its region
     int* U;                              // unauthorized extrema
     int* parent; int* wait_v;            // per class

@@ -78,8 +78,7 @@ template <> struct TeamCfg<6> { static constexpr int TS = 32; static constexpr i
 struct PropArgs {
     const int* U;
     int* owner;
-    unsigned long long* qmark;   // (pass tag << 32 | class) of the last class that queued the vertex
-    unsigned long long tag;      // this pass's tag, in the high 32 bits
+    int* qmark;                  // the last class that queued the vertex (cleared to -1 before each launch)
     int* parent;
     int* wait_v;
     int* cnt;
@@ -312,7 +311,7 @@ __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, cons
 // seed m but u, inserted unless the class `mark` already queued them.
 template <int DIR, int NN>
 __device__ __forceinline__ bool rebuild_first_queue(TeamState<NN>& T, const Geom& g, const int* __restrict__ O, int m,
-                                                    int u, unsigned long long mark, const PropArgs& a, int tl) {
+                                                    int u, int mark, const PropArgs& a, int tl) {
     int x, y, z;
     coords_of(g, m, x, y, z);
     const int nb = tl < NN ? nbr_q<NN>(g, x, y, z, tl) : -1;
@@ -467,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
 #pragma unroll
             for (int e = 0; e < E; ++e) T.sk[e] = -1;
             T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0; T.ovn = 0; T.ov_top = -1;
-            const unsigned long long mk = a.tag | (unsigned)c;
+            const int mk = c;
             bool ok;
             if (seed >= 0) {                           // u has one higher neighbour, the seed of c
                 merged = false;
@@ -548,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                 kv = K;
             }
         }
-        const unsigned long long mark = a.tag | (unsigned)c;
+        const int mark = c;
         // the leader claims v first, so that the atomic overlaps the neighbour loads
         int prev = 0;
         float fv = 0.f;
@@ -561,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
         coords_of(g, v, x, y, z);
         const int nb = tl < NN ? nbr_q<NN>(g, x, y, z, tl) : -1;
         int on = -1, ow = -1;
-        unsigned long long qm = 0;
+        int qm = -1;
         if (nb >= 0) {
             on = od<DIR>(__ldg(O + nb), g.n);
             ow = __ldcg(a.owner + nb);
@@ -779,7 +778,9 @@ template <int DIR, bool PERS>
 cudaError_t launch_propagate(Work& w, const Geom& g, const int* O, const float* F, double eps, int sms,
                              cudaStream_t s) {
     PropArgs a;
-    a.U = w.U; a.owner = w.owner; a.qmark = w.qmark; a.tag = (unsigned long long)(++w.pass_tag) << 32;
+    a.U = w.U; a.owner = w.owner; a.qmark = w.qmark;
+    // queue marks are class ids of this launch: clear them (-1) first
+    cudaMemsetAsync(w.qmark, 0xff, sizeof(int) * (size_t)g.n, s);
     a.parent = w.parent; a.wait_v = w.wait_v; a.cnt = w.cnt;
     a.spill_base = w.spill_base; a.spill_n = w.spill_n; a.heaprec = w.heaprec;
     a.spill_pool = w.spill_pool; a.spill_cap = w.spill_cap; a.heap_pool = w.heap_pool; a.heap_cap = w.heap_cap;
