@@ -465,6 +465,9 @@ __global__ void __launch_bounds__(128, 12) lo_team_kernel(Geom g, LOArgs a, cons
 template <int NN>
 struct Dense {
     int* v; int* L; int* L2; int* P; unsigned short* adj; unsigned char* f;   // f: kBnd | kVis | kTried | kInq | kSeed
+    unsigned short* rk;      // rank of each member's Od among the members (key-space propagations)
+    unsigned short* kidx;    // key -> local index
+    unsigned* b1; unsigned* b2;   // queue bitmaps over the keys (bit k of b1; bit w of b2: b1 word w is not 0)
 };
 constexpr unsigned char kInq = 8;
 
@@ -520,6 +523,72 @@ __device__ __forceinline__ void dense_checks(const Dense<NN>& D, int r, int m, i
     umax = __any_sync(0xffffffffu, a_max);
 }
 
+// The same propagation in key space (regions of at most kKeyMax vertices):
+// the priority of local index i is a key in 0..r-1 in the order of L, so the
+// queue is a two-level bitmap over the keys: a pop takes the highest (lowest)
+// set bit in two shared-memory loads, a push sets two bits, and the visiting
+// order is the dense scan's.  Keys: with tryc >= 0 (a candidate try of the
+// first propagation) the candidate has key 0, s key r-1 and the other members
+// their Od rank (shifted up by one below the candidate's); otherwise L itself,
+// a permutation of 0..r-1 after the first propagation.
+template <bool MAXF, int NN>
+__device__ __forceinline__ int dense_flood_keys(const Dense<NN>& D, int r, int lane, int tryc) {
+    const int rtry = tryc >= 0 ? D.rk[tryc] : 0;
+    auto key = [&](int i) -> int {
+        if (tryc < 0) return D.L[i];
+        if (i == tryc) return 0;
+        if (i == r - 1) return r - 1;
+        const int k = D.rk[i];
+        return k < rtry ? k + 1 : k;
+    };
+    const int w1n = (r + 31) >> 5;
+    for (int w = lane; w < w1n; w += 32) D.b1[w] = 0u;
+    if (lane == 0) D.b2[0] = 0u;
+    for (int i = lane; i < r; i += 32) D.kidx[key(i)] = (unsigned short)i;
+    __syncwarp();
+    for (int i = lane; i < r; i += 32)
+        if (D.f[i] & kInq) {
+            const int kk = key(i);
+            atomicOr(&D.b1[kk >> 5], 1u << (kk & 31));
+            atomicOr(&D.b2[0], 1u << (kk >> 5));
+        }
+    __syncwarp();
+    int last = -2;
+    for (int step = 0; step < r; ++step) {
+        const unsigned w2 = D.b2[0];
+        if (!w2) return -2;
+        const int i1 = MAXF ? 31 - __clz(w2) : __ffs(w2) - 1;
+        const unsigned w1 = D.b1[i1];
+        if (!w1) return -2;                               // inconsistent levels: reported as an error
+        const int b = MAXF ? 31 - __clz(w1) : __ffs(w1) - 1;
+        const int p = D.kidx[i1 * 32 + b];
+        __syncwarp();
+        if (lane == 0) {
+            const unsigned n1 = w1 & ~(1u << b);
+            D.b1[i1] = n1;
+            if (!n1) D.b2[0] = w2 & ~(1u << i1);
+            D.f[p] |= kVis;
+            D.L2[p] = MAXF ? r - 1 - step : step;
+        }
+        __syncwarp();
+        if (lane < NN) {
+            const unsigned short j = D.adj[p * NN + lane];
+            if (j != kNoNbr) {
+                const unsigned char fj = D.f[j];
+                if (!(fj & kInq)) {                       // enters the queue once (the neighbours of p are distinct)
+                    D.f[j] = fj | kInq;
+                    const int kj = key(j);
+                    atomicOr(&D.b1[kj >> 5], 1u << (kj & 31));
+                    atomicOr(&D.b2[0], 1u << (kj >> 5));
+                }
+            }
+        }
+        __syncwarp();
+        last = p;
+    }
+    return last;
+}
+
 // flags the seeds of a sublevel propagation (see mark_seeds); returns whether there is one
 template <int NN>
 __device__ __forceinline__ bool dense_mark_seeds(const Dense<NN>& D, int m, int lane, bool literal) {
@@ -540,8 +609,15 @@ __device__ __forceinline__ bool dense_mark_seeds(const Dense<NN>& D, int m, int 
     return __any_sync(0xffffffffu, any);
 }
 
+// regions of at most this many vertices run their propagations in key space
+// (two bitmap levels of 32 bits: keys below 1024)
+constexpr int kKeyMax = 1024;
+
 template <int NN, int RMAX>
-__host__ __device__ constexpr size_t dense_smem_per_warp() { return (size_t)RMAX * (4 * 4 + 2 * NN + 1) + 16; }
+__host__ __device__ constexpr size_t dense_smem_per_warp() {
+    return (size_t)RMAX * (4 * 4 + 2 * NN + 1) + 16 +
+           (RMAX <= kKeyMax ? (size_t)RMAX * 4 + (size_t)RMAX / 8 + 16 : 0);
+}
 
 // one region per warp, WPB warps per block, regions of at most RMAX vertices
 template <int DIR, int NN, int RMAX, int WPB>
@@ -556,7 +632,18 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
     D.L2 = D.L + RMAX;
     D.P = D.L2 + RMAX;
     D.adj = reinterpret_cast<unsigned short*>(D.P + RMAX);
-    D.f = reinterpret_cast<unsigned char*>(D.adj + RMAX * NN);
+    constexpr bool kKeys = RMAX <= kKeyMax;
+    if (kKeys) {
+        D.rk = D.adj + RMAX * NN;
+        D.kidx = D.rk + RMAX;
+        D.b1 = reinterpret_cast<unsigned*>(D.kidx + RMAX);
+        D.b2 = D.b1 + (RMAX + 31) / 32;
+        D.f = reinterpret_cast<unsigned char*>(D.b2 + 4);
+    } else {
+        D.rk = D.kidx = nullptr;
+        D.b1 = D.b2 = nullptr;
+        D.f = reinterpret_cast<unsigned char*>(D.adj + RMAX * NN);
+    }
     const int lane = threadIdx.x & 31;
     const int cnt = *d_count;
     const int gw = blockIdx.x * WPB + wib, nw = gridDim.x * WPB;
@@ -588,6 +675,15 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
             D.L[i] = i < m ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
         }
         __syncwarp();
+        if (kKeys) {                                      // Od rank of every member
+            for (int i = lane; i < m; i += 32) {
+                const int li = D.L[i];
+                int c = 0;
+                for (int j = 0; j < m; ++j) c += D.L[j] < li;
+                D.rk[i] = (unsigned short)c;
+            }
+            __syncwarp();
+        }
         // the minus-infinity vertex
         bool ok = false;
         int ai = -1;
@@ -604,7 +700,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
             if (lane == 0) D.L[ai] = -1;
             for (int i = lane; i < r; i += 32) D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
             __syncwarp();
-            const int last = dense_flood<true, NN>(D, r, lane);
+            const int last = kKeys ? dense_flood_keys<true, NN>(D, r, lane, ai) : dense_flood<true, NN>(D, r, lane);
             if (last == -2) break;
             if (last == ai) { ok = true; break; }
             if (lane == 0) { D.L[ai] = keep; D.f[ai] |= kTried; }
@@ -623,7 +719,8 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
                         D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
                     }
                     __syncwarp();
-                    if (dense_flood<true, NN>(D, r, lane) != ai) break;
+                    if ((kKeys ? dense_flood_keys<true, NN>(D, r, lane, ai) : dense_flood<true, NN>(D, r, lane)) != ai)
+                        break;
                 }
                 for (int i = lane; i < r; i += 32) { D.L[i] = D.L2[i]; D.P[i] = D.L2[i]; }
                 __syncwarp();
@@ -638,7 +735,10 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
                     for (int i = lane; i < r; i += 32)
                         D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | ((i < m && (D.f[i] & kSeed)) ? kInq : 0));
                     __syncwarp();
-                    if (dense_flood<false, NN>(D, r, lane) == -2) { res = -2; break; }
+                    if ((kKeys ? dense_flood_keys<false, NN>(D, r, lane, -1) : dense_flood<false, NN>(D, r, lane)) == -2) {
+                        res = -2;
+                        break;
+                    }
                     for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
                     __syncwarp();
                     dense_checks(D, r, m, lane, umin, umax);
@@ -647,7 +747,10 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
                     for (int i = lane; i < r; i += 32)
                         D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
                     __syncwarp();
-                    if (dense_flood<true, NN>(D, r, lane) == -2) { res = -2; break; }
+                    if ((kKeys ? dense_flood_keys<true, NN>(D, r, lane, -1) : dense_flood<true, NN>(D, r, lane)) == -2) {
+                        res = -2;
+                        break;
+                    }
                     for (int i = lane; i < r; i += 32) D.L[i] = D.L2[i];
                     __syncwarp();
                     if (literal) {
