@@ -28,10 +28,13 @@
 //     propagation step is one team max/min reduction over the frontier and
 //     one broadcast of the popped vertex's adjacency;
 //   r <= 128, r <= 1024 and r <= 4096: one region per warp, arrays in shared
-//     memory; each step scans the frontier densely (r/32 vertices per lane)
-//     and reduces over the warp;
-//   larger: one region per warp, a 32-ary heap in shared memory (one region
-//     per lane with binary heaps in HBM scratch when the heap overflows).
+//     memory; a propagation runs in key space (the members' priorities are
+//     ranks 0..r-1, the queue a bitmap over them with summary levels), so a
+//     step is a few shared-memory loads and the neighbours' pushes;
+//   larger: one region per warp, the same key-space queue in shared memory
+//     with the key-indexed adjacency in HBM scratch (a 32-ary heap in shared
+//     memory when the scratch pool is spent, and one region per lane with
+//     binary heaps in HBM scratch when that heap overflows).
 #include <climits>
 
 #include "lts_internal.cuh"
@@ -460,47 +463,18 @@ __global__ void __launch_bounds__(128, 12) lo_team_kernel(Geom g, LOArgs a, cons
     warp_atomic_add(&a.ctr->lo_fallbacks, nfb);
 }
 
-// ---- tier 3: one warp per region of at most kMedR vertices, dense scans ----
+// ---- tiers 3-5: one warp per region of at most 128, 1024 or 4096 vertices ----
 
 template <int NN>
 struct Dense {
     int* v; int* L; int* L2; int* P; unsigned short* adj; unsigned char* f;   // f: kBnd | kVis | kTried | kInq | kSeed
     unsigned short* rk;      // rank of each member's Od among the members (key-space propagations)
     unsigned short* kidx;    // key -> local index
-    unsigned* b1; unsigned* b2;   // queue bitmaps over the keys (bit k of b1; bit w of b2: b1 word w is not 0)
+    // queue bitmaps over the keys: bit k of b1; bit w of b2: b1 word w is not 0;
+    // bit u of b3: b2 word u is not 0 (b2 has one word below 1025 keys, b3 is then unused)
+    unsigned* b1; unsigned* b2; unsigned* b3;
 };
 constexpr unsigned char kInq = 8;
-
-// superlevel (MAXF) or sublevel propagation over the region; the frontier is
-// scanned densely: each lane takes the best of its vertices, the warp reduces.
-template <bool MAXF, int NN>
-__device__ __forceinline__ int dense_flood(const Dense<NN>& D, int r, int lane) {
-    int last = -2;
-    for (int step = 0; step < r; ++step) {
-        int best = MAXF ? INT_MIN : INT_MAX, bi = -1;
-        for (int i = lane; i < r; i += 32) {
-            const unsigned char fl = D.f[i];
-            if ((fl & (kInq | kVis)) != kInq) continue;
-            const int l = D.L[i];
-            if (MAXF ? l > best : l < best) { best = l; bi = i; }
-        }
-        const int K = MAXF ? __reduce_max_sync(0xffffffffu, best) : __reduce_min_sync(0xffffffffu, best);
-        if (K == (MAXF ? INT_MIN : INT_MAX)) return -2;
-        const int src = __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1;
-        const int p = __shfl_sync(0xffffffffu, bi, src);
-        if (lane == 0) {
-            D.f[p] |= kVis;
-            D.L2[p] = MAXF ? r - 1 - step : step;
-        }
-        if (lane < NN) {
-            const unsigned short j = D.adj[p * NN + lane];
-            if (j != kNoNbr) D.f[j] |= kInq;            // byte stores by distinct lanes to distinct vertices
-        }
-        __syncwarp();
-        last = p;
-    }
-    return last;
-}
 
 template <int NN>
 __device__ __forceinline__ void dense_checks(const Dense<NN>& D, int r, int m, int lane, bool& umin, bool& umax) {
@@ -523,16 +497,18 @@ __device__ __forceinline__ void dense_checks(const Dense<NN>& D, int r, int m, i
     umax = __any_sync(0xffffffffu, a_max);
 }
 
-// The same propagation in key space (regions of at most kKeyMax vertices):
+// Superlevel (MAXF) or sublevel propagation over the region in key space:
 // the priority of local index i is a key in 0..r-1 in the order of L, so the
-// queue is a two-level bitmap over the keys: a pop takes the highest (lowest)
-// set bit in two shared-memory loads, a push sets two bits, and the visiting
-// order is the dense scan's.  Keys: with tryc >= 0 (a candidate try of the
-// first propagation) the candidate has key 0, s key r-1 and the other members
-// their Od rank (shifted up by one below the candidate's); otherwise L itself,
-// a permutation of 0..r-1 after the first propagation.
-template <bool MAXF, int NN>
+// queue is a bitmap over the keys with one or two summary levels: a pop takes
+// the highest (lowest) set bit in two or three shared-memory loads, a push sets
+// as many bits, and the visiting order is that of any priority queue on the
+// same keys.  Keys: with tryc >= 0 (a candidate try of the first propagation)
+// the candidate has key 0, s key r-1 and the other members their Od rank
+// (shifted up by one below the candidate's); otherwise L itself, a
+// permutation of 0..r-1 after the first propagation.
+template <bool MAXF, int NN, int RMAX>
 __device__ __forceinline__ int dense_flood_keys(const Dense<NN>& D, int r, int lane, int tryc) {
+    constexpr bool kL3 = RMAX > 1024;
     const int rtry = tryc >= 0 ? D.rk[tryc] : 0;
     auto key = [&](int i) -> int {
         if (tryc < 0) return D.L[i];
@@ -541,23 +517,32 @@ __device__ __forceinline__ int dense_flood_keys(const Dense<NN>& D, int r, int l
         const int k = D.rk[i];
         return k < rtry ? k + 1 : k;
     };
+    auto push = [&](int kk) {
+        atomicOr(&D.b1[kk >> 5], 1u << (kk & 31));
+        atomicOr(&D.b2[kk >> 10], 1u << ((kk >> 5) & 31));
+        if (kL3) atomicOr(&D.b3[0], 1u << (kk >> 10));
+    };
     const int w1n = (r + 31) >> 5;
     for (int w = lane; w < w1n; w += 32) D.b1[w] = 0u;
-    if (lane == 0) D.b2[0] = 0u;
+    if (lane < 4) D.b2[lane] = 0u;
+    if (kL3 && lane == 0) D.b3[0] = 0u;
     for (int i = lane; i < r; i += 32) D.kidx[key(i)] = (unsigned short)i;
     __syncwarp();
     for (int i = lane; i < r; i += 32)
-        if (D.f[i] & kInq) {
-            const int kk = key(i);
-            atomicOr(&D.b1[kk >> 5], 1u << (kk & 31));
-            atomicOr(&D.b2[0], 1u << (kk >> 5));
-        }
+        if (D.f[i] & kInq) push(key(i));
     __syncwarp();
     int last = -2;
     for (int step = 0; step < r; ++step) {
-        const unsigned w2 = D.b2[0];
+        int i2 = 0;
+        unsigned w3 = 0u;
+        if (kL3) {
+            w3 = D.b3[0];
+            if (!w3) return -2;
+            i2 = MAXF ? 31 - __clz(w3) : __ffs(w3) - 1;
+        }
+        const unsigned w2 = D.b2[i2];
         if (!w2) return -2;
-        const int i1 = MAXF ? 31 - __clz(w2) : __ffs(w2) - 1;
+        const int i1 = i2 * 32 + (MAXF ? 31 - __clz(w2) : __ffs(w2) - 1);
         const unsigned w1 = D.b1[i1];
         if (!w1) return -2;                               // inconsistent levels: reported as an error
         const int b = MAXF ? 31 - __clz(w1) : __ffs(w1) - 1;
@@ -566,7 +551,11 @@ __device__ __forceinline__ int dense_flood_keys(const Dense<NN>& D, int r, int l
         if (lane == 0) {
             const unsigned n1 = w1 & ~(1u << b);
             D.b1[i1] = n1;
-            if (!n1) D.b2[0] = w2 & ~(1u << i1);
+            if (!n1) {
+                const unsigned n2 = w2 & ~(1u << (i1 & 31));
+                D.b2[i2] = n2;
+                if (kL3 && !n2) D.b3[0] = w3 & ~(1u << i2);
+            }
             D.f[p] |= kVis;
             D.L2[p] = MAXF ? r - 1 - step : step;
         }
@@ -577,9 +566,7 @@ __device__ __forceinline__ int dense_flood_keys(const Dense<NN>& D, int r, int l
                 const unsigned char fj = D.f[j];
                 if (!(fj & kInq)) {                       // enters the queue once (the neighbours of p are distinct)
                     D.f[j] = fj | kInq;
-                    const int kj = key(j);
-                    atomicOr(&D.b1[kj >> 5], 1u << (kj & 31));
-                    atomicOr(&D.b2[0], 1u << (kj >> 5));
+                    push(key(j));
                 }
             }
         }
@@ -587,6 +574,37 @@ __device__ __forceinline__ int dense_flood_keys(const Dense<NN>& D, int r, int l
         last = p;
     }
     return last;
+}
+
+// rk[i] = rank of L[i] among L[0..m-1] (distinct values): a bitonic sort of
+// the values in P (padded with INT_MAX to a power of two), then a binary
+// search per member
+template <int NN>
+__device__ __forceinline__ void dense_ranks(const Dense<NN>& D, int m, int lane) {
+    int n2 = 1;
+    while (n2 < m) n2 <<= 1;
+    for (int i = lane; i < n2; i += 32) D.P[i] = i < m ? D.L[i] : INT_MAX;
+    __syncwarp();
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < (n2 >> 1); t += 32) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));   // bit j of i is clear
+                const int a = D.P[i], b = D.P[i + j];
+                if ((a > b) == ((i & k) == 0)) { D.P[i] = b; D.P[i + j] = a; }
+            }
+            __syncwarp();
+        }
+    for (int i = lane; i < m; i += 32) {
+        const int li = D.L[i];
+        int lo = 0, hi = m;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (D.P[mid] < li) lo = mid + 1;
+            else hi = mid;
+        }
+        D.rk[i] = (unsigned short)lo;
+    }
+    __syncwarp();
 }
 
 // flags the seeds of a sublevel propagation (see mark_seeds); returns whether there is one
@@ -609,14 +627,12 @@ __device__ __forceinline__ bool dense_mark_seeds(const Dense<NN>& D, int m, int 
     return __any_sync(0xffffffffu, any);
 }
 
-// regions of at most this many vertices run their propagations in key space
-// (two bitmap levels of 32 bits: keys below 1024)
-constexpr int kKeyMax = 1024;
-
+// per warp: v, L, L2, P (ints), adj (NN ushorts), rk and kidx (ushorts) per
+// vertex; the key bitmaps (b1: RMAX bits, b2: 4 words, b3: 1 word, 16-byte
+// slots); the flags (a byte per vertex)
 template <int NN, int RMAX>
 __host__ __device__ constexpr size_t dense_smem_per_warp() {
-    return (size_t)RMAX * (4 * 4 + 2 * NN + 1) + 16 +
-           (RMAX <= kKeyMax ? (size_t)RMAX * 4 + (size_t)RMAX / 8 + 16 : 0);
+    return (size_t)RMAX * (4 * 4 + 2 * NN + 4 + 1) + (size_t)RMAX / 8 + 48;
 }
 
 // one region per warp, WPB warps per block, regions of at most RMAX vertices
@@ -632,18 +648,13 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
     D.L2 = D.L + RMAX;
     D.P = D.L2 + RMAX;
     D.adj = reinterpret_cast<unsigned short*>(D.P + RMAX);
-    constexpr bool kKeys = RMAX <= kKeyMax;
-    if (kKeys) {
-        D.rk = D.adj + RMAX * NN;
-        D.kidx = D.rk + RMAX;
-        D.b1 = reinterpret_cast<unsigned*>(D.kidx + RMAX);
-        D.b2 = D.b1 + (RMAX + 31) / 32;
-        D.f = reinterpret_cast<unsigned char*>(D.b2 + 4);
-    } else {
-        D.rk = D.kidx = nullptr;
-        D.b1 = D.b2 = nullptr;
-        D.f = reinterpret_cast<unsigned char*>(D.adj + RMAX * NN);
-    }
+    static_assert(RMAX % 64 == 0 && RMAX <= 4096, "key bitmaps of the dense tiers");
+    D.rk = D.adj + RMAX * NN;
+    D.kidx = D.rk + RMAX;
+    D.b1 = reinterpret_cast<unsigned*>(D.kidx + RMAX);
+    D.b2 = D.b1 + RMAX / 32;
+    D.b3 = D.b2 + 4;
+    D.f = reinterpret_cast<unsigned char*>(D.b3 + 4);
     const int lane = threadIdx.x & 31;
     const int cnt = *d_count;
     const int gw = blockIdx.x * WPB + wib, nw = gridDim.x * WPB;
@@ -675,15 +686,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
             D.L[i] = i < m ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
         }
         __syncwarp();
-        if (kKeys) {                                      // Od rank of every member
-            for (int i = lane; i < m; i += 32) {
-                const int li = D.L[i];
-                int c = 0;
-                for (int j = 0; j < m; ++j) c += D.L[j] < li;
-                D.rk[i] = (unsigned short)c;
-            }
-            __syncwarp();
-        }
+        dense_ranks(D, m, lane);                          // Od rank of every member
         // the minus-infinity vertex
         bool ok = false;
         int ai = -1;
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
             if (lane == 0) D.L[ai] = -1;
             for (int i = lane; i < r; i += 32) D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
             __syncwarp();
-            const int last = kKeys ? dense_flood_keys<true, NN>(D, r, lane, ai) : dense_flood<true, NN>(D, r, lane);
+            const int last = dense_flood_keys<true, NN, RMAX>(D, r, lane, ai);
             if (last == -2) break;
             if (last == ai) { ok = true; break; }
             if (lane == 0) { D.L[ai] = keep; D.f[ai] |= kTried; }
@@ -719,7 +722,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
                         D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
                     }
                     __syncwarp();
-                    if ((kKeys ? dense_flood_keys<true, NN>(D, r, lane, ai) : dense_flood<true, NN>(D, r, lane)) != ai)
+                    if (dense_flood_keys<true, NN, RMAX>(D, r, lane, ai) != ai)
                         break;
                 }
                 for (int i = lane; i < r; i += 32) { D.L[i] = D.L2[i]; D.P[i] = D.L2[i]; }
@@ -735,7 +738,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
                     for (int i = lane; i < r; i += 32)
                         D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | ((i < m && (D.f[i] & kSeed)) ? kInq : 0));
                     __syncwarp();
-                    if ((kKeys ? dense_flood_keys<false, NN>(D, r, lane, -1) : dense_flood<false, NN>(D, r, lane)) == -2) {
+                    if (dense_flood_keys<false, NN, RMAX>(D, r, lane, -1) == -2) {
                         res = -2;
                         break;
                     }
@@ -747,7 +750,7 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
                     for (int i = lane; i < r; i += 32)
                         D.f[i] = (unsigned char)((D.f[i] & ~(kVis | kInq)) | (i == m ? kInq : 0));
                     __syncwarp();
-                    if ((kKeys ? dense_flood_keys<true, NN>(D, r, lane, -1) : dense_flood<true, NN>(D, r, lane)) == -2) {
+                    if (dense_flood_keys<true, NN, RMAX>(D, r, lane, -1) == -2) {
                         res = -2;
                         break;
                     }
