@@ -929,12 +929,25 @@ __device__ int wr_flood(const WarpRegion& R, unsigned long long* H, int lane) {
 
 // ---- floods in key space (after the first flood L is a permutation of 0..r-1) ----
 // NK[k * NN + q] holds the key of neighbour q of the vertex with key k (-1 if
-// none), so a step is one load; the frontier is a three-level bitmap over the
-// keys in shared memory (pops find the highest or lowest set bit, pushes are
-// lane-parallel atomicOr, no capacity limit) and the visited set a bitmap.
+// none); the frontier is a three-level bitmap over the keys in shared memory
+// (the summary levels give the highest or lowest set bit in three loads,
+// pushes are lane-parallel atomicOr, no capacity limit) and the visited set a
+// bitmap.
+//
+// A propagation pops several keys per round.  The round takes the next keys
+// of the queue c_0, c_1, ... (up to 32: every set bit of the 32 bitmap words
+// from the top one on, in pop order), one per lane, and loads their NK rows
+// together.  Popping them one by one pops c_j right after c_{j-1} exactly
+// when no key queued by c_0..c_{j-1} comes before c_j; a queued key is a
+// neighbour key not yet visited, so a prefix scan over the lanes of the best
+// such key finds the longest prefix c_0..c_{V-1} (V >= 1) that the one-by-one
+// propagation pops in that order.  The round pops that prefix (visiting
+// order, queue bits cleared) and queues its new neighbours; the rest of the
+// candidates stay queued.  The visiting order is the one-by-one order.
 struct KeyQueue {
     unsigned* q1; unsigned* q2; unsigned* q3; unsigned* vis;
     int n1, n2, n3;                        // words per level (n3 <= 32)
+    int* candk;                            // the round's candidate keys (32 slots)
 };
 
 __device__ __forceinline__ void kq_push(const KeyQueue& Q, int k) {
@@ -943,51 +956,61 @@ __device__ __forceinline__ void kq_push(const KeyQueue& Q, int k) {
     atomicOr(Q.q3 + (k >> 15), 1u << ((k >> 10) & 31));
 }
 
+// index of the level-1 word that holds the highest (lowest) queued key, -1 if
+// the queue is empty
 template <bool MAXF>
-__device__ __forceinline__ int kq_pop(const KeyQueue& Q, int lane) {
+__device__ __forceinline__ int kq_top_word(const KeyQueue& Q, int lane) {
     const unsigned w3l = lane < Q.n3 ? Q.q3[lane] : 0u;
     const unsigned m3 = __ballot_sync(0xffffffffu, w3l != 0u);
     if (!m3) return -1;
     const int l3 = MAXF ? 31 - __clz(m3) : __ffs(m3) - 1;
     const unsigned w3 = __shfl_sync(0xffffffffu, w3l, l3);
-    const int b3 = MAXF ? 31 - __clz(w3) : __ffs(w3) - 1;
-    const int i2 = l3 * 32 + b3;
+    const int i2 = l3 * 32 + (MAXF ? 31 - __clz(w3) : __ffs(w3) - 1);
     if (i2 >= Q.n2) return -1;                 // inconsistent levels: reported as empty (an error)
     const unsigned w2 = Q.q2[i2];
     if (w2 == 0u) return -1;
-    const int b2 = MAXF ? 31 - __clz(w2) : __ffs(w2) - 1;
-    const int i1 = i2 * 32 + b2;
-    if (i1 >= Q.n1) return -1;
-    const unsigned w1 = Q.q1[i1];
-    if (w1 == 0u) return -1;
-    const int b1 = MAXF ? 31 - __clz(w1) : __ffs(w1) - 1;
-    __syncwarp();
-    if (lane == 0) {
-        const unsigned n1 = w1 & ~(1u << b1);
-        Q.q1[i1] = n1;
-        if (!n1) {
-            const unsigned n2 = w2 & ~(1u << b2);
-            Q.q2[i2] = n2;
-            if (!n2) Q.q3[l3] = w3 & ~(1u << b3);
-        }
-    }
-    __syncwarp();
-    return i1 * 32 + b1;
+    const int i1 = i2 * 32 + (MAXF ? 31 - __clz(w2) : __ffs(w2) - 1);
+    return i1 < Q.n1 ? i1 : -1;
+}
+
+// removes key k from the queue (lanes may remove keys of one word at once:
+// the lane whose removal empties a word clears its summary bit)
+__device__ __forceinline__ void kq_remove(const KeyQueue& Q, int k) {
+    const unsigned b1 = 1u << (k & 31);
+    if ((atomicAnd(Q.q1 + (k >> 5), ~b1) & ~b1) != 0u) return;
+    const unsigned b2 = 1u << ((k >> 5) & 31);
+    if ((atomicAnd(Q.q2 + (k >> 10), ~b2) & ~b2) != 0u) return;
+    atomicAnd(Q.q3 + (k >> 15), ~(1u << ((k >> 10) & 31)));
 }
 
 // One propagation in key space over the keys Lk (a permutation of 0..r-1; Lk
-// may be L2 itself); L2 gets the visiting order.  Returns the last key popped (the maxima flood) or
-// 0, or -2 if R was not covered.
+// may be L2 itself); L2 gets the visiting order.  Returns the last key popped
+// (the maxima flood) or 0, or -2 if R was not covered.
 template <bool MAXF, int NN>
 __device__ int wr_flood_keys(const WarpRegion& R, const int* Lk, int* NK, int* ordk, const KeyQueue& Q, int lane) {
     const int r = R.r;
-    for (int i = lane; i < r; i += 32) {
-        const int k = Lk[i];
+    // NK from the local adjacency, four vertices per lane in flight
+    constexpr int U = 4;
+    for (int i0 = lane; i0 < r; i0 += 32 * U) {
+        int k[U];
+        int j[U][NN];
 #pragma unroll
-        for (int q = 0; q < NN; ++q) {
-            const int j = R.adj[(long long)i * NN + q];
-            NK[(long long)k * NN + q] = j >= 0 ? Lk[j] : -1;
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + 32 * u;
+            k[u] = i < r ? Lk[i] : -1;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) j[u][q] = i < r ? R.adj[(long long)i * NN + q] : -1;
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < NN; ++q) j[u][q] = j[u][q] >= 0 ? Lk[j[u][q]] : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k[u] >= 0) {
+#pragma unroll
+                for (int q = 0; q < NN; ++q) NK[(long long)k[u] * NN + q] = j[u][q];
+            }
     }
     for (int w = lane; w < Q.n1; w += 32) { Q.q1[w] = 0u; Q.vis[w] = 0u; }
     for (int w = lane; w < Q.n2; w += 32) Q.q2[w] = 0u;
@@ -1009,32 +1032,167 @@ __device__ int wr_flood_keys(const WarpRegion& R, const int* Lk, int* NK, int* o
     }
     __syncwarp();
     int cnt = 0, last = -1;
-    for (;;) {
-        const int k = kq_pop<MAXF>(Q, lane);
-        if (k < 0 || cnt == r) break;               // at most r pops: every key is pushed once
-        if (lane == 0) ordk[k] = MAXF ? r - 1 - cnt : cnt;
-        ++cnt;
-        last = k;
-        if (lane < NN) {
-            const int kk = NK[(long long)k * NN + lane];
-            if (kk >= 0) {
-                const unsigned bit = 1u << (kk & 31);
-                if (!(atomicOr(Q.vis + (kk >> 5), bit) & bit)) kq_push(Q, kk);
+    // Rounds pay off where the queue is wide; on a thin region (a path-like
+    // propagation) most rounds pop one key, and single pops are cheaper: after
+    // 32 rounds that popped fewer than 48 keys the propagation pops one key at
+    // a time for the next 512 pops, then tries rounds again.
+    int rounds = 0, round_pops = 0, singles = 0;
+    while (cnt < r) {
+        const int w0 = kq_top_word<MAXF>(Q, lane);
+        if (w0 < 0) break;
+        if (singles > 0) {
+            --singles;
+            const unsigned w1 = Q.q1[w0];
+            if (!w1) break;                         // inconsistent levels: reported as an error
+            const int k = (w0 << 5) + (MAXF ? 31 - __clz(w1) : __ffs(w1) - 1);
+            __syncwarp();
+            if (lane == 0) {
+                ordk[k] = MAXF ? r - 1 - cnt : cnt;
+                kq_remove(Q, k);
+            }
+            ++cnt;
+            last = k;
+            __syncwarp();
+            if (lane < NN) {
+                const int kk = NK[(long long)k * NN + lane];
+                if (kk >= 0) {
+                    const unsigned bit = 1u << (kk & 31);
+                    if (!(atomicOr(Q.vis + (kk >> 5), bit) & bit)) kq_push(Q, kk);
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        // candidates: the set bits of the 32 words from w0 on, in pop order
+        const int wi = MAXF ? w0 - lane : w0 + lane;
+        unsigned w = (wi >= 0 && wi < Q.n1) ? Q.q1[wi] : 0u;
+        const int nb = __popc(w);
+        int x = nb;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        int slot = x - nb;
+        while (w && slot < 32) {
+            const int bt = MAXF ? 31 - __clz(w) : __ffs(w) - 1;
+            Q.candk[slot++] = (wi << 5) + bt;
+            w &= ~(1u << bt);
+        }
+        const int nc = min(32, __shfl_sync(0xffffffffu, x, 31));
+        __syncwarp();
+        const int c = lane < nc ? Q.candk[lane] : -1;
+        int nk[NN];
+#pragma unroll
+        for (int q = 0; q < NN; ++q) nk[q] = c >= 0 ? NK[(long long)c * NN + q] : -1;
+        // the best key that popping c would queue (not visited yet)
+        int best = MAXF ? -1 : INT_MAX;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const int kk = nk[q];
+            if (kk >= 0 && !(Q.vis[kk >> 5] & (1u << (kk & 31)))) best = MAXF ? max(best, kk) : min(best, kk);
+        }
+        // the best key queued by the candidates before this lane's
+        int pre = best;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, pre, d);
+            if (lane >= d) pre = MAXF ? max(pre, y) : min(pre, y);
+        }
+        pre = __shfl_up_sync(0xffffffffu, pre, 1);
+        if (lane == 0) pre = MAXF ? -1 : INT_MAX;
+        const unsigned okm = __ballot_sync(0xffffffffu, c >= 0 && (MAXF ? pre < c : pre > c));
+        const int V = min(okm == 0xffffffffu ? 32 : __ffs(~okm) - 1, r - cnt);
+        if (V <= 0) break;                          // cannot happen: the top key is always popped
+        if (lane < V) {
+            ordk[c] = MAXF ? r - 1 - (cnt + lane) : cnt + lane;
+            kq_remove(Q, c);
+        }
+        __syncwarp();
+        if (lane < V) {
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                const int kk = nk[q];
+                if (kk >= 0) {
+                    const unsigned bit = 1u << (kk & 31);
+                    if (!(atomicOr(Q.vis + (kk >> 5), bit) & bit)) kq_push(Q, kk);
+                }
             }
         }
         __syncwarp();
+        last = __shfl_sync(0xffffffffu, c, V - 1);
+        cnt += V;
+        round_pops += V;
+        if (++rounds == 32) {
+            if (round_pops < 48) singles = 512;
+            rounds = round_pops = 0;
+        }
     }
+#pragma unroll 4
     for (int i = lane; i < r; i += 32) R.L2[i] = ordk[Lk[i]];
     __syncwarp();
     return cnt == r ? (MAXF ? last : 0) : -2;
+}
+
+// The scans below run one lane per vertex with kScanU vertices per lane in
+// flight (all their adjacency entries, then all their neighbours' orders), so
+// that the warp of a large region waits for one round of loads per 32 * kScanU
+// vertices instead of one per neighbour.
+constexpr int kScanU = 4;
+
+// Whether vertex i is a strict local minimum and maximum of L among its
+// neighbours in R, for the kScanU vertices b + lane + 32 u (u < kScanU) below
+// lim; li gets their L.
+template <int NN>
+__device__ __forceinline__ void wr_scan_ext(const WarpRegion& R, int b, int lim, int lane, int (&li)[kScanU],
+                                            bool (&is_min)[kScanU], bool (&is_max)[kScanU]) {
+    int lj[kScanU][NN];
+#pragma unroll
+    for (int u = 0; u < kScanU; ++u) {
+        const int i = b + lane + 32 * u;
+        li[u] = i < lim ? R.L[i] : 0;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) lj[u][q] = i < lim ? R.adj[(long long)i * NN + q] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kScanU; ++u)
+#pragma unroll
+        for (int q = 0; q < NN; ++q) lj[u][q] = lj[u][q] >= 0 ? R.L[lj[u][q]] : -1;
+#pragma unroll
+    for (int u = 0; u < kScanU; ++u) {
+        bool mn = true, mx = true;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const int l = lj[u][q];      // -1: no neighbour in R (L is never negative here)
+            if (l >= 0 && l < li[u]) mn = false;
+            if (l > li[u]) mx = false;
+        }
+        is_min[u] = mn;
+        is_max[u] = mx;
+    }
 }
 
 // some vertex (not s, for minima: without an outside neighbour) is a strict
 // local minimum (MINF) or maximum of L
 template <bool MINF, int NN>
 __device__ bool wr_has_extremum(const WarpRegion& R, int lane) {
-    bool found = false;
     const int lim = MINF ? R.r : R.m;
+    if (R.adj) {
+        for (int b = 0; b < lim; b += 32 * kScanU) {
+            int li[kScanU];
+            bool mn[kScanU], mx[kScanU];
+            wr_scan_ext<NN>(R, b, lim, lane, li, mn, mx);
+            bool found = false;
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const int i = b + lane + 32 * u;
+                if (i < lim && (MINF ? (mn[u] && !(R.F[i] & kBnd)) : mx[u])) found = true;
+            }
+            if (__any_sync(0xffffffffu, found)) return true;
+        }
+        return false;
+    }
+    bool found = false;
     for (int i = lane; i < lim && !found; i += 32) {
         if (MINF && (R.F[i] & kBnd)) continue;
         const int li = R.L[i];
@@ -1052,6 +1210,25 @@ __device__ bool wr_has_extremum(const WarpRegion& R, int lane) {
 template <int NN>
 __device__ bool wr_mark_seeds(const WarpRegion& R, int lane, bool literal) {
     bool any = false;
+    if (R.adj) {
+        for (int b = 0; b < R.m; b += 32 * kScanU) {
+            int li[kScanU];
+            bool mn[kScanU], mx[kScanU];
+            if (literal) wr_scan_ext<NN>(R, b, R.m, lane, li, mn, mx);
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const int i = b + lane + 32 * u;
+                if (i < R.m) {
+                    const unsigned char f = R.F[i];
+                    const bool sd = (f & kBnd) && (!literal || mn[u]);
+                    R.F[i] = (unsigned char)(sd ? (f | kSeed) : (f & ~kSeed));
+                    any |= sd;
+                }
+            }
+        }
+        __syncwarp();
+        return __any_sync(0xffffffffu, any);
+    }
     for (int i = lane; i < R.m; i += 32) {
         bool sd = (R.F[i] & kBnd) != 0;
         if (sd && literal) {
@@ -1102,28 +1279,52 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         Q.n3 = (Q.n2 + 31) >> 5;
         unsigned* sm = reinterpret_cast<unsigned*>(H);
         Q.q1 = sm; Q.vis = sm + Q.n1; Q.q2 = sm + 2 * Q.n1; Q.q3 = sm + 2 * Q.n1 + Q.n2;
+        Q.candk = reinterpret_cast<int*>(Q.q3 + 32);
         const bool keyspace = adj && nbase + (long long)NN * (m + 1) <= a.lo_adj_cap && Q.n3 <= 32 &&
-                              2LL * Q.n1 + Q.n2 + 32 <= 2LL * kWarpHeapCap;
+                              2LL * Q.n1 + Q.n2 + 64 <= 2LL * kWarpHeapCap;
         int* NK = keyspace ? a.lo_adj + nbase : nullptr;
         int* ordk = a.lo_heap + off;
-        for (int i = lane; i <= m; i += 32) {
-            const int vtx = i < m ? a.members[st0 + i] : s;
-            R.V[i] = vtx;
-            int x, y, z;
-            coords_of(g, vtx, x, y, z);
-            unsigned char fl = 0;
-            for (int q = 0; q < NN; ++q) {
-                const int nb = nbr_of(g, x, y, z, q);
-                int j = -1;
-                if (nb == s) j = m;
-                else if (nb >= 0) {
-                    if (__ldg(a.owner + nb) != R.tag) fl = kBnd;
-                    else j = __ldg(a.loc + nb);
-                }
-                if (adj) adj[(long long)i * NN + q] = j;
+        // members, flags, l0 and the local adjacency, kScanU vertices per lane in flight
+        for (int b = 0; b <= m; b += 32 * kScanU) {
+            int vtx[kScanU], ov[kScanU];
+            int nb[kScanU][NN], j[kScanU][NN];
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const int i = b + lane + 32 * u;
+                vtx[u] = i < m ? a.members[st0 + i] : (i == m ? s : -1);
             }
-            R.F[i] = fl;
-            R.L[i] = i < m ? od<DIR>(__ldg(a.O + vtx), g.n) : INT_MAX;
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                int x = 0, y = 0, z = 0;
+                if (vtx[u] >= 0) coords_of(g, vtx[u], x, y, z);
+#pragma unroll
+                for (int q = 0; q < NN; ++q) nb[u][q] = vtx[u] >= 0 ? nbr_of(g, x, y, z, q) : -1;
+                ov[u] = vtx[u] >= 0 && vtx[u] != s ? __ldg(a.O + vtx[u]) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u)
+#pragma unroll
+                for (int q = 0; q < NN; ++q)
+                    j[u][q] = nb[u][q] >= 0 && nb[u][q] != s ? __ldg(a.owner + nb[u][q]) : 0;
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const int i = b + lane + 32 * u;
+                if (vtx[u] < 0) continue;
+                R.V[i] = vtx[u];
+                unsigned char fl = 0;
+#pragma unroll
+                for (int q = 0; q < NN; ++q) {
+                    int jj = -1;
+                    if (nb[u][q] == s) jj = m;
+                    else if (nb[u][q] >= 0) {
+                        if (j[u][q] != R.tag) fl = kBnd;
+                        else jj = __ldg(a.loc + nb[u][q]);
+                    }
+                    if (adj) adj[(long long)i * NN + q] = jj;
+                }
+                R.F[i] = fl;
+                R.L[i] = i < m ? od<DIR>(ov[u], g.n) : INT_MAX;
+            }
         }
         R.adj = adj;
         __syncwarp();
@@ -1137,6 +1338,7 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         bool dense = false;
         if (keyspace) {
             int mn = INT_MAX, mx = INT_MIN;
+            #pragma unroll 4
             for (int i = lane; i < m; i += 32) { mn = min(mn, R.L[i]); mx = max(mx, R.L[i]); }
             mn = __reduce_min_sync(0xffffffffu, mn);
             mx = __reduce_max_sync(0xffffffffu, mx);
@@ -1200,8 +1402,12 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         };
         for (;;) {
             int best = INT_MAX, bi = -1;
-            for (int i = lane; i < m; i += 32)
-                if ((R.F[i] & (kBnd | kTried)) == kBnd && R.L[i] < best) { best = R.L[i]; bi = i; }
+#pragma unroll 4
+            for (int i = lane; i < m; i += 32) {
+                const unsigned char f = R.F[i];
+                const int l = R.L[i];
+                if ((f & (kBnd | kTried)) == kBnd && l < best) { best = l; bi = i; }
+            }
             const int K = __reduce_min_sync(0xffffffffu, best);
             if (K == INT_MAX) break;
             ai = __shfl_sync(0xffffffffu, bi, __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1);
@@ -1228,6 +1434,7 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
                     if (last == -3) { overflow = true; break; }
                     if (last != ai) break;
                 }
+                #pragma unroll 4
                 for (int i = lane; i < R.r; i += 32) { R.L[i] = R.L2[i]; P[i] = R.L2[i]; }
                 __syncwarp();
                 int fl = 1, res = 0;            // res: 1 done, -1 does not end, -2 error, -3 overflow
@@ -1240,6 +1447,7 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
                                               : wr_flood<false, NN>(R, H, lane);
                     if (rmin == -3) { res = -3; break; }
                     if (rmin < 0) { res = -2; break; }
+                    #pragma unroll 4
                     for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
                     __syncwarp();
                     if (!wr_has_extremum<false, NN>(R, lane)) { res = 1; break; }
@@ -1248,13 +1456,16 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
                                               : wr_flood<true, NN>(R, H, lane);
                     if (rmax == -3) { res = -3; break; }
                     if (rmax < 0) { res = -2; break; }
+                    #pragma unroll 4
                     for (int i = lane; i < R.r; i += 32) R.L[i] = R.L2[i];
                     __syncwarp();
                     if (literal) {
                         bool same = true;
+                        #pragma unroll 4
                         for (int i = lane; i < R.r; i += 32) same &= P[i] == R.L[i];
                         if (__all_sync(0xffffffffu, same)) { res = -1; break; }
                         if (++lam == power) {
+                            #pragma unroll 4
                             for (int i = lane; i < R.r; i += 32) P[i] = R.L[i];
                             __syncwarp();
                             power *= 2;
@@ -1291,6 +1502,7 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
             if (lane == 0) set_status(&a.ctr->status, LTS_ERR_INTERNAL);
             continue;
         }
+        #pragma unroll 4
         for (int i = lane; i < m; i += 32) a.lhat[st0 + i] = R.L[i];
         mx = max(mx, nfl);
         tot += nfl;
