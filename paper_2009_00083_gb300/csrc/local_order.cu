@@ -1245,6 +1245,69 @@ __device__ bool wr_mark_seeds(const WarpRegion& R, int lane, bool literal) {
     return __any_sync(0xffffffffu, any);
 }
 
+// The first propagation with candidate a at minus infinity ends on a exactly
+// when R \ {a} is connected.  Candidates that cut off a few vertices are
+// common on thin regions, so before propagating, a bounded search from each
+// neighbour of a in R (but s) over R \ {a} looks for such a piece: a search
+// that ends within kCutBudget vertices without reaching s, or a vertex that
+// an earlier search for a reached, has found one, and a is then not the
+// minus-infinity vertex.  mark[] holds a * 16 + t for the vertices reached by
+// the t-th search for a (other values otherwise); q is kCutBudget + 1 ints of
+// shared memory.  false: no such piece within the budget (the propagation
+// decides).
+constexpr int kCutBudget = 64;
+
+template <int NN>
+__device__ bool wr_cuts(const WarpRegion& R, int ai, int* mark, int* q, int lane) {
+    const int nb = lane < NN ? R.adj[(long long)ai * NN + lane] : -1;
+    unsigned todo = __ballot_sync(0xffffffffu, nb >= 0 && nb != R.m);
+    const int base = ai * 16;
+    int t = 0;
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int b0 = __shfl_sync(0xffffffffu, nb, src);
+        const int mb = __ldcg(mark + b0);
+        if (mb >= base && mb < base + 16) continue;   // reached by an earlier search for a
+        const int stamp = base + t++;
+        __syncwarp();
+        if (lane == 0) {
+            __stcg(mark + b0, stamp);
+            q[0] = b0;
+            q[kCutBudget] = 1;
+        }
+        __syncwarp();
+        int head = 0;
+        bool reach = false, over = false;
+        for (;;) {
+            const int tail = q[kCutBudget];
+            if (head >= tail) break;
+            const int i = head + lane < tail ? q[head + lane] : -1;
+            head = min(tail, head + 32);
+            bool rs = false;
+            if (i >= 0) {
+#pragma unroll
+                for (int k = 0; k < NN; ++k) {
+                    const int j = R.adj[(long long)i * NN + k];
+                    if (j < 0 || j == ai) continue;
+                    if (j == R.m) { rs = true; continue; }
+                    const int old = atomicExch(mark + j, stamp);
+                    if (old == stamp) continue;
+                    if (old >= base && old < base + 16) { rs = true; continue; }   // joins an earlier search's piece
+                    const int slot = atomicAdd(q + kCutBudget, 1);
+                    if (slot < kCutBudget) q[slot] = j;
+                }
+            }
+            __syncwarp();
+            reach = __any_sync(0xffffffffu, rs);
+            over = q[kCutBudget] > kCutBudget;
+            if (reach || over) break;
+        }
+        if (!reach && !over) return true;
+    }
+    return false;
+}
+
 template <int DIR, int NN>
 __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int* list, const int* d_count) {
     extern __shared__ unsigned long long H[];
@@ -1281,7 +1344,7 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
         Q.q1 = sm; Q.vis = sm + Q.n1; Q.q2 = sm + 2 * Q.n1; Q.q3 = sm + 2 * Q.n1 + Q.n2;
         Q.candk = reinterpret_cast<int*>(Q.q3 + 32);
         const bool keyspace = adj && nbase + (long long)NN * (m + 1) <= a.lo_adj_cap && Q.n3 <= 32 &&
-                              2LL * Q.n1 + Q.n2 + 64 <= 2LL * kWarpHeapCap;
+                              2LL * Q.n1 + Q.n2 + 64 + kCutBudget + 1 <= 2LL * kWarpHeapCap;
         int* NK = keyspace ? a.lo_adj + nbase : nullptr;
         int* ordk = a.lo_heap + off;
         // members, flags, l0 and the local adjacency, kScanU vertices per lane in flight
@@ -1400,6 +1463,13 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
             __syncwarp();
             return wr_flood<true, NN>(R, H, lane);
         };
+        // the bounded searches of wr_cuts: marks in P (free until the alternation), queue at the end of H
+        int* cutq = reinterpret_cast<int*>(H + kWarpHeapCap) - (kCutBudget + 1);
+        if (R.adj) {
+#pragma unroll 4
+            for (int i = lane; i <= m; i += 32) P[i] = -1;
+            __syncwarp();
+        }
         for (;;) {
             int best = INT_MAX, bi = -1;
 #pragma unroll 4
@@ -1412,6 +1482,11 @@ __global__ void __launch_bounds__(32) lo_warp_kernel(Geom g, LOArgs a, const int
             if (K == INT_MAX) break;
             ai = __shfl_sync(0xffffffffu, bi, __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1);
             __syncwarp();
+            if (R.adj && m < (1 << 26) && wr_cuts<NN>(R, ai, P, cutq, lane)) {   // marks ai * 16 + t fit an int
+                if (lane == 0) R.F[ai] |= kTried;
+                __syncwarp();
+                continue;
+            }
             const int last = first_flood(ai);
             if (last == -3) { overflow = true; break; }
             if (last == -2) break;
