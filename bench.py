@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2009_00083_gb300 import workloads as W  # noqa: E402
+from paper_2009_00083_gb300 import autotune  # noqa: E402
 
 METRIC = "LTS Mvertices/s (bit-exact vs oracle), batched vs plain per-field; serve p50/p99"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -65,7 +66,7 @@ STAGE_BYTES = {"order_field": (64, "vertex"), "classify": (8, "vertex"), "reorde
 #   order field: the two-pass sort on compressed keys (the recipe's fields have
 #     few distinct values; the algorithmic count above stays the general one)
 #   propagate: first_step_kernel + propagate_kernel, both passes
-STAGE_TRAFFIC = {"order_field": 41.7, "propagate": 799.0}
+STAGE_TRAFFIC = {"order_field": 41.7, "propagate": 677.0}
 PATH_BYTES_PER_VERTEX = 100   # sort + classify + flatten, both passes
 
 
@@ -322,6 +323,7 @@ def batch_leg(lts, torch, dev, reps=3, ranks=None):
     ids = [torch.from_numpy(a).to(dev) for a in auth]
     total = sum(sizes)
     ctx = lts.Context(max(f.numel() for f in fields), device=dev.index)
+    tuning = autotune.apply(ctx, key="batch")       # the autotuner's cached choice for this batch
     outs = [(torch.empty_like(f), torch.empty(f.shape, dtype=torch.int32, device=dev)) for f in fields]
     grids = [lts.grid_of_shape(tuple(f.shape)) for f in fields]
 
@@ -363,7 +365,7 @@ def batch_leg(lts, torch, dev, reps=3, ranks=None):
     return {"workload": "mixed_batch_256: 128 2D squares (side 64..1024) + 128 3D cubes (side 32..160)",
             "fields": len(specs), "vertices": total, "plain_mvps": round(total / tp / 1e6, 1),
             "batched_mvps": round(total / tb / 1e6, 1), "plain_ms": round(tp * 1e3, 2),
-            "batched_ms": round(tb * 1e3, 2), "parity_vs_oracle": bool(parity),
+            "batched_ms": round(tb * 1e3, 2), "parity_vs_oracle": bool(parity), "tuning": tuning,
             "ranks": ranks.world, "sharding": "by field, largest first to the least loaded rank",
             "timing": "wall clock around synchronized calls (slowest rank), median of up to 3 after a warm-up, "
                       "inputs on the device"}
@@ -585,6 +587,7 @@ def main():
     n = f.size
     stream = torch.cuda.current_stream(dev)
     ctx = lts.Context(n, device=local, stream=stream)
+    tuning = autotune.apply(ctx, f.shape)          # the autotuner's cached choice for this size bucket
     fd = torch.from_numpy(f).to(dev)
     idd = torch.from_numpy(ids).to(dev)
     g = torch.empty_like(fd)
@@ -682,7 +685,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
         "config": {"workload": args.workload, "shape": list(f.shape), "vertices": n,
                    "authorized": int(ids.size), "mode": "both", "l2": "inputs (512 MB) larger than L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "tuning": tuning},
         "parity_vs_oracle": bool(parity),
         "batch": batch,
         "serve": serve,

@@ -250,6 +250,29 @@ lts_status lts_poll(lts_ctx* ctx, uint64_t ticket, int* done);
  * Errors: LTS_ERR_ARG (max_concurrent outside [0, 15], negative budget). */
 lts_status lts_serve_config(lts_ctx* ctx, int32_t max_concurrent, int64_t hbm_budget_bytes);
 
+/* Launch tuning of a context (the paper has no counterpart: these are
+ * resource choices of this library, picked per workload by the package's
+ * autotuner).  A field of 0 keeps the default.
+ *   engine_blocks_per_sm: resident 128-thread blocks per multiprocessor of
+ *     the persistent propagation engine (1..8; default 8);
+ *   team_blocks_per_sm: blocks per multiprocessor of the 16- and 32-lane
+ *     local-order team kernels (1..16; default 12);
+ *   batch_workspaces: workspaces lts_simplify_batch spreads a batch over,
+ *     the context's own included (1..32; default 32).
+ * The tuning changes no result, only the launch shapes, and applies to the
+ * calls that start after it.  lts_set_tuning with NULL restores the
+ * defaults; LTS_ERR_ARG for a value outside its range (nothing changes).
+ * lts_get_tuning writes the values in force (defaults as numbers). */
+typedef struct lts_tuning {
+    int32_t engine_blocks_per_sm;
+    int32_t team_blocks_per_sm;
+    int32_t batch_workspaces;
+    int32_t reserved[5];          /* must be 0 */
+} lts_tuning;
+
+lts_status lts_set_tuning(lts_ctx* ctx, const lts_tuning* tuning);
+lts_status lts_get_tuning(const lts_ctx* ctx, lts_tuning* out);
+
 /* Message describing the last error on this context ("" if none). */
 const char* lts_last_error(const lts_ctx* ctx);
 

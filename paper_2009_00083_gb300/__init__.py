@@ -16,6 +16,7 @@ __all__ = [
     "LtsGrid", "LtsStats", "LtsError", "Context", "lts_create", "lts_simplify", "lts_destroy",
     "lts_workspace_bytes", "lts_last_error", "lts_order_field_static", "lts_simplify_batch", "lts_submit",
     "lts_poll", "lts_simplify_persistence", "lts_simplify_f64", "lts_classify", "lts_serve_config", "library_path",
+    "LtsTuning", "lts_set_tuning", "lts_get_tuning",
     "load", "simplify",
     "simplify_persistence",
     "MODE_MIN", "MODE_MAX", "MODE_BOTH", "ORDER_STATIC_MAX_VERTICES",
@@ -36,6 +37,15 @@ STATUS = {0: "LTS_OK", 1: "LTS_ERR_ARG", 2: "LTS_ERR_NAN", 3: "LTS_ERR_NO_AUTHOR
 
 class LtsGrid(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int32), ("dims", ctypes.c_int64 * 3)]
+
+
+class LtsTuning(ctypes.Structure):
+    _fields_ = [("engine_blocks_per_sm", ctypes.c_int32), ("team_blocks_per_sm", ctypes.c_int32),
+                ("batch_workspaces", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+    def as_dict(self):
+        return {"engine_blocks_per_sm": self.engine_blocks_per_sm, "team_blocks_per_sm": self.team_blocks_per_sm,
+                "batch_workspaces": self.batch_workspaces}
 
 
 class LtsStats(ctypes.Structure):
@@ -123,6 +133,10 @@ def load():
         lib.lts_poll.restype = ctypes.c_int
         lib.lts_serve_config.argtypes = [P, ctypes.c_int32, ctypes.c_int64]
         lib.lts_serve_config.restype = ctypes.c_int
+        lib.lts_set_tuning.argtypes = [P, ctypes.POINTER(LtsTuning)]
+        lib.lts_set_tuning.restype = ctypes.c_int
+        lib.lts_get_tuning.argtypes = [P, ctypes.POINTER(LtsTuning)]
+        lib.lts_get_tuning.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -227,6 +241,26 @@ def lts_serve_config(ctx, max_concurrent: int, hbm_budget_bytes: int) -> int:
     return load().lts_serve_config(ctx, int(max_concurrent), int(hbm_budget_bytes))
 
 
+def lts_set_tuning(ctx, tuning: dict | None) -> int:
+    """Sets the context's launch tuning from a dict of LtsTuning fields (None: defaults)."""
+    if tuning is None:
+        return load().lts_set_tuning(ctx, None)
+    t = LtsTuning()
+    for k, v in tuning.items():
+        if k not in ("engine_blocks_per_sm", "team_blocks_per_sm", "batch_workspaces"):
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    return load().lts_set_tuning(ctx, ctypes.byref(t))
+
+
+def lts_get_tuning(ctx) -> dict:
+    t = LtsTuning()
+    code = load().lts_get_tuning(ctx, ctypes.byref(t))
+    if code != 0:
+        raise LtsError(code, "lts_get_tuning")
+    return t.as_dict()
+
+
 def lts_order_field_static(device: int, grid: LtsGrid, d_field: int, d_order: int, cuda_stream: int = 0):
     """Order field with the library's static scratch (no allocation); returns (status, message)."""
     buf = ctypes.create_string_buffer(256)
@@ -319,6 +353,15 @@ class Context:
         if code != 0:
             raise LtsError(code, lts_last_error(self._ctx))
         return outs, ([st[i].as_dict() for i in range(len(fields))] if st is not None else None)
+
+    def set_tuning(self, tuning: dict | None = None):
+        """Launch tuning (see lts_set_tuning); None restores the defaults."""
+        code = lts_set_tuning(self._ctx, tuning)
+        if code != 0:
+            raise LtsError(code, lts_last_error(self._ctx))
+
+    def tuning(self) -> dict:
+        return lts_get_tuning(self._ctx)
 
     def serve_config(self, max_concurrent: int, hbm_budget_bytes: int = 120 << 30):
         code = lts_serve_config(self._ctx, max_concurrent, hbm_budget_bytes)

@@ -35,6 +35,7 @@
 //     with the key-indexed adjacency in HBM scratch (a 32-ary heap in shared
 //     memory when the scratch pool is spent, and one region per lane with
 //     binary heaps in HBM scratch when that heap overflows).
+#include <algorithm>
 #include <climits>
 
 #include "lts_internal.cuh"
@@ -1610,8 +1611,9 @@ void launch_tiers(Work& w, const Geom& g, const LOArgs& a, int sms, cudaStream_t
         for (int i = 0; i < 3; ++i) cudaStreamWaitEvent(w.aux[i], w.fork_ev, 0);
         s0 = w.aux[0]; s1 = w.aux[1]; s2 = w.aux[2];
     }
-    lo_team_kernel<DIR, NN, 16><<<sms * 12, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t16);
-    lo_team_kernel<DIR, NN, 32><<<sms * 12, 128, 0, s2>>>(g, a, tl, &w.ctr->n_t32);
+    const int tb = sms * std::max(1, std::min(w.team_bpsm, 16));
+    lo_team_kernel<DIR, NN, 16><<<tb, 128, 0, s>>>(g, a, w.tier_list, &w.ctr->n_t16);
+    lo_team_kernel<DIR, NN, 32><<<tb, 128, 0, s2>>>(g, a, tl, &w.ctr->n_t32);
     lo_dense_kernel<DIR, NN, 128, 4><<<sms * 10, 128, small, s1>>>(g, a, tl + q, &w.ctr->n_med);
     lo_dense_kernel<DIR, NN, kMedR, 1><<<sms * 5, 32, large, s0>>>(g, a, tl + 2 * q, &w.ctr->n_large);
     lo_dense_kernel<DIR, NN, kHugeR, 1><<<sms, 32, huge, s0>>>(g, a, tl + 3 * q, &w.ctr->n_huge);

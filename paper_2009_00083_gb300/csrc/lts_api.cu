@@ -81,6 +81,7 @@ struct lts_ctx {
     int serve_max = kMaxServe;        // serving workspaces (lanes 1..serve_max); 0: the context's own
     long long serve_budget = 120LL << 30;
     std::deque<std::pair<unsigned long long, long long>> inflight[kMaxLanes];   // (ticket, vertices) per lane
+    lts_tuning tune{};                // launch tuning (0: default)
 };
 
 namespace {
@@ -184,6 +185,8 @@ lts_status lane_alloc(Lane& L, long long nmax, int sms, cudaStream_t stream, boo
     w.nblk = (int)z.nblk;
     w.scan_tmp_cap = (int)z.scan_tiles;
     w.sms = sms;
+    w.eng_bpsm = 8;
+    w.team_bpsm = 12;
     // tests only: LTS_TEST_MIN_TIER=k (1..5) runs step 2 of small regions in tier k
     // (the results do not depend on the tier)
     w.min_tier = 0;
@@ -656,6 +659,34 @@ void lts_destroy(lts_ctx* c) {
 
 const char* lts_last_error(const lts_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+lts_status lts_set_tuning(lts_ctx* c, const lts_tuning* t) {
+    if (!c) return LTS_ERR_ARG;
+    c->err.clear();
+    if (!t) {
+        c->tune = lts_tuning{};
+        return LTS_OK;
+    }
+    if (t->engine_blocks_per_sm < 0 || t->engine_blocks_per_sm > 8)
+        return fail(c, LTS_ERR_ARG, "engine_blocks_per_sm outside [0, 8]");
+    if (t->team_blocks_per_sm < 0 || t->team_blocks_per_sm > 16)
+        return fail(c, LTS_ERR_ARG, "team_blocks_per_sm outside [0, 16]");
+    if (t->batch_workspaces < 0 || t->batch_workspaces > kBatchLanes)
+        return fail(c, LTS_ERR_ARG, "batch_workspaces outside [0, 32]");
+    for (int r : t->reserved)
+        if (r != 0) return fail(c, LTS_ERR_ARG, "reserved tuning fields must be 0");
+    c->tune = *t;
+    return LTS_OK;
+}
+
+lts_status lts_get_tuning(const lts_ctx* c, lts_tuning* out) {
+    if (!c || !out) return LTS_ERR_ARG;
+    *out = lts_tuning{};
+    out->engine_blocks_per_sm = c->tune.engine_blocks_per_sm > 0 ? c->tune.engine_blocks_per_sm : 8;
+    out->team_blocks_per_sm = c->tune.team_blocks_per_sm > 0 ? c->tune.team_blocks_per_sm : 12;
+    out->batch_workspaces = c->tune.batch_workspaces > 0 ? c->tune.batch_workspaces : kBatchLanes;
+    return LTS_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -697,6 +728,12 @@ bool grow_pool(Lane& L, int pool) {
     return true;
 }
 
+// The context's launch tuning, copied into a workspace before a call uses it.
+void tune_lane(const lts_ctx* c, Lane& L) {
+    L.w.eng_bpsm = c->tune.engine_blocks_per_sm > 0 ? c->tune.engine_blocks_per_sm : 8;
+    L.w.team_bpsm = c->tune.team_blocks_per_sm > 0 ? c->tune.team_blocks_per_sm : 12;
+}
+
 lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const void* d_field, const Selection& sel, lts_mode mode,
                         void* d_out_field, int32_t* d_out_order, lts_stats* opt_stats, bool f64 = false) {
     Lane& L = c->lane[0];
@@ -715,6 +752,7 @@ lts_status simplify_one(lts_ctx* c, const lts_grid* gr, const void* d_field, con
     PassStats* hps = reinterpret_cast<PassStats*>(w.h_ctr + 1);
     int status = 0;
     for (int attempt = 0;; ++attempt) {
+        tune_lane(c, L);
         if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, nullptr, 0, f64)) !=
             cudaSuccess)
             return cuda_fail(c, L, e, "launch");
@@ -822,7 +860,7 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
     // the largest field, while the device has room for them (a batch runs on
     // as many as it could get; it needs at least one more than the context's
     // own when it has several fields)
-    int want = std::min(kBatchLanes, nf);
+    int want = std::min(c->tune.batch_workspaces > 0 ? c->tune.batch_workspaces : kBatchLanes, nf);
     const size_t per_lane = bytes_for(sizes_for(nbig, c->sms));
     for (int i = 1; i < want; ++i) {
         Lane& L = c->lane[i];
@@ -885,6 +923,7 @@ lts_status lts_simplify_batch(lts_ctx* c, int32_t nf, const lts_grid* grids, con
         Lane& L = c->lane[l];
         const Geom g = geom_of(&grids[i], n[i]);
         const Selection sel{d_authorized[i], n_authorized[i], false, 0.0};
+        tune_lane(c, L);
         if ((e = enqueue_simplify(L, g, d_fields[i], sel, mode, d_out_fields[i], d_out_orders[i], c->sms,
                                   c->batch_dev + i, 0)) != cudaSuccess)
             return cuda_fail(c, L, e, "launch");
@@ -954,6 +993,7 @@ lts_status lts_submit(lts_ctx* c, const lts_grid* gr, const float* d_field, cons
     }
     const Geom g = geom_of(gr, n);
     const Selection sel{d_authorized, n_authorized, false, 0.0};
+    tune_lane(c, L);
     if ((e = enqueue_simplify(L, g, d_field, sel, mode, d_out_field, d_out_order, c->sms, c->ring_dev + slot, t)) !=
         cudaSuccess)
         return cuda_fail(c, L, e, "launch");

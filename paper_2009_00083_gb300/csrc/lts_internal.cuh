@@ -192,6 +192,8 @@ struct Work {
     int min_tier;                        // tests only: step-2 regions go to at least this tier (0: by size)
     const unsigned long long* test_stall; // tests only: look-back words nothing sets, or null
     int sms;                             // multiprocessors of the workspace's device
+    int eng_bpsm;                        // resident blocks per SM of the propagation engine
+    int team_bpsm;                       // blocks per SM of the local-order team kernels
     unsigned char* link6; unsigned char* link14;   // link component tables of interior vertices (2D, 3D)
     unsigned long long* crit_counts;     // critical point counts of lts_classify
     int lanes;                           // propagation lanes (threads)

@@ -56,6 +56,7 @@
 // eps (with the global one): at a saddle where a class stops for good, the
 // class on the other side has a higher extremum, and a class that crossed a
 // saddle was within eps of its extremum there.
+#include <algorithm>
 #include <climits>
 
 #include <cuda/atomic>
@@ -787,7 +788,7 @@ cudaError_t launch_propagate(Work& w, const Geom& g, const int* O, const float* 
     a.vlog = w.vlog; a.vlog_cls = w.vlog_cls; a.log_cap = w.log_cap; a.tasks = w.tasks; a.ctr = w.ctr;
     a.F = F; a.eps = eps; a.ctop = w.ctop; a.authbits = w.authbits;
     const int pb = sms * 8;
-    const int blocks = w.lanes / kThreads;
+    const int blocks = std::min(w.lanes / kThreads, sms * std::max(1, std::min(w.eng_bpsm, 8)));
     if (g.nn == 14) {
         first_step_kernel<DIR, 14, PERS><<<pb, 256, 0, s>>>(g, O, a, w.tasks);
         propagate_kernel<DIR, 14, PERS><<<blocks, kThreads, 0, s>>>(g, O, a);

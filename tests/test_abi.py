@@ -27,7 +27,7 @@ def test_header_declares_the_boundary():
     assert declared_entry_points() == sorted(
         ["lts_create", "lts_workspace_bytes", "lts_simplify", "lts_last_error", "lts_destroy",
          "lts_order_field_static", "lts_simplify_batch", "lts_submit", "lts_poll", "lts_simplify_persistence",
-         "lts_serve_config", "lts_simplify_f64", "lts_classify"])
+         "lts_serve_config", "lts_simplify_f64", "lts_classify", "lts_set_tuning", "lts_get_tuning"])
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -56,6 +56,8 @@ def test_argument_checks_need_no_device(lib):
     assert lts.load().lts_poll(None, 1, None) == 1
     assert lts.load().lts_simplify_f64(None, ctypes.byref(g), None, None, 0, 3, None, None, None) == 1
     assert lts.load().lts_classify(None, ctypes.byref(g), None, None, None, None) == 1
+    assert lts.load().lts_set_tuning(None, None) == 1
+    assert lts.load().lts_get_tuning(None, None) == 1
 
 
 def test_static_order_field_rejects_oversize_grids_before_any_device_call(lib):
