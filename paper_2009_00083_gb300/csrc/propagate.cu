@@ -85,7 +85,7 @@ struct PropArgs {
     int* cnt;
     int* spill_base;
     int* spill_n;
-    int4* heaprec;               // a stopped class's overflow heap: (offset low, offset high, entries, capacity)
+    int4* heaprec;               // a stopped class's overflow queue: (table offset low, high, entries, 0)
     int* spill_pool;
     long long spill_cap;
     unsigned long long* heap_pool;
@@ -142,34 +142,262 @@ __device__ __forceinline__ unsigned long long pack(int key, int v) {
     return ((unsigned long long)(unsigned)key << 32) | (unsigned)v;
 }
 
-// The overflow heap of a team: a 32-ary max-heap in HBM (so a pop sifts down
-// one level per coalesced load of 32 children and a team reduction).  Lane 0
-// holds the state and pushes; pops are run by the whole team.
-struct Overflow {
-    unsigned long long* h;
-    int n, cap;
+// The overflow queue of a team (entries beyond the register frontier): a
+// radix queue in HBM.  Pops of a propagation come in decreasing order (a
+// vertex is taken only when every higher neighbour is in the class, so what
+// it queues is lower than it), and every queued key is at most the key of
+// the class's last pop.  So the queue keeps a base key b at least as high as
+// every key it holds and files an entry with key k in bucket 0 if k == b,
+// else in bucket 32 - clz(b ^ k) (the highest bit where they differ, + 1):
+// every key of a lower bucket is higher than every key of a higher one.  A
+// push appends to its bucket; a pop takes bucket 0 if it holds anything,
+// else refiles the lowest non-empty bucket under a new base, its highest key
+// (each entry moves to a lower bucket: a few moves per entry over its
+// life).  The team's bucket table (32 blocks of the HBM pool, with their
+// lengths and highest entries) lives in shared memory and every operation
+// is run by the whole team, so appends and refiling move 32 entries per
+// round of coalesced loads.  A class that stops leaves its buckets in the
+// pool with a copy of the table; the class that absorbs it refiles the
+// smaller queue into the larger one.
+struct RQ {
+    long long off[32];                 // pool offset of each bucket's block
+    int len[32], cap[32];
+    unsigned long long mx[32];         // each non-empty bucket's highest entry
+    int base;                          // every queued key is at most base
+    unsigned nz;                       // non-empty buckets
+    int total;                         // queued entries
+    long long tpos, tend;              // the team's reserve of pool words for stopped queues' tables
 };
 
-__device__ bool ov_push(Overflow& H, unsigned long long e, const PropArgs& a) {
-    if (H.n == H.cap) {
-        const int ncap = max(2 * H.cap, 256);
-        const long long off = atomicAdd((unsigned long long*)&a.ctr->heap_cursor, (unsigned long long)ncap);
-        if (off + ncap > a.heap_cap) { set_oom(a.ctr, 1); return false; }
-        unsigned long long* nh = a.heap_pool + off;
-        for (int i = 0; i < H.n; ++i) nh[i] = H.h[i];
-        if (H.cap == 0) atomicAdd(&a.ctr->heap_spills, 1);
-        H.h = nh;
-        H.cap = ncap;
+// one queue per team of the engine's blocks (shared memory)
+__shared__ RQ g_team_rq[kThreads / 32];
+
+__device__ __forceinline__ RQ& team_rq() { return g_team_rq[threadIdx.x >> 5]; }
+
+__device__ __forceinline__ int rq_bucket(int base, int key) {
+    return key == base ? 0 : 32 - __clz((unsigned)(base ^ key));
+}
+
+__device__ __forceinline__ void rq_reset(RQ& q, int lane) {
+    q.len[lane] = 0;
+    q.cap[lane] = 0;
+    q.off[lane] = 0;
+    q.mx[lane] = 0ull;
+    if (lane == 0) { q.base = INT_MAX; q.nz = 0u; q.total = 0; }
+    __syncwarp();
+}
+
+// key of the highest queued entry, -1 if the queue is empty
+__device__ __forceinline__ int rq_top(const RQ& q) {
+    return q.nz ? (int)(q.mx[__ffs(q.nz) - 1] >> 32) : -1;
+}
+
+// Bucket t gets room for `more` entries (a block twice as large from the
+// pool, the entries copied by the team).  false (uniform) when the pool is spent.
+__device__ bool rq_reserve(RQ& q, int t, int more, int lane, const PropArgs& a) {
+    const int len = q.len[t], cap = q.cap[t];
+    if (len + more <= cap) return true;
+    const int ncap = max(2 * cap, max(64, len + more));
+    long long noff = 0;
+    if (lane == 0) {
+        noff = (long long)atomicAdd((unsigned long long*)&a.ctr->heap_cursor, (unsigned long long)ncap);
+        if (noff + ncap > a.heap_cap) { set_oom(a.ctr, 1); noff = -1; }
+        else if (cap == 0 && q.total == 0) atomicAdd(&a.ctr->heap_spills, 1);
     }
-    int i = H.n++;
-    while (i > 0) {
-        const int p = (i - 1) >> 5;
-        const unsigned long long pe = H.h[p];
-        if (pe >= e) break;
-        H.h[i] = pe;
-        i = p;
+    noff = __shfl_sync(0xffffffffu, noff, 0);
+    if (noff < 0) return false;
+    const unsigned long long* src = a.heap_pool + q.off[t];
+    unsigned long long* dst = a.heap_pool + noff;
+    for (int i = lane; i < len; i += 32) __stcg(dst + i, __ldcg(src + i));
+    __syncwarp();
+    if (lane == 0) { q.off[t] = noff; q.cap[t] = ncap; }
+    __syncwarp();
+    return true;
+}
+
+// Files the entries e of the lanes with `has` under the queue's base (one
+// round: lanes with the same bucket form a group; the buckets that lack room
+// grow first, then each group's leader reserves its slots with one
+// shared-memory atomic).
+__device__ bool rq_file(RQ& q, bool has, unsigned long long e, int lane, const PropArgs& a) {
+    const int t = has ? rq_bucket(q.base, (int)(e >> 32)) : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, t);
+    const int leader = __ffs(grp) - 1;
+    const int cnt = __popc(grp);
+    const bool lead = has && lane == leader;
+    // buckets without room for their group grow (rare), one at a time
+    unsigned short_m = __ballot_sync(0xffffffffu, lead && q.len[t] + cnt > q.cap[t]);
+    while (short_m) {
+        const int L = __ffs(short_m) - 1;
+        short_m &= short_m - 1;
+        if (!rq_reserve(q, __shfl_sync(0xffffffffu, t, L), __shfl_sync(0xffffffffu, cnt, L), lane, a))
+            return false;
     }
-    H.h[i] = e;
+    int base = 0;
+    if (lead) {
+        base = atomicAdd(&q.len[t], cnt);
+        atomicOr(&q.nz, 1u << t);
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (has) {
+        __stcg(a.heap_pool + q.off[t] + base + __popc(grp & ((1u << lane) - 1u)), e);
+        atomicMax(&q.mx[t], e);                  // an empty bucket's highest entry is 0
+    }
+    const unsigned hm = __ballot_sync(0xffffffffu, has);
+    if (lane == 0) atomicAdd(&q.total, __popc(hm));
+    __syncwarp();
+    return true;
+}
+
+// Pushes one entry (the same e in every lane).
+__device__ __forceinline__ bool rq_push(RQ& q, unsigned long long e, int lane, const PropArgs& a) {
+    const int t = rq_bucket(q.base, (int)(e >> 32));
+    if (q.len[t] == q.cap[t] && !rq_reserve(q, t, 1, lane, a)) return false;
+    if (lane == 0) {
+        const int l = q.len[t];
+        __stcg(a.heap_pool + q.off[t] + l, e);
+        if (e > q.mx[t]) q.mx[t] = e;
+        q.len[t] = l + 1;
+        q.nz |= 1u << t;
+        ++q.total;
+    }
+    __syncwarp();
+    return true;
+}
+
+// Files the `n` entries at pool offset `off` (read in rounds of 32).
+__device__ bool rq_file_block(RQ& q, long long off, int n, int lane, const PropArgs& a) {
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const bool has = i0 + lane < n;
+        const unsigned long long e = has ? __ldcg(a.heap_pool + off + i0 + lane) : 0ull;
+        if (!rq_file(q, has, e, lane, a)) return false;
+    }
+    return true;
+}
+
+// Pops the highest entry (the queue is not empty).  false (uniform) when
+// refiling ran out of pool.
+__device__ bool rq_pop(RQ& q, unsigned long long& out, int lane, const PropArgs& a) {
+    int b = __ffs(q.nz) - 1;
+    if (b > 0 && q.len[b] == 1) {
+        // a bucket of one entry: it is the highest, and taking it leaves every bucket valid
+        out = q.mx[b];
+        __syncwarp();
+        if (lane == 0) {
+            q.len[b] = 0;
+            q.mx[b] = 0ull;
+            q.nz &= ~(1u << b);
+            --q.total;
+        }
+        __syncwarp();
+        return true;
+    }
+    if (b > 0) {
+        // refile bucket b under its highest key (its entries go to lower buckets)
+        const long long off = q.off[b];
+        const int n = q.len[b];
+        const unsigned long long top = q.mx[b];
+        __syncwarp();
+        if (lane == 0) {
+            q.len[b] = 0;
+            q.mx[b] = 0ull;
+            q.nz &= ~(1u << b);
+            q.total -= n;
+            q.base = (int)(top >> 32);
+        }
+        __syncwarp();
+        if (!rq_file_block(q, off, n, lane, a)) return false;
+        b = 0;
+    }
+    // bucket 0 holds entries of key base: copies of one vertex, all equal to its highest entry
+    out = q.mx[0];
+    __syncwarp();
+    if (lane == 0) {
+        if (--q.len[0] == 0) { q.nz &= ~1u; q.mx[0] = 0ull; }
+        --q.total;
+    }
+    __syncwarp();
+    return true;
+}
+
+// A stopped class's queue: its table (base, non-empty buckets, then per
+// bucket: offset, capacity and length, highest entry) written to the pool.  Returns the
+// table's pool offset (-1 for an empty queue, -2 when the pool is spent).
+__device__ long long rq_store_table(RQ& q, int lane, const PropArgs& a) {
+    const int nb = __popc(q.nz);
+    const int words = 1 + 3 * nb;
+    if (q.tend - q.tpos < words) {             // a new reserve (one global atomic per 1024 words)
+        long long r = 0;
+        if (lane == 0) {
+            r = (long long)atomicAdd((unsigned long long*)&a.ctr->heap_cursor, 1024ull);
+            if (r + 1024 > a.heap_cap) { set_oom(a.ctr, 1); r = -2; }
+        }
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (r < 0) return r;
+        __syncwarp();
+        if (lane == 0) { q.tpos = r; q.tend = r + 1024; }
+        __syncwarp();
+    }
+    const long long t = q.tpos;
+    __syncwarp();
+    if (lane == 0) q.tpos = t + words;
+    unsigned long long* w = a.heap_pool + t;
+    if (lane == 0) __stcg(w, ((unsigned long long)q.nz << 32) | (unsigned)q.base);
+    if ((q.nz >> lane) & 1u) {
+        const int r = __popc(q.nz & ((1u << lane) - 1u));
+        __stcg(w + 1 + 3 * r, (unsigned long long)q.off[lane]);
+        __stcg(w + 2 + 3 * r, ((unsigned long long)(unsigned)q.cap[lane] << 32) | (unsigned)q.len[lane]);
+        __stcg(w + 3 + 3 * r, q.mx[lane]);
+    }
+    return t;
+}
+
+__device__ __forceinline__ long long rq_store(RQ& q, int lane, const PropArgs& a) {
+    return q.total == 0 ? -1 : rq_store_table(q, lane, a);
+}
+
+// The team's queue absorbs a stopped class's queue (table at pool offset t,
+// `n` entries): the smaller queue is refiled into the larger one.  false
+// (uniform) when the pool is spent.
+__device__ bool rq_absorb(RQ& q, long long t, int n, int lane, const PropArgs& a) {
+    const unsigned long long* w = a.heap_pool + t;
+    const unsigned long long h = __ldcg(w);
+    const unsigned onz = (unsigned)(h >> 32);
+    const int obase = (int)(unsigned)h;
+    const int r = __popc(onz & ((1u << lane) - 1u));
+    const bool has = (onz >> lane) & 1u;
+    long long ooff = 0;
+    int olen = 0, ocap = 0;
+    unsigned long long omx = 0ull;
+    if (has) {
+        ooff = (long long)__ldcg(w + 1 + 3 * r);
+        const unsigned long long lc = __ldcg(w + 2 + 3 * r);
+        olen = (int)(unsigned)lc;
+        ocap = (int)(lc >> 32);
+        omx = __ldcg(w + 3 + 3 * r);
+    }
+    if (n > q.total) {
+        // adopt the other queue's buckets, then refile this queue's entries into it
+        const long long moff = q.off[lane];
+        const int mlen = q.len[lane];
+        const unsigned mnz = q.nz;
+        __syncwarp();
+        q.off[lane] = ooff;
+        q.len[lane] = olen;
+        q.cap[lane] = ocap;
+        q.mx[lane] = omx;
+        if (lane == 0) { q.base = obase; q.nz = onz; q.total = n; }
+        __syncwarp();
+        for (int b = 0; b < 32; ++b)
+            if (((mnz >> b) & 1u) && !rq_file_block(q, __shfl_sync(0xffffffffu, moff, b),
+                                                    __shfl_sync(0xffffffffu, mlen, b), lane, a))
+                return false;
+        return true;
+    }
+    for (int b = 0; b < 32; ++b)
+        if (((onz >> b) & 1u) && !rq_file_block(q, __shfl_sync(0xffffffffu, ooff, b),
+                                                __shfl_sync(0xffffffffu, olen, b), lane, a))
+            return false;
     return true;
 }
 
@@ -177,65 +405,15 @@ template <int NN>
 struct TeamState {
     static constexpr int TS = TeamCfg<NN>::TS;
     static constexpr int E = TeamCfg<NN>::E;
+    static_assert(TS == 32, "the overflow queue is run by whole warps");
     int sk[E];        // frontier slots: key (Od), -1 = empty
     int sv[E];        //                 vertex
     int rot;          // rotation of the slot assignment (spreads entries over lanes)
     unsigned tmask;
     int tb, lane;
-    Overflow ov;      // meaningful in team lane 0
-    int ovn;          // uniform copy of ov.n
-    int ov_top;       // uniform: key on top of the overflow heap, -1 if empty
+    int ov_top;       // uniform: key of the overflow queue's highest entry, -1 if empty
+    bool qused;       // uniform: the team's queue holds blocks of the current class
 };
-
-template <int NN>
-__device__ __forceinline__ void ov_sync(TeamState<NN>& T) {
-    int n = T.ov.n;
-    int top = n > 0 ? (int)(T.ov.h[0] >> 32) : -1;
-    T.ovn = __shfl_sync(T.tmask, n, T.tb);
-    T.ov_top = __shfl_sync(T.tmask, top, T.tb);
-}
-
-// Pops the top of the team's overflow heap (all team lanes call it).
-template <int NN>
-__device__ unsigned long long ov_pop_team(TeamState<NN>& T) {
-    __syncwarp(T.tmask);                       // the leader's pushes before the team's loads
-    unsigned long long* h = reinterpret_cast<unsigned long long*>(
-        __shfl_sync(T.tmask, reinterpret_cast<unsigned long long>(T.ov.h), T.tb));
-    const int n = __shfl_sync(T.tmask, T.ov.n, T.tb) - 1;
-    const bool leader = T.lane == T.tb;
-    const unsigned long long top = __ldcg(h);
-    if (n > 0) {
-        const unsigned long long last = __ldcg(h + n);
-        int i = 0;
-        constexpr int TS = TeamState<NN>::TS, K = 32 / TS;   // children per lane
-        for (;;) {
-            const int c0 = 32 * i + 1;
-            if (c0 >= n) break;
-            unsigned long long ce = 0ull;
-            int ci = -1;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                const int c = c0 + (T.lane - T.tb) + kk * TS;
-                if (c < n) {
-                    const unsigned long long e = __ldcg(h + c);
-                    if (ci < 0 || e > ce) { ce = e; ci = c; }
-                }
-            }
-            const unsigned hi = (unsigned)(ce >> 32), lo = (unsigned)ce;
-            const unsigned kh = __reduce_max_sync(T.tmask, hi);
-            const unsigned kl = __reduce_max_sync(T.tmask, hi == kh ? lo : 0u);
-            const int L = __ffs(__ballot_sync(T.tmask, ci >= 0 && hi == kh && lo == kl)) - 1;
-            const unsigned long long mv = ((unsigned long long)kh << 32) | kl;
-            if (mv <= last) break;
-            if (leader) __stcg(h + i, mv);
-            i = __shfl_sync(T.tmask, ci, L);
-        }
-        if (leader) __stcg(h + i, last);
-    }
-    if (leader) T.ov.n = n;
-    __syncwarp(T.tmask);
-    return top;
-}
 
 // Adds one candidate per lane (has, key, vert) to the team frontier.
 // Returns false (uniformly) if the overflow pool is exhausted.
@@ -299,10 +477,9 @@ __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, cons
             }
             out = pack(MK, ev);
         }
-        int r = 1;
-        if (T.lane == T.tb) r = ov_push(T.ov, out, a) ? 1 : 0;
-        r = __shfl_sync(T.tmask, r, T.tb);
-        ov_sync(T);
+        const bool r = rq_push(team_rq(), out, T.lane, a);
+        T.qused = true;
+        T.ov_top = rq_top(team_rq());
         if (!r) { ok = false; break; }
     }
     return ok;
@@ -428,8 +605,10 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
     const int tl = T.lane - T.tb;
     const bool leader = tl == 0;
     T.rot = 0;
-    T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0;
-    T.ovn = 0; T.ov_top = -1;
+    if (T.lane == 0) { team_rq().tpos = 0; team_rq().tend = 0; }
+    rq_reset(team_rq(), T.lane);
+    T.qused = false;
+    T.ov_top = -1;
 #pragma unroll
     for (int e = 0; e < E; ++e) { T.sk[e] = -1; T.sv[e] = 0; }
 
@@ -466,7 +645,9 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             const int seed = __shfl_sync(T.tmask, t.w, T.tb);
 #pragma unroll
             for (int e = 0; e < E; ++e) T.sk[e] = -1;
-            T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0; T.ovn = 0; T.ov_top = -1;
+            if (T.qused) rq_reset(team_rq(), T.lane);
+            T.qused = false;
+            T.ov_top = -1;
             const int mk = c;
             bool ok;
             if (seed >= 0) {                           // u has one higher neighbour, the seed of c
@@ -529,8 +710,9 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                 break;
             }
             if (T.ov_top > K) {
-                const unsigned long long e = ov_pop_team(T);
-                ov_sync(T);
+                unsigned long long e;
+                if (!rq_pop(team_rq(), e, T.lane, a)) break;
+                T.ov_top = rq_top(team_rq());
                 v = (int)(e & 0xffffffffu);
                 kv = (int)(e >> 32);
             } else {
@@ -646,14 +828,17 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                 }
                 pos += 2 * __popc(m);
             }
-            __syncwarp(T.tmask);                       // orders the team's spill writes before the leader's release
+            // the overflow queue stays in the pool; its table is written there
+            const long long qrec = T.qused ? rq_store(team_rq(), T.lane, a) : -1;
+            if (qrec == -2) break;
+            const int qn = qrec >= 0 ? team_rq().total : 0;
+            __syncwarp(T.tmask);                       // orders the team's spill and queue writes before the leader's release
             int tot = 0;
             if (leader) {
                 __stcg(a.spill_base + c, (int)base);
                 __stcg(a.spill_n + c, total);
                 __stcg(a.wait_v + c, v);
-                const long long ho = T.ov.h ? (long long)(T.ov.h - a.heap_pool) : 0;
-                __stcg(a.heaprec + c, make_int4((int)(ho & 0xffffffffLL), (int)(ho >> 32), T.ov.n, T.ov.cap));
+                __stcg(a.heaprec + c, make_int4((int)(qrec & 0xffffffffLL), (int)(qrec >> 32), qn, 0));
                 if (PERS) __stcg(a.ctop + c, make_int2(top_v, top_k));
                 // release: this class's spill and records; acquire: those of the
                 // classes that arrived before
@@ -663,8 +848,9 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             tot = __shfl_sync(T.tmask, tot, T.tb);
             if (tot < h) {                             // a higher neighbour is still unvisited: stop
                 c = -1;
-                T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0;   // the heap block now belongs to the class
-                T.ovn = 0; T.ov_top = -1;
+                if (T.qused) rq_reset(team_rq(), T.lane);   // the queue's blocks now belong to the class
+                T.qused = false;
+                T.ov_top = -1;
                 continue;
             }
             // ---- last arrival: merge every class stopped at v ----
@@ -719,22 +905,13 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                     }
                     okm = insert_batch(T, hs, ou, u, a);
                 }
-                // its overflow heap: keep the larger heap, push the smaller one's
-                // entries into it (each entry moves O(log) times over the pass)
+                // its overflow queue: the smaller of the two queues is refiled into the larger
                 const int rhn = __shfl_sync(T.tmask, hr.z, L);
                 if (rhn > 0 && okm) {
                     const int rlo = __shfl_sync(T.tmask, hr.x, L), rhi = __shfl_sync(T.tmask, hr.y, L);
-                    const int rcap = __shfl_sync(T.tmask, hr.w, L);
-                    int hok = 1;
-                    if (leader) {
-                        const long long off = ((long long)rhi << 32) | (unsigned)rlo;
-                        Overflow R{a.heap_pool + off, rhn, rcap};
-                        if (R.n > T.ov.n) { const Overflow t2 = T.ov; T.ov = R; R = t2; }
-                        for (int i = 0; i < R.n && hok; ++i) hok = ov_push(T.ov, __ldcg(R.h + i), a) ? 1 : 0;
-                    }
-                    hok = __shfl_sync(T.tmask, hok, T.tb);
-                    ov_sync(T);
-                    okm = hok != 0;
+                    okm = rq_absorb(team_rq(), ((long long)rhi << 32) | (unsigned)rlo, rhn, T.lane, a);
+                    T.qused = true;
+                    T.ov_top = rq_top(team_rq());
                 }
             }
             if (!okm) break;
