@@ -66,7 +66,7 @@ STAGE_BYTES = {"order_field": (64, "vertex"), "classify": (8, "vertex"), "reorde
 #   order field: the two-pass sort on compressed keys (the recipe's fields have
 #     few distinct values; the algorithmic count above stays the general one)
 #   propagate: first_step_kernel + propagate_kernel, both passes
-STAGE_TRAFFIC = {"order_field": 41.7, "propagate": 677.0}
+STAGE_TRAFFIC = {"order_field": 41.7, "propagate": 712.0}
 PATH_BYTES_PER_VERTEX = 100   # sort + classify + flatten, both passes
 
 

@@ -11,7 +11,10 @@ per (GPU name, number of dimensions, size bucket) in a JSON cache:
   batch_workspaces      workspaces a batch spreads its fields over.
 
 A tuning changes launch shapes only, never a result; the tuner checks that
-every candidate reproduces the default tuning's output bit for bit.
+every candidate reproduces the default tuning's output bit for bit.  A
+candidate replaces the current choice only when it is faster by more than
+MARGIN (timing noise between candidates is about 1%), so the cache keeps the
+defaults where no choice is clearly better.
 
 Per-shape entries are timed on lts_simplify_persistence over a synthetic
 field of the bucket's size (every stage of both passes runs, and no
@@ -28,6 +31,7 @@ import time
 KNOBS = {"engine_blocks_per_sm": (4, 6, 8), "team_blocks_per_sm": (8, 12, 16)}
 BATCH_KNOBS = {"batch_workspaces": (8, 16, 32)}
 DEFAULTS = {"engine_blocks_per_sm": 8, "team_blocks_per_sm": 12, "batch_workspaces": 32}
+MARGIN = 0.02
 CACHE_ENV = "LTS_TUNING_CACHE"
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 
@@ -100,9 +104,10 @@ def _time(fn, sync, reps):
     return statistics.median(ts)
 
 
-def _descend(ctx, knobs, run, same, reps, sync, timer=None):
+def _descend(ctx, knobs, run, same, reps, sync, timer=None, margin=MARGIN):
     """One pass of coordinate descent from the defaults: each knob in turn
-    takes the fastest of its candidates, the others held."""
+    takes the fastest of its candidates (when it beats the current choice by
+    more than `margin`), the others held."""
     timer = timer or (lambda fn: _time(fn, sync, reps))
     best = {k: DEFAULTS[k] for k in knobs}
     ctx.set_tuning(best)
@@ -124,7 +129,7 @@ def _descend(ctx, knobs, run, same, reps, sync, timer=None):
                 raise RuntimeError(f"tuning {t} changed the result")
             dt = timer(run)
             trials.append((dict(t), dt))
-            if dt < best_t:
+            if dt < best_t * (1.0 - margin):
                 best, best_t = t, dt
     ctx.set_tuning(best)
     return best, best_t, trials

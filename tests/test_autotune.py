@@ -70,6 +70,22 @@ def test_descent_keeps_the_fastest_candidate_of_each_knob():
     assert len(trials) == 1 + 2 + 2
 
 
+def test_descent_keeps_the_default_unless_a_candidate_is_clearly_faster():
+    ctx = FakeCtx()
+    cost = {4: 1.00, 6: 0.995, 8: 1.0}                   # 0.5% apart: noise
+
+    def timer(run):
+        return cost[ctx.tuning()["engine_blocks_per_sm"]]
+
+    best, sec, _ = AT._descend(ctx, {"engine_blocks_per_sm": (4, 6, 8)}, lambda: 1, lambda a, b: a == b, 1,
+                               lambda: None, timer)
+    assert best == {"engine_blocks_per_sm": 8} and sec == 1.0
+    cost[6] = 0.9
+    best, sec, _ = AT._descend(ctx, {"engine_blocks_per_sm": (4, 6, 8)}, lambda: 1, lambda a, b: a == b, 1,
+                               lambda: None, timer)
+    assert best == {"engine_blocks_per_sm": 6} and sec == 0.9
+
+
 def test_descent_refuses_a_tuning_that_changes_the_result():
     ctx = FakeCtx()
     with pytest.raises(RuntimeError):
