@@ -85,7 +85,8 @@ struct PropArgs {
     int* cnt;
     int* spill_base;
     int* spill_n;
-    int4* heaprec;               // a stopped class's overflow queue: (table offset low, high, entries, 0)
+    int4* heaprec;               // a stopped class's overflow queue: (table offset low, high, entries, 0),
+                                 // or for the selection's heap (block offset low, high, entries, capacity)
     int* spill_pool;
     long long spill_cap;
     unsigned long long* heap_pool;
@@ -401,6 +402,39 @@ __device__ bool rq_absorb(RQ& q, long long t, int n, int lane, const PropArgs& a
     return true;
 }
 
+// The persistence-driven selection keeps a 32-ary max-heap in HBM instead
+// (a pop sifts down one level per coalesced load of 32 children and a team
+// reduction; lane 0 holds the state and pushes): its propagations end at eps
+// with most of their queue unpopped, and a heap touches only what it pops,
+// where refiling would move entries that are never taken.
+struct Overflow {
+    unsigned long long* h;
+    int n, cap;
+};
+
+__device__ bool ov_push(Overflow& H, unsigned long long e, const PropArgs& a) {
+    if (H.n == H.cap) {
+        const int ncap = max(2 * H.cap, 256);
+        const long long off = atomicAdd((unsigned long long*)&a.ctr->heap_cursor, (unsigned long long)ncap);
+        if (off + ncap > a.heap_cap) { set_oom(a.ctr, 1); return false; }
+        unsigned long long* nh = a.heap_pool + off;
+        for (int i = 0; i < H.n; ++i) nh[i] = H.h[i];
+        if (H.cap == 0) atomicAdd(&a.ctr->heap_spills, 1);
+        H.h = nh;
+        H.cap = ncap;
+    }
+    int i = H.n++;
+    while (i > 0) {
+        const int p = (i - 1) >> 5;
+        const unsigned long long pe = H.h[p];
+        if (pe >= e) break;
+        H.h[i] = pe;
+        i = p;
+    }
+    H.h[i] = e;
+    return true;
+}
+
 template <int NN>
 struct TeamState {
     static constexpr int TS = TeamCfg<NN>::TS;
@@ -413,11 +447,57 @@ struct TeamState {
     int tb, lane;
     int ov_top;       // uniform: key of the overflow queue's highest entry, -1 if empty
     bool qused;       // uniform: the team's queue holds blocks of the current class
+    Overflow ov;      // the selection's heap (meaningful in team lane 0)
 };
+
+template <int NN>
+__device__ __forceinline__ void ov_sync(TeamState<NN>& T) {
+    const int n = T.ov.n;
+    const int top = n > 0 ? (int)(T.ov.h[0] >> 32) : -1;
+    T.ov_top = __shfl_sync(T.tmask, top, T.tb);
+}
+
+// Pops the top of the team's overflow heap (all team lanes call it).
+template <int NN>
+__device__ unsigned long long ov_pop_team(TeamState<NN>& T) {
+    __syncwarp(T.tmask);                       // the leader's pushes before the team's loads
+    unsigned long long* h = reinterpret_cast<unsigned long long*>(
+        __shfl_sync(T.tmask, reinterpret_cast<unsigned long long>(T.ov.h), T.tb));
+    const int n = __shfl_sync(T.tmask, T.ov.n, T.tb) - 1;
+    const bool leader = T.lane == T.tb;
+    const unsigned long long top = __ldcg(h);
+    if (n > 0) {
+        const unsigned long long last = __ldcg(h + n);
+        int i = 0;
+        for (;;) {
+            const int c0 = 32 * i + 1;
+            if (c0 >= n) break;
+            unsigned long long ce = 0ull;
+            int ci = -1;
+            const int c = c0 + (T.lane - T.tb);
+            if (c < n) {
+                ce = __ldcg(h + c);
+                ci = c;
+            }
+            const unsigned hi = (unsigned)(ce >> 32), lo = (unsigned)ce;
+            const unsigned kh = __reduce_max_sync(T.tmask, hi);
+            const unsigned kl = __reduce_max_sync(T.tmask, hi == kh ? lo : 0u);
+            const int L = __ffs(__ballot_sync(T.tmask, ci >= 0 && hi == kh && lo == kl)) - 1;
+            const unsigned long long mv = ((unsigned long long)kh << 32) | kl;
+            if (mv <= last) break;
+            if (leader) __stcg(h + i, mv);
+            i = __shfl_sync(T.tmask, ci, L);
+        }
+        if (leader) __stcg(h + i, last);
+    }
+    if (leader) T.ov.n = n;
+    __syncwarp(T.tmask);
+    return top;
+}
 
 // Adds one candidate per lane (has, key, vert) to the team frontier.
 // Returns false (uniformly) if the overflow pool is exhausted.
-template <int NN>
+template <bool PERS, int NN>
 __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, const PropArgs& a) {
     constexpr int TS = TeamState<NN>::TS, E = TeamState<NN>::E;
     const int tl = T.lane - T.tb;
@@ -477,9 +557,17 @@ __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, cons
             }
             out = pack(MK, ev);
         }
-        const bool r = rq_push(team_rq(), out, T.lane, a);
-        T.qused = true;
-        T.ov_top = rq_top(team_rq());
+        bool r;
+        if constexpr (PERS) {
+            int rr = 1;
+            if (T.lane == T.tb) rr = ov_push(T.ov, out, a) ? 1 : 0;
+            r = __shfl_sync(T.tmask, rr, T.tb) != 0;
+            ov_sync(T);
+        } else {
+            r = rq_push(team_rq(), out, T.lane, a);
+            T.qused = true;
+            T.ov_top = rq_top(team_rq());
+        }
         if (!r) { ok = false; break; }
     }
     return ok;
@@ -487,7 +575,7 @@ __device__ bool insert_batch(TeamState<NN>& T, bool has, int key, int vert, cons
 
 // The queue of a class that stopped at its first pop u: the neighbours of its
 // seed m but u, inserted unless the class `mark` already queued them.
-template <int DIR, int NN>
+template <int DIR, int NN, bool PERS>
 __device__ __forceinline__ bool rebuild_first_queue(TeamState<NN>& T, const Geom& g, const int* __restrict__ O, int m,
                                                     int u, int mark, const PropArgs& a, int tl) {
     int x, y, z;
@@ -500,7 +588,7 @@ __device__ __forceinline__ bool rebuild_first_queue(TeamState<NN>& T, const Geom
         if (__ldcg(a.qmark + nb) == mark) cand = false;
         else __stcg(a.qmark + nb, mark);
     }
-    return insert_batch(T, cand, key, nb, a);
+    return insert_batch<PERS>(T, cand, key, nb, a);
 }
 
 // First step (thread per class c): claim the seed m and log it (log slots
@@ -605,8 +693,11 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
     const int tl = T.lane - T.tb;
     const bool leader = tl == 0;
     T.rot = 0;
-    if (T.lane == 0) { team_rq().tpos = 0; team_rq().tend = 0; }
-    rq_reset(team_rq(), T.lane);
+    T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0;
+    if constexpr (!PERS) {
+        if (T.lane == 0) { team_rq().tpos = 0; team_rq().tend = 0; }
+        rq_reset(team_rq(), T.lane);
+    }
     T.qused = false;
     T.ov_top = -1;
 #pragma unroll
@@ -645,7 +736,11 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             const int seed = __shfl_sync(T.tmask, t.w, T.tb);
 #pragma unroll
             for (int e = 0; e < E; ++e) T.sk[e] = -1;
-            if (T.qused) rq_reset(team_rq(), T.lane);
+            if constexpr (PERS) {
+                T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0;
+            } else if (T.qused) {
+                rq_reset(team_rq(), T.lane);
+            }
             T.qused = false;
             T.ov_top = -1;
             const int mk = c;
@@ -657,7 +752,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                     top_k = od<DIR>(__ldg(O + seed), g.n);
                     top_f = __ldg(a.F + seed);
                 }
-                ok = rebuild_first_queue<DIR, NN>(T, g, O, seed, u, mk, a, tl);
+                ok = rebuild_first_queue<DIR, NN, PERS>(T, g, O, seed, u, mk, a, tl);
             } else {
                 // a meeting at u: its higher neighbours are the seeds of the classes that met
                 merged = true;
@@ -684,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                     const int w = __shfl_sync(T.tmask, unb, L);
                     const int r = __shfl_sync(T.tmask, own, L);
                     if (leader && r != c) __stcg(a.parent + r, c);
-                    ok = rebuild_first_queue<DIR, NN>(T, g, O, w, u, mk, a, tl);
+                    ok = rebuild_first_queue<DIR, NN, PERS>(T, g, O, w, u, mk, a, tl);
                 }
                 if (leader) __stcg(a.cnt + u, 0);
             }
@@ -711,8 +806,13 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             }
             if (T.ov_top > K) {
                 unsigned long long e;
-                if (!rq_pop(team_rq(), e, T.lane, a)) break;
-                T.ov_top = rq_top(team_rq());
+                if constexpr (PERS) {
+                    e = ov_pop_team(T);
+                    ov_sync(T);
+                } else {
+                    if (!rq_pop(team_rq(), e, T.lane, a)) break;
+                    T.ov_top = rq_top(team_rq());
+                }
                 v = (int)(e & 0xffffffffu);
                 kv = (int)(e >> 32);
             } else {
@@ -829,16 +929,25 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                 pos += 2 * __popc(m);
             }
             // the overflow queue stays in the pool; its table is written there
-            const long long qrec = T.qused ? rq_store(team_rq(), T.lane, a) : -1;
-            if (qrec == -2) break;
-            const int qn = qrec >= 0 ? team_rq().total : 0;
+            long long qrec = -1;
+            int qn = 0, qcap = 0;
+            if constexpr (PERS) {
+                // the heap block stays where it is, recorded with the class
+                qrec = T.ov.h ? (long long)(T.ov.h - a.heap_pool) : 0;
+                qn = T.ov.n;
+                qcap = T.ov.cap;
+            } else {
+                qrec = T.qused ? rq_store(team_rq(), T.lane, a) : -1;
+                if (qrec == -2) break;
+                qn = qrec >= 0 ? team_rq().total : 0;
+            }
             __syncwarp(T.tmask);                       // orders the team's spill and queue writes before the leader's release
             int tot = 0;
             if (leader) {
                 __stcg(a.spill_base + c, (int)base);
                 __stcg(a.spill_n + c, total);
                 __stcg(a.wait_v + c, v);
-                __stcg(a.heaprec + c, make_int4((int)(qrec & 0xffffffffLL), (int)(qrec >> 32), qn, 0));
+                __stcg(a.heaprec + c, make_int4((int)(qrec & 0xffffffffLL), (int)(qrec >> 32), qn, qcap));
                 if (PERS) __stcg(a.ctop + c, make_int2(top_v, top_k));
                 // release: this class's spill and records; acquire: those of the
                 // classes that arrived before
@@ -848,7 +957,11 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
             tot = __shfl_sync(T.tmask, tot, T.tb);
             if (tot < h) {                             // a higher neighbour is still unvisited: stop
                 c = -1;
-                if (T.qused) rq_reset(team_rq(), T.lane);   // the queue's blocks now belong to the class
+                if constexpr (PERS) {
+                    T.ov.h = nullptr; T.ov.n = 0; T.ov.cap = 0;   // the heap block now belongs to the class
+                } else if (T.qused) {
+                    rq_reset(team_rq(), T.lane);               // the queue's blocks now belong to the class
+                }
                 T.qused = false;
                 T.ov_top = -1;
                 continue;
@@ -889,7 +1002,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                 const int rsb = __shfl_sync(T.tmask, sb, L);
                 const int rsn = __shfl_sync(T.tmask, sn, L);
                 if (rsn < 0) {                         // stopped at its first pop: v, below its seed
-                    okm = rebuild_first_queue<DIR, NN>(T, g, O, __shfl_sync(T.tmask, nb, L), v, mark, a, tl);
+                    okm = rebuild_first_queue<DIR, NN, PERS>(T, g, O, __shfl_sync(T.tmask, nb, L), v, mark, a, tl);
                 }
                 for (int i = 0; i < rsn && okm; i += TS) {
                     const int idx = i + tl;
@@ -903,15 +1016,29 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
                         if (__ldcg(a.qmark + u) == mark) hs = false;
                         else __stcg(a.qmark + u, mark);
                     }
-                    okm = insert_batch(T, hs, ou, u, a);
+                    okm = insert_batch<PERS>(T, hs, ou, u, a);
                 }
                 // its overflow queue: the smaller of the two queues is refiled into the larger
                 const int rhn = __shfl_sync(T.tmask, hr.z, L);
                 if (rhn > 0 && okm) {
                     const int rlo = __shfl_sync(T.tmask, hr.x, L), rhi = __shfl_sync(T.tmask, hr.y, L);
-                    okm = rq_absorb(team_rq(), ((long long)rhi << 32) | (unsigned)rlo, rhn, T.lane, a);
-                    T.qused = true;
-                    T.ov_top = rq_top(team_rq());
+                    const long long roff = ((long long)rhi << 32) | (unsigned)rlo;
+                    if constexpr (PERS) {
+                        // keep the larger heap, push the smaller one's entries into it
+                        const int rcap = __shfl_sync(T.tmask, hr.w, L);
+                        int hok = 1;
+                        if (leader) {
+                            Overflow R{a.heap_pool + roff, rhn, rcap};
+                            if (R.n > T.ov.n) { const Overflow t2 = T.ov; T.ov = R; R = t2; }
+                            for (int i = 0; i < R.n && hok; ++i) hok = ov_push(T.ov, __ldcg(R.h + i), a) ? 1 : 0;
+                        }
+                        okm = __shfl_sync(T.tmask, hok, T.tb) != 0;
+                        ov_sync(T);
+                    } else {
+                        okm = rq_absorb(team_rq(), roff, rhn, T.lane, a);
+                        T.qused = true;
+                        T.ov_top = rq_top(team_rq());
+                    }
                 }
             }
             if (!okm) break;
@@ -927,7 +1054,7 @@ __global__ void __launch_bounds__(kThreads, 8) propagate_kernel(Geom g, const in
         // ---- v belongs to c: queue its lower neighbours ----
         const bool cand = nb >= 0 && on < kv && !inC && qm != mark;
         if (cand) __stcg(a.qmark + nb, mark);
-        if (!insert_batch(T, cand, on, nb, a)) break;
+        if (!insert_batch<PERS>(T, cand, on, nb, a)) break;
     }
     // every reserved log slot must hold a vertex or -1
     if (leader)
