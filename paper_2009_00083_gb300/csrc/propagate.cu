@@ -20,7 +20,8 @@
 // neighbours go out in one round trip and every branch is uniform within the
 // team.  The priority queue of the class is a top-K frontier in the team's
 // registers (E slots per lane), popped with a team max-reduction; entries that
-// do not fit go to a per-team binary heap in an HBM pool.  Popping v:
+// do not fit go to the team's overflow queue in an HBM pool (a radix queue,
+// see RQ below; a 32-ary heap in the persistence-driven selection).  Popping v:
 //   - v already in the class: skip;
 //   - claim v (atomicCAS on owner[v]); the vertex log records every claim;
 //   - k = higher neighbours of v in the class, h = all higher neighbours;
