@@ -628,6 +628,68 @@ __device__ __forceinline__ bool dense_mark_seeds(const Dense<NN>& D, int m, int 
     return __any_sync(0xffffffffu, any);
 }
 
+// The bounded cut search of the warp tier (wr_cuts below) on a dense tier's
+// shared-memory adjacency: before candidate a's first propagation, a search
+// from each neighbour of a in R (but s, local index m) over R \ {a} that ends
+// within 64 vertices without reaching s or a vertex an earlier search for a
+// reached has found a piece that a cuts off, so the propagation would not end
+// on a.  mark[] (P) holds a * 16 + t for the vertices the t-th search for a
+// reached; q (L2, free before the propagation) holds the search queue and, in
+// q[64], its length.
+template <int NN>
+__device__ bool dense_cuts(const Dense<NN>& D, int ai, int m, int lane) {
+    constexpr int kBudget = 64;
+    int* mark = D.P;
+    int* q = D.L2;
+    const int nb = lane < NN ? (int)D.adj[ai * NN + lane] : (int)kNoNbr;
+    unsigned todo = __ballot_sync(0xffffffffu, nb != kNoNbr && nb != m);
+    const int base = ai * 16;
+    int t = 0;
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int b0 = __shfl_sync(0xffffffffu, nb, src);
+        const int mb = mark[b0];
+        if (mb >= base && mb < base + 16) continue;   // reached by an earlier search for a
+        const int stamp = base + t++;
+        __syncwarp();
+        if (lane == 0) {
+            mark[b0] = stamp;
+            q[0] = b0;
+            q[kBudget] = 1;
+        }
+        __syncwarp();
+        int head = 0;
+        bool reach = false, over = false;
+        for (;;) {
+            const int tail = q[kBudget];
+            if (head >= tail) break;
+            const int i = head + lane < tail ? q[head + lane] : -1;
+            head = min(tail, head + 32);
+            bool rs = false;
+            if (i >= 0) {
+#pragma unroll
+                for (int k = 0; k < NN; ++k) {
+                    const int j = (int)D.adj[i * NN + k];
+                    if (j == (int)kNoNbr || j == ai) continue;
+                    if (j == m) { rs = true; continue; }
+                    const int old = atomicExch(mark + j, stamp);
+                    if (old == stamp) continue;
+                    if (old >= base && old < base + 16) { rs = true; continue; }   // joins an earlier search's piece
+                    const int slot = atomicAdd(q + kBudget, 1);
+                    if (slot < kBudget) q[slot] = j;
+                }
+            }
+            __syncwarp();
+            reach = __any_sync(0xffffffffu, rs);
+            over = q[kBudget] > kBudget;
+            if (reach || over) break;
+        }
+        if (!reach && !over) return true;
+    }
+    return false;
+}
+
 // per warp: v, L, L2, P (ints), adj (NN ushorts), rk and kidx (ushorts) per
 // vertex; the key bitmaps (b1: RMAX bits, b2: 4 words, b3: 1 word, 16-byte
 // slots); the flags (a byte per vertex)
@@ -688,6 +750,8 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
         }
         __syncwarp();
         dense_ranks(D, m, lane);                          // Od rank of every member
+        for (int i = lane; i < r; i += 32) D.P[i] = -1;  // the cut searches' marks
+        __syncwarp();
         // the minus-infinity vertex
         bool ok = false;
         int ai = -1;
@@ -699,6 +763,11 @@ __global__ void __launch_bounds__(32 * WPB) lo_dense_kernel(Geom g, LOArgs a, co
             if (K == INT_MAX) break;
             const int src = __ffs(__ballot_sync(0xffffffffu, bi >= 0 && best == K)) - 1;
             ai = __shfl_sync(0xffffffffu, bi, src);
+            if (dense_cuts(D, ai, m, lane)) {            // ai cuts off a small piece of R
+                if (lane == 0) D.f[ai] |= kTried;
+                __syncwarp();
+                continue;
+            }
             const int keep = D.L[ai];
             __syncwarp();
             if (lane == 0) D.L[ai] = -1;
