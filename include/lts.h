@@ -83,7 +83,7 @@ typedef struct {
     int64_t max_region[2];       /* members of the largest region                   */
     int32_t max_local_floods[2]; /* most propagations one region needed in step 2   */
     int64_t total_local_floods[2];
-    int64_t heap_spills[2];      /* floods whose priority queue left shared memory  */
+    int64_t heap_spills[2];      /* floods whose queue outgrew the register frontier */
     float stage_us[8];           /* device time per stage: order field, classify,   */
                                  /* propagation, regions, local order, reorder      */
                                  /* (summed over passes); [6] total; [7] unused.    */
@@ -196,9 +196,10 @@ lts_status lts_simplify_persistence(lts_ctx* ctx, const lts_grid* g, const float
  * at a time, and batching is this library's addition).  Array arguments
  * hold one entry per field, with the meaning they have in lts_simplify;
  * every field must fit the context's max_vertices.  The fields are spread
- * over the context's workspace and up to 31 more (allocated on first use
- * while the device keeps 1 GiB free beyond them, each sized for the largest
- * field of the batch, kept for later batches), each on its own stream,
+ * over the context's workspace and up to 31 more (batch_workspaces of
+ * lts_set_tuning bounds the total; allocated on first use while the device
+ * keeps 1 GiB free beyond them, each sized for the largest field of the
+ * batch, kept for later batches), each on its own stream,
  * largest fields first; LTS_ERR_OOM if not even one more fits.  (Streams
  * beyond the process's CUDA_DEVICE_MAX_CONNECTIONS hardware queues share
  * them.)  The extra streams start
